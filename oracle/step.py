@@ -1,0 +1,34 @@
+"""Oracle DNN-MG correction step (S8).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Algorithm 2 lines 6-9, in the paper's order:
+  v~     <- P(v^L)                      (line 6; S1)
+  d      <- N(v~, Omega_L, Omega_L+K)   (line 7; S2 residual, S3 features, S4 net)
+  b^L+K  <- Rhs(v~ + d)                 (line 8; S5 averaging, S6 right-hand side)
+  b^L    <- R(b^L+K)                    (line 9; S7)
+The residual of S2 uses the fine right-hand side b_f of the current step,
+i.e. the one assembled by the previous step's line 8.
+"""
+
+from .average import scatter_average
+from .features import patch_features
+from .fem import residual, rhs
+from .gru import gru_step
+from .transfer import prolongate, restrict
+
+
+def dnnmg_step(mesh, prm, weights, xc, h, bf, t):
+    """One correction step; returns every intermediate as float64 arrays.
+
+    weights = (Wx, Uh, Wfc); xc [3][Nc]; h [P][H]; bf [2][Nf]; t = t_n.
+    """
+    xf = prolongate(mesh, prm, xc, t)
+    r = residual(mesh, prm, xf, bf)
+    X = patch_features(mesh, prm, xf, r)
+    h_new, d = gru_step(X, h, *weights)
+    vcorr = scatter_average(mesh, d, xf)
+    bf_new = rhs(mesh, prm, vcorr)
+    bc = restrict(mesh, bf_new)
+    return {"xf": xf, "r": r, "X": X, "h": h_new, "d": d, "vcorr": vcorr,
+            "bf": bf_new, "bc": bc}
