@@ -1,0 +1,342 @@
+"""Benchmark of the DNN-MG fine-level correction step on GB300.
+
+One step = one full correction (Algorithm 2 lines 6-9: prolongation, residual
+and patch features, GRU patch network, averaging, right-hand side,
+restriction) of the large single instance: 2048 x 512 coarse cells, K = 2
+(8192 x 2048 fine cells, 16.8 M fine nodes), 2 x 2-cell patches (262 144
+patches), GRU width 128, BF16 network GEMMs with FP32 accumulation, FP32 fine
+fields, FP64 coarse vectors.  Inputs are synthetic (seeded Poiseuille flow
+with vortices around an elliptic obstacle); weights N(0, 0.1) from a seed.
+
+Metric: fine velocity DOF corrected per second (2 Nf per step / step time),
+with p50/p99 step latency.  Every step moves ~2.5 GB, far more than the 129 MB
+L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (one process per GPU under torchrun) every rank runs its own
+instance (replicas; there is no data-path collective) and value is the sum.
+--impl reference times the CPU FP64 oracle on a bounded window of the same
+workload on the host cores.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2008_11520_gb300 import synth  # noqa: E402
+
+METRIC = "fine DOF corrected/s per DNN-MG step"
+UNIT = "DOF/s"
+WORKLOAD = "large"
+
+
+def describe(c):
+    return (f"{c['nxc']}x{c['nyc']} coarse cells, K={c['K']} ({c['nxc'] << c['K']}x{c['nyc'] << c['K']} fine), "
+            f"{c['s']}x{c['s']}-cell patches, GRU hidden {c['H']}, {c['precision']} network, "
+            f"ellipse semi-axes {c['ellipse'][2]:.3f}x{c['ellipse'][3]:.4f}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        self.out.flush()
+        with open(self.out.name) as f:
+            rows = [r.split(",") for r in f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_work(info, H):
+    """Bytes each stage must move and the GEMM flops, per step."""
+    Nf, Nc, P, ldx, n_in, n_out = info.Nf, info.Nc, info.P, info.ldx, info.n_in, info.n_out
+    rb, fb = info.real_bytes, info.feature_bytes
+    return {
+        "prolongate": {"bytes": 3 * Nc * 8 + 3 * Nf * rb},
+        "residual_features": {"bytes": 3 * Nf * rb + 2 * Nf * rb + P * ldx * fb},
+        "gru": {"bytes": P * ldx * fb + 2 * P * H * rb + P * n_out * rb,
+                "flops": 2 * P * (3 * H * (n_in + H) + H * n_out)},
+        "scatter_avg": {"bytes": P * n_out * rb + 2 * Nf * rb + 2 * Nf * rb},
+        "rhs": {"bytes": 2 * Nf * rb + 2 * Nf * rb},
+        "restrict": {"bytes": 2 * Nf * rb + 3 * Nc * 8},
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2008_11520_gb300 import dnnmg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = synth.config(WORKLOAD)
+    mesh = dnnmg.Mesh(dnnmg.make_desc(c["nxc"], c["nyc"], c["K"], c["s"], c["ellipse"], precision=c["precision"]))
+    I = mesh.info
+    W = synth.net_weights(I.n_in, c["H"], I.n_out, seed=c["seed"])
+    net = dnnmg.Net(*W, precision=c["precision"])
+    spec = synth.FlowSpec.from_seed(c["seed"] + rank, c["ellipse"])
+    xc_np = synth.coarse_state(spec, c["nxc"], c["nyc"], 0.0)
+    v0 = synth.fine_state(spec, I.nxf, I.nyf, 0.0)[:2]
+    xc = torch.as_tensor(xc_np).to(dev).contiguous()
+    h = torch.zeros(I.P, c["H"], dtype=torch.float32, device=dev)
+    bf = torch.zeros(2, I.Nf, dtype=torch.float32, device=dev)
+    bc = torch.zeros(3, I.Nc, dtype=torch.float64, device=dev)
+    dnnmg.dnnmg_rhs_restrict(mesh, torch.as_tensor(v0, dtype=torch.float32).to(dev).contiguous(), bf, bc)
+    del v0
+    ws = mesh.workspace(dev)
+    stream = torch.cuda.current_stream()
+    k = 0.01
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for i in range(args.warmup):
+        dnnmg.dnnmg_step(mesh, net, xc, h, bf, bc, ws, i * k)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps of dnnmg_step, one event pair per step
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local_rank) as clk:
+        t0 = time.perf_counter()
+        ev[0].record(stream)
+        for i in range(args.steps):
+            dnnmg.dnnmg_step(mesh, net, xc, h, bf, bc, ws, (args.warmup + i) * k)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    clocks = clk.summary()
+
+    # ---- stage timing: the same kernels called stage by stage with events between them
+    wsv = torch.empty(0)
+    xf = torch.empty(3, I.Nf, dtype=torch.float32, device=dev)
+    X = torch.empty(I.P, I.ldx, dtype=torch.bfloat16, device=dev)
+    d = torch.empty(I.P, I.n_out, dtype=torch.float32, device=dev)
+    vc = torch.empty(2, I.Nf, dtype=torch.float32, device=dev)
+    names = ["prolongate", "residual_features", "gru", "scatter_avg", "rhs_restrict"]
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        e = sev[i]
+        e[0].record(stream)
+        dnnmg.dnnmg_prolongate(mesh, xc, xf, 0.0)
+        e[1].record(stream)
+        dnnmg.dnnmg_patch_features(mesh, xf, bf, X)
+        e[2].record(stream)
+        dnnmg.dnnmg_gru_step(net, X, h, d, I.P)
+        e[3].record(stream)
+        dnnmg.dnnmg_scatter_avg(mesh, d, xf, vc)
+        e[4].record(stream)
+        dnnmg.dnnmg_rhs_restrict(mesh, vc, bf, bc)
+        e[5].record(stream)
+    torch.cuda.synchronize()
+    stage_ms = {n: statistics.mean(sev[i][j].elapsed_time(sev[i][j + 1]) for i in range(args.steps))
+                for j, n in enumerate(names)}
+    del wsv
+
+    # ---- end to end: host x_c in, host b_c out, through dnnmg_step_host
+    xch = torch.as_tensor(xc_np).pin_memory()
+    bch = torch.empty(3 * I.Nc, dtype=torch.float64).pin_memory()
+    for i in range(2):
+        dnnmg.dnnmg_step_host(mesh, net, xch, h, bf, bch, ws, i * k)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        dnnmg.dnnmg_step_host(mesh, net, xch, h, bf, bch, ws, i * k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    assert np.isfinite(bch.numpy()).all()
+
+    times = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+    total_ms, e2e_ms = times.tolist()
+    return dict(cfg=c, info=I, per_step=per_step, total_ms=total_ms, stage_ms=stage_ms, clocks=clocks,
+                e2e_ms=e2e_ms, wall=wall, launches=dnnmg.dnnmg_step_launches(mesh, net))
+
+
+def cpu_baseline(seconds=12.0):
+    """The oracle as it stands on a window of the large workload; fine DOF/s."""
+    from oracle.mesh import Mesh as OMesh, Params
+    from oracle import fem, step as ostep
+
+    c = synth.config(WORKLOAD)
+    win = (1000, 200, 1064, 264)         # 64 x 64 coarse cells behind the obstacle
+    om = OMesh(c["nxc"], c["nyc"], c["K"], c["s"], ellipse=c["ellipse"], window=win)
+    spec = synth.FlowSpec.from_seed(c["seed"], c["ellipse"])
+    xc = synth.coarse_state(spec, c["nxc"], c["nyc"], 0.0, window=win)
+    r = om.r
+    fwin = (win[0] * r, win[1] * r, win[2] * r, win[3] * r)
+    v0 = synth.fine_state(spec, om.nxf, om.nyf, 0.0, window=fwin)[:2]
+    W = synth.net_weights(om.n_in, c["H"], om.n_out, seed=c["seed"])
+    prm = Params()
+    bf = fem.rhs(om, prm, v0)
+    h = np.zeros((om.P, c["H"]))
+    n, t0 = 0, time.perf_counter()
+    while True:
+        out = ostep.dnnmg_step(om, prm, W, xc, h, bf, n * prm.k)
+        h, bf = out["h"], out["bf"]
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    return {"value": 2 * om.Nf * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} steps of a 64x64-coarse-cell window ({om.Nf} fine nodes) of the workload, "
+                      f"{el:.1f} s; NumPy FP64, BLAS threads up to {threads}",
+            "steps": n, "seconds": el}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    c = synth.config(WORKLOAD)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(args.warmup):
+            cpu_baseline(seconds=1.0)
+        for _ in range(args.steps):
+            steps.append(cpu_baseline(seconds=2.0))
+        v = sum(s["value"] * s["seconds"] for s in steps) / sum(s["seconds"] for s in steps)
+        base = steps[0]
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sum(s["seconds"] for s in steps) / sum(s["steps"] for s in steps),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD + ": " + describe(c),
+                                                "sample": "64x64-coarse-cell window per step, CPU oracle"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                                 "sample": base["sample"]},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+    I = r["info"]
+    dof = 2 * I.Nf
+    step_ms = r["total_ms"] / args.steps
+    value = world * dof * args.steps / (r["total_ms"] / 1e3)
+    pk = peaks()
+    work = algorithmic_work(I, c["H"])
+    work["rhs_restrict"] = {"bytes": work.pop("rhs")["bytes"] + work.pop("restrict")["bytes"]}
+    # dominant kernel: the stage with the largest share of the step
+    dom = max(r["stage_ms"], key=r["stage_ms"].get)
+    dom_ms = r["stage_ms"][dom]
+    if dom == "gru":
+        ach = work["gru"]["flops"] / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": ach / pk["bf16_tflops"], "traffic": None,
+                "peak_src": pk["src"] + " bf16 burst"}
+    else:
+        ach = work[dom]["bytes"] / (dom_ms / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"] + " copy bandwidth"}
+    stages = {}
+    for n, ms in r["stage_ms"].items():
+        e = {"ms": ms, "GB/s": work[n]["bytes"] / (ms / 1e3) / 1e9}
+        e["hbm_frac"] = e["GB/s"] / pk["hbm_gbs"]
+        if "flops" in work[n]:
+            e["TFLOP/s"] = work[n]["flops"] / (ms / 1e3) / 1e12
+        stages[n] = e
+    per = sorted(r["per_step"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD + ": " + describe(c), "fine_dof_per_step": dof, "patches": I.P,
+                   "l2": "no flush: each step moves ~2.5 GB, inputs larger than the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "p50_ms": per[len(per) // 2], "p99_ms": per[min(len(per) - 1, int(0.99 * len(per)))],
+        "e2e": {"value": world * dof * args.steps / (r["e2e_ms"] / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": 3 * I.Nc * 8, "d2h_bytes_per_step": 3 * I.Nc * 8},
+        "gpu_launches": r["launches"] * args.steps,
+        "roofline": roof, "stages": stages, "clocks": r["clocks"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * dnnmg.h -- C ABI of the DNN-MG fine-level correction step on one GPU.
+ *
+ * DNN-MG (Margenberg, Hartmann, Lessig, Richter, arXiv 2008.11520) corrects a
+ * coarse multigrid solution on level L with a patch-wise recurrent network on
+ * level L+K.  After the coarse Newton-Krylov solve of a time step, Algorithm 2
+ * lines 6-9 do
+ *     v~    <- P(v^L)                      prolongation            (dnnmg_prolongate)
+ *     d     <- N(v~, Omega_L, Omega_L+K)   residual + features     (dnnmg_patch_features)
+ *                                          GRU + output layer      (dnnmg_gru_step)
+ *     b^L+K <- Rhs(v~ + d)                 averaging               (dnnmg_scatter_avg)
+ *                                          right-hand side
+ *     b^L   <- R(b^L+K)                    restriction             (dnnmg_rhs_restrict)
+ * and dnnmg_step runs all of them in order on one stream.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns DNNMG_OK (0) or an error code; dnnmg_last_error()
+ *    returns the calling thread's last message.  Invalid arguments are
+ *    reported before anything is enqueued.
+ *  - Array arguments are DEVICE pointers owned by the caller unless the name
+ *    ends in _host.  The library never frees caller memory and allocates
+ *    device memory only in *_create.  Compute calls are asynchronous on the
+ *    given stream and never synchronise.
+ *  - Node fields are planes [component][Nf] with Nf = (nxf+1)(nyf+1) fine
+ *    nodes numbered x fastest (node (I, J) at index J (nxf+1) + I), and
+ *    likewise [component][Nc] on the coarse level.  The fine "real" type is
+ *    double for DNNMG_F64 and float otherwise; coarse vectors are double.
+ *  - Patch arrays are row-major [P][.] over the fluid patches, numbered
+ *    lexicographically over the patch grid, patch-x fastest.
+ */
+#ifndef DNNMG_H
+#define DNNMG_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DNNMG_OK 0
+#define DNNMG_EINVAL 1       /* null pointer, size or parameter out of range */
+#define DNNMG_ECUDA 2        /* a CUDA runtime call or kernel launch failed */
+#define DNNMG_EUNSUPPORTED 3 /* valid request this build does not implement */
+#define DNNMG_ENOMEM 4       /* device allocation in *_create failed */
+
+/* precision of the fine fields and of the patch network */
+#define DNNMG_F64 0      /* fine fields, features and network in double */
+#define DNNMG_F32 1      /* fine fields, features and network in float */
+#define DNNMG_BF16NET 2  /* fine fields float; features and network GEMM
+                            operands bfloat16, accumulation and gates float */
+
+/*
+ * Mesh description (Sec. 6.1, Fig. geom; Sec. 5.2 patches).
+ * Channel [0, lx] x [0, ly] with nxc x nyc coarse cells (level L), refined K
+ * times (level L+K: nxf = nxc 2^K, nyf = nyc 2^K).  A coarse cell is solid iff
+ * its centroid lies strictly inside the ellipse (obst_*; obst_ax <= 0 means
+ * no obstacle) or, if `solid` is non-null, iff solid[j nxc + i] != 0 (host
+ * array, read only during the call).  Fine cells inherit the parent's flag.
+ * Velocity Dirichlet nodes: x = 0 (inflow profile u_max 4y(ly-y)/ly^2 w(t),
+ * w the start-up ramp of Sec. 6.1 if ramp != 0, else 1), y = 0 and y = ly
+ * (walls, 0) and nodes of solid cells (0).  Outflow x = lx is do-nothing.
+ * Patches are s x s coarse cells; a patch is fluid if one of its cells is.
+ * nu: viscosity (1/Re), k: time step, alpha0: LPS constant
+ * (alpha_T = alpha0 h_T^2 / nu, h_T the fine cell diagonal, Sec. 3.1).
+ * Constraints: nxc, nyc even and divisible by s; K in 1..3; s in 1..2.
+ */
+typedef struct dnnmg_mesh_desc {
+    int nxc, nyc;
+    int K;
+    int s;
+    double lx, ly;
+    double obst_cx, obst_cy, obst_ax, obst_ay;
+    const unsigned char *solid;
+    double nu, k, alpha0, u_max;
+    int ramp;
+    int precision;
+} dnnmg_mesh_desc;
+
+/*
+ * Sizes derived from a description.  nf = (s 2^K + 1)^2 fine and
+ * nc = (s+1)^2 coarse nodes per patch; n_in = 3 nf + 3 nc + 12 network inputs
+ * (residual, coarse velocity, Peclet number, geometry; Sec. 5.2), n_out = 2 nf
+ * outputs.  Feature rows are stored with leading dimension ldx =
+ * round_up(n_in, 16); columns n_in..ldx-1 are written as zero.
+ * workspace_bytes is what dnnmg_step / dnnmg_step_host need.
+ */
+typedef struct dnnmg_mesh_info {
+    int nxc, nyc, nxf, nyf, K, s;
+    int npx, npy;          /* patch grid */
+    long long Nc, Nf;      /* coarse / fine nodes */
+    int P;                 /* fluid patches */
+    int nf, nc, n_in, n_out, ldx;
+    int n_solid_coarse;    /* solid coarse cells */
+    int precision;
+    int real_bytes;        /* 8 for DNNMG_F64, else 4 */
+    int feature_bytes;     /* element size of the feature matrix X */
+    size_t workspace_bytes;
+} dnnmg_mesh_info;
+
+typedef struct dnnmg_mesh_s *dnnmg_mesh_t;
+typedef struct dnnmg_net_s *dnnmg_net_t;
+
+/* Host-only: validate a description and compute its sizes (no GPU needed). */
+int dnnmg_mesh_query(const dnnmg_mesh_desc *desc, dnnmg_mesh_info *info);
+
+/* Create a mesh on the current device: uploads the coarse cell mask and the
+ * patch numbering (owned by the handle).  Synchronous. */
+int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out);
+int dnnmg_mesh_destroy(dnnmg_mesh_t mesh);
+int dnnmg_mesh_get_info(dnnmg_mesh_t mesh, dnnmg_mesh_info *info);
+
+/*
+ * Index maps, for checking (Sec. 5.2 patches; Sec. 6.1 boundary classes):
+ *   patch_cell [P] int: patch-grid index pj npx + pi of fluid patch p;
+ *   node_flags [Nf] uint8: bit0 velocity Dirichlet, bit1 inflow value,
+ *                          bit2 pressure row active (touches a fluid cell);
+ *   node_mult  [Nf] uint8: number of fluid patches containing the node.
+ * Any output may be NULL.  Device pointers; asynchronous.
+ */
+int dnnmg_mesh_maps(dnnmg_mesh_t mesh, int *patch_cell, unsigned char *node_flags,
+                    unsigned char *node_mult, cudaStream_t stream);
+
+/*
+ * Patch network (Eq. gru, Sec. 6.2: GRU then a fully connected layer, no
+ * biases).  Host arrays, row-major, gate order z, r, h:
+ *   Wx [3H][n_in], Uh [3H][H], Wfc [n_out][H].
+ * Weights are copied to the device in the network precision (owned by the
+ * handle).  Synchronous.
+ */
+int dnnmg_net_create(int n_in, int hidden, int n_out, const double *Wx, const double *Uh,
+                     const double *Wfc, int precision, dnnmg_net_t *out);
+int dnnmg_net_destroy(dnnmg_net_t net);
+
+/*
+ * S1, Algorithm 2 line 6: xf = P xc on (u, v, p) by bilinear interpolation
+ * from level L to L+K, then the fine velocity Dirichlet values at time t.
+ *   xc [3][Nc] double (in), xf [3][Nf] real (out).
+ */
+int dnnmg_prolongate(dnnmg_mesh_t mesh, const double *xc, void *xf, double t,
+                     cudaStream_t stream);
+
+/*
+ * S2 + S3, Sec. 5.2 network inputs: the nonlinear residual
+ * r = b_f - A(xf) of Eq. nonlinearshort (Q1, 2x2 Gauss, LPS), zero on
+ * Dirichlet velocity rows and inactive pressure rows, and the feature matrix
+ *   X [P][ldx] (feature type: double / float / bfloat16 by precision), row
+ *   = [r_u(nf), r_v(nf), r_p(nf), u(nc), v(nc), Pe(nc), geometry(12), 0...]
+ * with patch nodes lexicographic (x fastest), u, v the prolongated velocity
+ * at the coarse patch nodes, Pe = q |v| / nu (q the longest patch edge) and
+ * geometry = edge lengths (bottom, right, top, left), aspect ratios
+ * (bottom/right, top/left, bottom/top, left/right), corner angles
+ * (SW, SE, NE, NW).
+ *   xf [3][Nf] real, bf [2][Nf] real (the current fine right-hand side),
+ *   rf [3][Nf] real (out, may be NULL), X (out).
+ */
+int dnnmg_patch_features(dnnmg_mesh_t mesh, const void *xf, const void *bf, void *rf,
+                         void *X, cudaStream_t stream);
+
+/*
+ * S4, Eq. gru and the output layer, for P patches at once:
+ *   z = sig(W_z x + U_z h), r = sig(W_r x + U_r h),
+ *   h <- z h + (1-z) tanh(W_h x + U_h (r h)),  d = W_fc h.
+ *   X [P][ldx] feature type (in), h [P][H] real (in/out; float for
+ *   DNNMG_BF16NET), d [P][n_out] real (out).  ldx = round_up(n_in, 16).
+ */
+int dnnmg_gru_step(dnnmg_net_t net, const void *X, void *h, void *d, int P,
+                   cudaStream_t stream);
+
+/*
+ * S5, Sec. 5.2 duplicate predictions averaged: vcorr = xf + mean of the
+ * predictions of the fluid patches containing each node, on velocity
+ * unknowns; Dirichlet nodes keep xf.  d row layout [u corr(nf), v corr(nf)].
+ *   d [P][n_out] real, xf [3][Nf] real (only u, v read), vcorr [2][Nf] real.
+ */
+int dnnmg_scatter_avg(dnnmg_mesh_t mesh, const void *d, const void *xf, void *vcorr,
+                      cudaStream_t stream);
+
+/*
+ * S6 + S7, Algorithm 2 lines 8-9: bf = Rhs(vcorr) of Eq. 4cranknicholson3
+ * (1/k (v,phi) - 1/2 (v.grad v,phi) - nu/2 (grad v,grad phi), no forcing),
+ * zero on Dirichlet rows; then bc = R bf with R = P^T, coarse Dirichlet
+ * velocity rows and all pressure rows zero.
+ *   vcorr [2][Nf] real (in), bf [2][Nf] real (out), bc [3][Nc] double (out).
+ */
+int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *bc,
+                       cudaStream_t stream);
+
+/*
+ * S1-S7 in order (Algorithm 2 lines 6-9) on one stream.
+ *   xc [3][Nc] double (in), h [P][H] (in/out), bf [2][Nf] (in: this step's
+ *   fine right-hand side; out: the next step's), bc [3][Nc] double (out),
+ *   workspace >= info.workspace_bytes device bytes (scratch, caller-owned,
+ *   256-byte aligned), t = t_n for the inflow values.
+ */
+int dnnmg_step(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf,
+               double *bc, void *workspace, size_t workspace_bytes, double t,
+               cudaStream_t stream);
+
+/*
+ * dnnmg_step with the coarse vectors in HOST memory: copies xc_host
+ * [3][Nc] to the device, runs the step, copies bc back to bc_host [3][Nc],
+ * all enqueued on `stream`.  Both host buffers must stay valid until the
+ * stream reaches this point; page-locked buffers make the copies
+ * asynchronous.  h and bf stay device-resident.
+ */
+int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, void *h,
+                    void *bf, double *bc_host, void *workspace, size_t workspace_bytes,
+                    double t, cudaStream_t stream);
+
+/* Number of kernel launches one dnnmg_step enqueues for this mesh/net. */
+int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net);
+
+/* Last error message of the calling thread ("" if none). */
+const char *dnnmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DNNMG_H */

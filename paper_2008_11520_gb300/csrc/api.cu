@@ -1,0 +1,573 @@
+// C ABI of libdnnmg (include/dnnmg.h): argument checks, handles, per-mesh
+// element constants, and the ordered launch sequence of one correction step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+// Opaque handle types of the C ABI are the internal structures.
+struct dnnmg_mesh_s : dnnmg::Mesh {};
+struct dnnmg_net_s : dnnmg::Net {};
+
+namespace dnnmg {
+
+namespace {
+thread_local std::string g_error;
+}
+
+int fail(int code, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+void clear_error() { g_error.clear(); }
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+cudaError_t launch_gru_cuda_core(const Net &n, const void *X, void *h, void *d, int P,
+                                 cudaStream_t st);
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Coarse solid mask by the centroid test (Sec. 6.1 geometry on a structured mesh).
+std::vector<uint8_t> solid_mask(const dnnmg_mesh_desc &d) {
+    std::vector<uint8_t> m((size_t)d.nxc * d.nyc, 0);
+    if (d.solid) {
+        for (size_t i = 0; i < m.size(); ++i) m[i] = d.solid[i] ? 1 : 0;
+        return m;
+    }
+    if (!(d.obst_ax > 0 && d.obst_ay > 0)) return m;
+    const double hx = d.lx / d.nxc, hy = d.ly / d.nyc;
+    for (int j = 0; j < d.nyc; ++j)
+        for (int i = 0; i < d.nxc; ++i) {
+            const double xc = (i + 0.5) * hx, yc = (j + 0.5) * hy;
+            const double tx = (xc - d.obst_cx) / d.obst_ax, ty = (yc - d.obst_cy) / d.obst_ay;
+            const double tx2 = tx * tx, ty2 = ty * ty;
+            m[(size_t)j * d.nxc + i] = (tx2 + ty2 < 1.0) ? 1 : 0;
+        }
+    return m;
+}
+
+// Fluid patch numbering: lexicographic over the patch grid, patch-x fastest.
+int patch_numbering(const dnnmg_mesh_desc &d, const std::vector<uint8_t> &solid,
+                    std::vector<int> *id, std::vector<int> *cell) {
+    const int npx = d.nxc / d.s, npy = d.nyc / d.s;
+    if (id) id->assign((size_t)npx * npy, -1);
+    if (cell) cell->clear();
+    int P = 0;
+    for (int pj = 0; pj < npy; ++pj)
+        for (int pi = 0; pi < npx; ++pi) {
+            bool fluid = false;
+            for (int b = 0; b < d.s; ++b)
+                for (int a = 0; a < d.s; ++a)
+                    if (!solid[(size_t)(pj * d.s + b) * d.nxc + pi * d.s + a]) fluid = true;
+            if (!fluid) continue;
+            if (id) (*id)[(size_t)pj * npx + pi] = P;
+            if (cell) cell->push_back(pj * npx + pi);
+            ++P;
+        }
+    return P;
+}
+
+int validate_desc(const dnnmg_mesh_desc *d) {
+    if (!d) return fail(DNNMG_EINVAL, "mesh description is NULL");
+    if (d->nxc <= 0 || d->nyc <= 0 || d->nxc % 2 || d->nyc % 2)
+        return fail(DNNMG_EINVAL, "nxc=%d, nyc=%d: cell counts must be positive and even", d->nxc, d->nyc);
+    if (d->K < 1 || d->K > 3) return fail(DNNMG_EINVAL, "K=%d out of range 1..3", d->K);
+    if (d->s < 1 || d->s > 2) return fail(DNNMG_EINVAL, "s=%d out of range 1..2", d->s);
+    if (d->nxc % d->s || d->nyc % d->s)
+        return fail(DNNMG_EINVAL, "patch size s=%d must divide nxc=%d and nyc=%d", d->s, d->nxc, d->nyc);
+    if (!(d->lx > 0) || !(d->ly > 0) || !(d->nu > 0) || !(d->k > 0) || !(d->alpha0 >= 0))
+        return fail(DNNMG_EINVAL, "lx, ly, nu, k must be > 0 and alpha0 >= 0");
+    if (d->precision < DNNMG_F64 || d->precision > DNNMG_BF16NET)
+        return fail(DNNMG_EINVAL, "unknown precision %d", d->precision);
+    const long long nyf = (long long)d->nyc << d->K, nxf = (long long)d->nxc << d->K;
+    if (nyf + 1 > 65535) return fail(DNNMG_EUNSUPPORTED, "nyf=%lld: at most 65534 fine rows", nyf);
+    if ((nxf + 1) * (nyf + 1) > (1LL << 31))
+        return fail(DNNMG_EUNSUPPORTED, "%lld fine nodes: at most 2^31", (nxf + 1) * (nyf + 1));
+    return DNNMG_OK;
+}
+
+void fill_info(const dnnmg_mesh_desc &d, int P, int n_solid, dnnmg_mesh_info *info) {
+    dnnmg_mesh_info &I = *info;
+    memset(&I, 0, sizeof I);
+    I.nxc = d.nxc;
+    I.nyc = d.nyc;
+    I.K = d.K;
+    I.s = d.s;
+    I.nxf = d.nxc << d.K;
+    I.nyf = d.nyc << d.K;
+    I.npx = d.nxc / d.s;
+    I.npy = d.nyc / d.s;
+    I.Nc = (long long)(d.nxc + 1) * (d.nyc + 1);
+    I.Nf = (long long)(I.nxf + 1) * (I.nyf + 1);
+    I.P = P;
+    const int S = d.s << d.K;
+    I.nf = (S + 1) * (S + 1);
+    I.nc = (d.s + 1) * (d.s + 1);
+    I.n_in = 3 * I.nf + 3 * I.nc + 12;
+    I.n_out = 2 * I.nf;
+    I.ldx = round_up(I.n_in, 16);
+    I.n_solid_coarse = n_solid;
+    I.precision = d.precision;
+    I.real_bytes = d.precision == DNNMG_F64 ? 8 : 4;
+    I.feature_bytes = d.precision == DNNMG_F64 ? 8 : (d.precision == DNNMG_F32 ? 4 : 2);
+    size_t ws = 0;
+    ws += align256(3 * (size_t)I.Nf * I.real_bytes);            // x~
+    ws += align256((size_t)P * I.ldx * I.feature_bytes);        // X
+    ws += align256((size_t)P * I.n_out * I.real_bytes);         // d
+    ws += align256(2 * (size_t)I.Nf * I.real_bytes);            // v_corr
+    ws += 2 * align256(3 * (size_t)I.Nc * sizeof(double));      // host-call staging of x_c, b_c
+    I.workspace_bytes = ws;
+}
+
+struct Workspace {
+    void *xf, *X, *d, *vc;
+    double *xc, *bc;
+};
+
+Workspace carve(const dnnmg_mesh_info &I, void *base) {
+    Workspace w;
+    char *p = static_cast<char *>(base);
+    w.xf = p;
+    p += align256(3 * (size_t)I.Nf * I.real_bytes);
+    w.X = p;
+    p += align256((size_t)I.P * I.ldx * I.feature_bytes);
+    w.d = p;
+    p += align256((size_t)I.P * I.n_out * I.real_bytes);
+    w.vc = p;
+    p += align256(2 * (size_t)I.Nf * I.real_bytes);
+    w.xc = reinterpret_cast<double *>(p);
+    p += align256(3 * (size_t)I.Nc * sizeof(double));
+    w.bc = reinterpret_cast<double *>(p);
+    return w;
+}
+
+// Element matrices of a fine hx x hy cell from 1D linear factors, the 2x2
+// Gauss tables for the convection term, and the LPS patch matrix.
+void fem_coefficients(const dnnmg_mesh_desc &d, FemCoef<double> *out) {
+    FemCoef<double> &f = *out;
+    memset(&f, 0, sizeof f);
+    const double hx = d.lx / (d.nxc << d.K), hy = d.ly / (d.nyc << d.K);
+    double M1x[2][2], M1y[2][2], K1x[2][2], K1y[2][2], C1x[2][2], C1y[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            M1x[a][b] = hx / 6.0 * (a == b ? 2.0 : 1.0);
+            M1y[a][b] = hy / 6.0 * (a == b ? 2.0 : 1.0);
+            K1x[a][b] = (a == b ? 1.0 : -1.0) / hx;
+            K1y[a][b] = (a == b ? 1.0 : -1.0) / hy;
+            C1x[a][b] = a == 0 ? -0.5 : 0.5;   // int l_b l_a' over the 1D cell
+            C1y[a][b] = a == 0 ? -0.5 : 0.5;
+        }
+    double Kd[4][4];
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            const int ax = a & 1, ay = a >> 1, bx = b & 1, by = b >> 1;
+            const double M = M1x[ax][bx] * M1y[ay][by];
+            Kd[a][b] = K1x[ax][bx] * M1y[ay][by] + M1x[ax][bx] * K1y[ay][by];
+            f.Av[a][b] = M / d.k + 0.5 * d.nu * Kd[a][b];
+            f.Bv[a][b] = M / d.k - 0.5 * d.nu * Kd[a][b];
+            f.Gx[a][b] = C1x[ax][bx] * M1y[ay][by];
+            f.Gy[a][b] = M1x[ax][bx] * C1y[ay][by];
+        }
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            f.Dx[a][b] = f.Gx[b][a];
+            f.Dy[a][b] = f.Gy[b][a];
+        }
+    const double gp[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+    for (int qy = 0; qy < 2; ++qy)
+        for (int qx = 0; qx < 2; ++qx) {
+            const int q = 2 * qy + qx;
+            const double xi = gp[qx], eta = gp[qy];
+            const double lx[2] = {1 - xi, xi}, ly[2] = {1 - eta, eta}, dl[2] = {-1.0, 1.0};
+            for (int a = 0; a < 4; ++a) {
+                const int ax = a & 1, ay = a >> 1;
+                f.qphi[q][a] = lx[ax] * ly[ay];
+                f.qdx[q][a] = dl[ax] * ly[ay] / hx;
+                f.qdy[q][a] = lx[ax] * dl[ay] / hy;
+            }
+        }
+    f.qw = hx * hy / 4.0;
+    // LPS on a 2x2-cell patch: S9 = alpha (I - Pi)^T L (I - Pi)
+    double L[9][9] = {}, Pi[9][9] = {}, Q[9][9], T1[9][9];
+    for (int cb = 0; cb < 2; ++cb)
+        for (int ca = 0; ca < 2; ++ca) {
+            const int idx[4] = {3 * cb + ca, 3 * cb + ca + 1, 3 * (cb + 1) + ca, 3 * (cb + 1) + ca + 1};
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) L[idx[a]][idx[b]] += Kd[a][b];
+        }
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const double X = a / 2.0, Y = b / 2.0;
+            Pi[3 * b + a][0] += (1 - X) * (1 - Y);
+            Pi[3 * b + a][2] += X * (1 - Y);
+            Pi[3 * b + a][6] += (1 - X) * Y;
+            Pi[3 * b + a][8] += X * Y;
+        }
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) Q[i][j] = (i == j ? 1.0 : 0.0) - Pi[i][j];
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            double s = 0;
+            for (int k = 0; k < 9; ++k) s += L[i][k] * Q[k][j];
+            T1[i][j] = s;
+        }
+    const double alpha = d.alpha0 * (hx * hx + hy * hy) / d.nu;
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            double s = 0;
+            for (int k = 0; k < 9; ++k) s += Q[k][i] * T1[k][j];
+            f.S9[i][j] = alpha * s;
+        }
+    // patch geometry from its corners: edges, aspect ratios, angles
+    const double w = d.s * (d.lx / d.nxc), h = d.s * (d.ly / d.nyc);
+    const double cx[4] = {0, w, w, 0}, cy[4] = {0, 0, h, h};   // SW, SE, NE, NW
+    double len[4];
+    for (int e = 0; e < 4; ++e) len[e] = std::hypot(cx[(e + 1) % 4] - cx[e], cy[(e + 1) % 4] - cy[e]);
+    f.geo[0] = len[0];
+    f.geo[1] = len[1];
+    f.geo[2] = len[2];
+    f.geo[3] = len[3];
+    f.geo[4] = len[0] / len[1];
+    f.geo[5] = len[2] / len[3];
+    f.geo[6] = len[0] / len[2];
+    f.geo[7] = len[3] / len[1];
+    for (int c = 0; c < 4; ++c) {
+        const int n = (c + 1) % 4, p = (c + 3) % 4;
+        const double ax = cx[n] - cx[c], ay = cy[n] - cy[c], bx = cx[p] - cx[c], by = cy[p] - cy[c];
+        f.geo[8 + c] = std::acos((ax * bx + ay * by) / (std::hypot(ax, ay) * std::hypot(bx, by)));
+    }
+    f.q_over_nu = d.s * std::fmax(d.lx / d.nxc, d.ly / d.nyc) / d.nu;
+    (void)kPi;
+}
+
+void to_float(const FemCoef<double> &a, FemCoef<float> *b) {
+    const double *src = reinterpret_cast<const double *>(&a);
+    float *dst = reinterpret_cast<float *>(b);
+    static_assert(sizeof(FemCoef<double>) == 2 * sizeof(FemCoef<float>), "layout");
+    for (size_t i = 0; i < sizeof(FemCoef<float>) / sizeof(float); ++i) dst[i] = (float)src[i];
+}
+
+int check_device(int dev) {
+    int cur = -1;
+    DNNMG_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != dev)
+        return fail(DNNMG_EINVAL, "handle belongs to device %d but device %d is current", dev, cur);
+    return DNNMG_OK;
+}
+
+int check_mesh(dnnmg_mesh_t m) {
+    if (!m) return fail(DNNMG_EINVAL, "mesh handle is NULL");
+    return check_device(m->device);
+}
+
+}  // namespace
+}  // namespace dnnmg
+
+using namespace dnnmg;
+
+extern "C" {
+
+const char *dnnmg_last_error(void) { return g_error.c_str(); }
+
+int dnnmg_mesh_query(const dnnmg_mesh_desc *desc, dnnmg_mesh_info *info) {
+    clear_error();
+    if (int e = validate_desc(desc)) return e;
+    if (!info) return fail(DNNMG_EINVAL, "info is NULL");
+    std::vector<uint8_t> solid = solid_mask(*desc);
+    int n_solid = 0;
+    for (uint8_t v : solid) n_solid += v;
+    const int P = patch_numbering(*desc, solid, nullptr, nullptr);
+    fill_info(*desc, P, n_solid, info);
+    return DNNMG_OK;
+}
+
+int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out) {
+    clear_error();
+    if (int e = validate_desc(desc)) return e;
+    if (!out) return fail(DNNMG_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::vector<uint8_t> solid = solid_mask(*desc);
+    std::vector<int> pid, pcell;
+    int n_solid = 0;
+    for (uint8_t v : solid) n_solid += v;
+    const int P = patch_numbering(*desc, solid, &pid, &pcell);
+    dnnmg_mesh_s *m = new (std::nothrow) dnnmg_mesh_s();
+    if (!m) return fail(DNNMG_ENOMEM, "host allocation failed");
+    m->desc = *desc;
+    m->desc.solid = nullptr;
+    fill_info(*desc, P, n_solid, &m->info);
+    if (cudaGetDevice(&m->device) != cudaSuccess) {
+        delete m;
+        return fail(DNNMG_ECUDA, "cudaGetDevice failed");
+    }
+    m->d_solid = nullptr;
+    m->d_patch_id = nullptr;
+    m->d_patch_cell = nullptr;
+    const size_t ns = solid.size(), np = pid.size(), nc = pcell.size();
+    if (cudaMalloc(&m->d_solid, ns) != cudaSuccess ||
+        cudaMalloc(&m->d_patch_id, np * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&m->d_patch_cell, (nc ? nc : 1) * sizeof(int)) != cudaSuccess) {
+        cudaFree(m->d_solid);
+        cudaFree(m->d_patch_id);
+        cudaFree(m->d_patch_cell);
+        delete m;
+        cudaGetLastError();
+        return fail(DNNMG_ENOMEM, "device allocation of the mesh maps failed");
+    }
+    if (cudaMemcpy(m->d_solid, solid.data(), ns, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->d_patch_id, pid.data(), np * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (nc && cudaMemcpy(m->d_patch_cell, pcell.data(), nc * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)) {
+        cudaFree(m->d_solid);
+        cudaFree(m->d_patch_id);
+        cudaFree(m->d_patch_cell);
+        delete m;
+        return fail(DNNMG_ECUDA, "upload of the mesh maps failed");
+    }
+    MeshGeom &g = m->g;
+    const dnnmg_mesh_info &I = m->info;
+    g.nxc = I.nxc; g.nyc = I.nyc; g.K = I.K; g.r = 1 << I.K; g.s = I.s; g.S = I.s << I.K;
+    g.nxf = I.nxf; g.nyf = I.nyf; g.npx = I.npx; g.npy = I.npy; g.P = P;
+    g.nf = I.nf; g.nc = I.nc; g.n_in = I.n_in; g.n_out = I.n_out; g.ldx = I.ldx;
+    g.lx = desc->lx; g.ly = desc->ly;
+    g.hxc = desc->lx / I.nxc; g.hyc = desc->ly / I.nyc;
+    g.hxf = desc->lx / I.nxf; g.hyf = desc->ly / I.nyf;
+    g.nu = desc->nu; g.k = desc->k; g.u_max = desc->u_max; g.ramp = desc->ramp;
+    g.solid = m->d_solid;
+    g.patch_id = m->d_patch_id;
+    g.patch_cell = m->d_patch_cell;
+    fem_coefficients(*desc, &m->fem64);
+    to_float(m->fem64, &m->fem32);
+    *out = m;
+    return DNNMG_OK;
+}
+
+int dnnmg_mesh_destroy(dnnmg_mesh_t mesh) {
+    clear_error();
+    if (!mesh) return DNNMG_OK;
+    cudaFree(mesh->d_solid);
+    cudaFree(mesh->d_patch_id);
+    cudaFree(mesh->d_patch_cell);
+    delete mesh;
+    return DNNMG_OK;
+}
+
+int dnnmg_mesh_get_info(dnnmg_mesh_t mesh, dnnmg_mesh_info *info) {
+    clear_error();
+    if (!mesh || !info) return fail(DNNMG_EINVAL, "NULL argument");
+    *info = mesh->info;
+    return DNNMG_OK;
+}
+
+int dnnmg_mesh_maps(dnnmg_mesh_t mesh, int *patch_cell, unsigned char *node_flags,
+                    unsigned char *node_mult, cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if (patch_cell && mesh->info.P)
+        DNNMG_CUDA_TRY(cudaMemcpyAsync(patch_cell, mesh->d_patch_cell, sizeof(int) * mesh->info.P,
+                                       cudaMemcpyDeviceToDevice, stream));
+    if (node_flags || node_mult) {
+        DNNMG_CUDA_TRY(launch_mesh_maps(mesh->g, node_flags, node_mult, stream));
+    }
+    return DNNMG_OK;
+}
+
+int dnnmg_net_create(int n_in, int hidden, int n_out, const double *Wx, const double *Uh,
+                     const double *Wfc, int precision, dnnmg_net_t *out) {
+    clear_error();
+    if (!out || !Wx || !Uh || !Wfc) return fail(DNNMG_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n_in <= 0 || hidden <= 0 || n_out <= 0 || n_in > 4096 || hidden > 1024 || n_out > 4096)
+        return fail(DNNMG_EINVAL, "network sizes n_in=%d H=%d n_out=%d out of range", n_in, hidden, n_out);
+    if (precision < DNNMG_F64 || precision > DNNMG_BF16NET)
+        return fail(DNNMG_EINVAL, "unknown precision %d", precision);
+    dnnmg_net_s *n = new (std::nothrow) dnnmg_net_s();
+    if (!n) return fail(DNNMG_ENOMEM, "host allocation failed");
+    n->n_in = n_in;
+    n->ldx = round_up(n_in, 16);
+    n->H = hidden;
+    n->n_out = n_out;
+    n->precision = precision;
+    n->WxT = n->UhT = n->WfcT = n->tc_weights = nullptr;
+    n->tc_bytes = 0;
+    cudaGetDevice(&n->device);
+    const int G = 3 * hidden;
+    std::vector<double> wx((size_t)n->ldx * G, 0.0), uh((size_t)hidden * G), wfc((size_t)hidden * n_out);
+    for (int j = 0; j < G; ++j)
+        for (int k = 0; k < n_in; ++k) wx[(size_t)k * G + j] = Wx[(size_t)j * n_in + k];
+    for (int j = 0; j < G; ++j)
+        for (int k = 0; k < hidden; ++k) uh[(size_t)k * G + j] = Uh[(size_t)j * hidden + k];
+    for (int o = 0; o < n_out; ++o)
+        for (int k = 0; k < hidden; ++k) wfc[(size_t)k * n_out + o] = Wfc[(size_t)o * hidden + k];
+    auto upload = [&](const std::vector<double> &src, void **dst) -> int {
+        const size_t cnt = src.size();
+        if (precision == DNNMG_F64) {
+            if (cudaMalloc(dst, cnt * 8) != cudaSuccess) return DNNMG_ENOMEM;
+            return cudaMemcpy(*dst, src.data(), cnt * 8, cudaMemcpyHostToDevice) == cudaSuccess ? 0 : DNNMG_ECUDA;
+        }
+        if (precision == DNNMG_F32) {
+            std::vector<float> t(src.begin(), src.end());
+            if (cudaMalloc(dst, cnt * 4) != cudaSuccess) return DNNMG_ENOMEM;
+            return cudaMemcpy(*dst, t.data(), cnt * 4, cudaMemcpyHostToDevice) == cudaSuccess ? 0 : DNNMG_ECUDA;
+        }
+        std::vector<__nv_bfloat16> t(cnt);
+        for (size_t i = 0; i < cnt; ++i) t[i] = __float2bfloat16_rn((float)src[i]);
+        if (cudaMalloc(dst, cnt * 2) != cudaSuccess) return DNNMG_ENOMEM;
+        return cudaMemcpy(*dst, t.data(), cnt * 2, cudaMemcpyHostToDevice) == cudaSuccess ? 0 : DNNMG_ECUDA;
+    };
+    int e = upload(wx, &n->WxT);
+    if (!e) e = upload(uh, &n->UhT);
+    if (!e) e = upload(wfc, &n->WfcT);
+    if (e) {
+        cudaFree(n->WxT);
+        cudaFree(n->UhT);
+        cudaFree(n->WfcT);
+        delete n;
+        cudaGetLastError();
+        return fail(e, "uploading the network weights failed");
+    }
+    *out = n;
+    return DNNMG_OK;
+}
+
+int dnnmg_net_destroy(dnnmg_net_t net) {
+    clear_error();
+    if (!net) return DNNMG_OK;
+    cudaFree(net->WxT);
+    cudaFree(net->UhT);
+    cudaFree(net->WfcT);
+    cudaFree(net->tc_weights);
+    delete net;
+    return DNNMG_OK;
+}
+
+int dnnmg_prolongate(dnnmg_mesh_t mesh, const double *xc, void *xf, double t, cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if (!xc || !xf) return fail(DNNMG_EINVAL, "NULL array");
+    DNNMG_CUDA_TRY(launch_prolongate(mesh->g, mesh->info.precision, xc, xf, t, stream));
+    return DNNMG_OK;
+}
+
+int dnnmg_patch_features(dnnmg_mesh_t mesh, const void *xf, const void *bf, void *rf, void *X,
+                         cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if (!xf || !bf || (!X && mesh->info.P)) return fail(DNNMG_EINVAL, "NULL array");
+    DNNMG_CUDA_TRY(launch_residual_features(mesh->g, mesh->info.precision, mesh->fem64, mesh->fem32,
+                                            xf, bf, rf, X, stream));
+    return DNNMG_OK;
+}
+
+int dnnmg_gru_step(dnnmg_net_t net, const void *X, void *h, void *d, int P, cudaStream_t stream) {
+    clear_error();
+    if (!net) return fail(DNNMG_EINVAL, "net handle is NULL");
+    if (int e = check_device(net->device)) return e;
+    if (P < 0) return fail(DNNMG_EINVAL, "P=%d < 0", P);
+    if (P == 0) return DNNMG_OK;
+    if (!X || !h || !d) return fail(DNNMG_EINVAL, "NULL array");
+    DNNMG_CUDA_TRY(launch_gru(*net, X, h, d, P, stream));
+    return DNNMG_OK;
+}
+
+int dnnmg_scatter_avg(dnnmg_mesh_t mesh, const void *d, const void *xf, void *vcorr,
+                      cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if ((!d && mesh->info.P) || !xf || !vcorr) return fail(DNNMG_EINVAL, "NULL array");
+    DNNMG_CUDA_TRY(launch_scatter_avg(mesh->g, mesh->info.precision, d, xf, vcorr, stream));
+    return DNNMG_OK;
+}
+
+int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *bc,
+                       cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if (!vcorr || !bf || !bc) return fail(DNNMG_EINVAL, "NULL array");
+    if (vcorr == bf) return fail(DNNMG_EINVAL, "vcorr and bf must not alias");
+    DNNMG_CUDA_TRY(launch_rhs(mesh->g, mesh->info.precision, mesh->fem64, mesh->fem32, vcorr, bf, stream));
+    DNNMG_CUDA_TRY(launch_restrict(mesh->g, mesh->info.precision, bf, bc, stream));
+    return DNNMG_OK;
+}
+
+static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, void *workspace,
+                       size_t workspace_bytes) {
+    if (int e = check_mesh(mesh)) return e;
+    if (!net) return fail(DNNMG_EINVAL, "net handle is NULL");
+    const dnnmg_mesh_info &I = mesh->info;
+    if (net->n_in != I.n_in || net->n_out != I.n_out)
+        return fail(DNNMG_EINVAL, "network is %d -> %d but the mesh needs %d -> %d", net->n_in,
+                    net->n_out, I.n_in, I.n_out);
+    if (net->precision != I.precision)
+        return fail(DNNMG_EINVAL, "network precision %d differs from mesh precision %d",
+                    net->precision, I.precision);
+    if (!h || !bf || !workspace) return fail(DNNMG_EINVAL, "NULL array");
+    if (workspace_bytes < I.workspace_bytes)
+        return fail(DNNMG_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, I.workspace_bytes);
+    if (reinterpret_cast<uintptr_t>(workspace) % 256)
+        return fail(DNNMG_EINVAL, "workspace must be 256-byte aligned");
+    return DNNMG_OK;
+}
+
+static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf,
+                     double *bc, const Workspace &w, double t, cudaStream_t s) {
+    const int prec = mesh->info.precision;
+    const MeshGeom &g = mesh->g;
+    DNNMG_CUDA_TRY(launch_prolongate(g, prec, xc, w.xf, t, s));
+    DNNMG_CUDA_TRY(launch_residual_features(g, prec, mesh->fem64, mesh->fem32, w.xf, bf, nullptr, w.X, s));
+    if (mesh->info.P) DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
+    DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, w.xf, w.vc, s));
+    DNNMG_CUDA_TRY(launch_rhs(g, prec, mesh->fem64, mesh->fem32, w.vc, bf, s));
+    DNNMG_CUDA_TRY(launch_restrict(g, prec, bf, bc, s));
+    return DNNMG_OK;
+}
+
+int dnnmg_step(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
+               void *workspace, size_t workspace_bytes, double t, cudaStream_t stream) {
+    clear_error();
+    if (int e = step_checks(mesh, net, h, bf, workspace, workspace_bytes)) return e;
+    if (!xc || !bc) return fail(DNNMG_EINVAL, "NULL array");
+    return step_body(mesh, net, xc, h, bf, bc, carve(mesh->info, workspace), t, stream);
+}
+
+int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, void *h, void *bf,
+                    double *bc_host, void *workspace, size_t workspace_bytes, double t,
+                    cudaStream_t stream) {
+    clear_error();
+    if (int e = step_checks(mesh, net, h, bf, workspace, workspace_bytes)) return e;
+    if (!xc_host || !bc_host) return fail(DNNMG_EINVAL, "NULL array");
+    const Workspace w = carve(mesh->info, workspace);
+    const size_t nbytes = 3 * (size_t)mesh->info.Nc * sizeof(double);
+    DNNMG_CUDA_TRY(cudaMemcpyAsync(w.xc, xc_host, nbytes, cudaMemcpyHostToDevice, stream));
+    if (int e = step_body(mesh, net, w.xc, h, bf, w.bc, w, t, stream)) return e;
+    DNNMG_CUDA_TRY(cudaMemcpyAsync(bc_host, w.bc, nbytes, cudaMemcpyDeviceToHost, stream));
+    return DNNMG_OK;
+}
+
+int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net) {
+    if (!mesh || !net) return -1;
+    return 5 + (mesh->info.P ? gru_launch_count(*net) : 0);
+}
+
+}  // extern "C"
+
+namespace dnnmg {
+cudaError_t launch_gru(const Net &net, const void *X, void *h, void *d, int P, cudaStream_t st) {
+    return launch_gru_cuda_core(net, X, h, d, P, st);
+}
+int gru_launch_count(const Net &) { return 1; }
+}  // namespace dnnmg

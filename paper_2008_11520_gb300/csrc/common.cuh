@@ -1,0 +1,112 @@
+// Internal declarations of libdnnmg: mesh/net handles, per-mesh constants and
+// kernel launchers.  The public boundary is include/dnnmg.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "dnnmg.h"
+
+namespace dnnmg {
+
+// ---------------------------------------------------------------- errors
+int fail(int code, const char *fmt, ...);
+void clear_error();
+
+#define DNNMG_CUDA_TRY(expr)                                                               \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ::dnnmg::fail(DNNMG_ECUDA, "%s failed: %s (%s:%d)", #expr,              \
+                                 cudaGetErrorString(e_), __FILE__, __LINE__);               \
+    } while (0)
+
+// Launch check: reports configuration errors of the launch just enqueued.
+#define DNNMG_LAUNCH_CHECK(name)                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                                \
+        if (e_ != cudaSuccess)                                                              \
+            return ::dnnmg::fail(DNNMG_ECUDA, "launch of %s failed: %s", name,              \
+                                 cudaGetErrorString(e_));                                   \
+    } while (0)
+
+// ---------------------------------------------------------------- geometry
+// Plain-value view of a mesh handed to kernels.
+struct MeshGeom {
+    int nxc, nyc, K, r, s, S;     // r = 2^K fine cells per coarse cell, S = s r per patch
+    int nxf, nyf, npx, npy, P;
+    int nf, nc, n_in, n_out, ldx;
+    double lx, ly, hxc, hyc, hxf, hyf;
+    double nu, k, u_max;
+    int ramp;
+    const uint8_t *solid;         // device [nyc][nxc], 1 = solid coarse cell
+    const int *patch_id;          // device [npy][npx], fluid patch number or -1
+    const int *patch_cell;        // device [P], pj npx + pi
+};
+
+// Element constants of one fine cell (local nodes SW, SE, NW, NE) and of one
+// 2x2-cell LPS patch, in the arithmetic type of the fine fields.
+template <typename T>
+struct FemCoef {
+    T Av[4][4];     // 1/k M + nu/2 Kd : linear velocity operator (Eq. nonlinearshort)
+    T Bv[4][4];     // 1/k M - nu/2 Kd : right-hand side (Eq. 4cranknicholson3)
+    T Gx[4][4];     // int phi_b d_x phi_a : pressure term of velocity row a
+    T Gy[4][4];     // int phi_b d_y phi_a
+    T Dx[4][4];     // int d_x phi_b phi_a : divergence term of pressure row a
+    T Dy[4][4];
+    T S9[9][9];     // LPS: alpha (I - Pi)^T L (I - Pi) on a 2x2-cell patch
+    T qphi[4][4];   // [gauss point][node] shape values (2x2 Gauss)
+    T qdx[4][4];    // x derivatives at the Gauss points
+    T qdy[4][4];
+    T qw;           // Gauss weight hx hy / 4
+    T geo[12];      // patch geometry features
+    T q_over_nu;    // Peclet scale: longest patch edge / nu
+};
+
+struct Mesh {
+    dnnmg_mesh_desc desc;
+    dnnmg_mesh_info info;
+    MeshGeom g;
+    FemCoef<double> fem64;
+    FemCoef<float> fem32;
+    int device;
+    uint8_t *d_solid;
+    int *d_patch_id;
+    int *d_patch_cell;
+};
+
+struct Net {
+    int n_in, ldx, H, n_out, precision;
+    int device;
+    // transposed weights for the CUDA-core kernel: WxT [ldx][3H], UhT [H][3H], WfcT [H][n_out]
+    void *WxT, *UhT, *WfcT;
+    // K-major bf16 operands for the tensor-core kernel (BF16NET only, may be null)
+    void *tc_weights;
+    size_t tc_bytes;
+};
+
+int round_up(int v, int m);
+size_t align256(size_t v);
+
+// ---------------------------------------------------------------- launchers
+// All return cudaSuccess or the launch error; `prec` is DNNMG_F64/F32/BF16NET.
+cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, void *xf,
+                              double t, cudaStream_t st);
+cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<double> &f64,
+                                     const FemCoef<float> &f32, const void *xf, const void *bf,
+                                     void *rf, void *X, cudaStream_t st);
+cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf,
+                               void *vcorr, cudaStream_t st);
+cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
+                       const FemCoef<float> &f32, const void *vcorr, void *bf, cudaStream_t st);
+cudaError_t launch_restrict(const MeshGeom &g, int prec, const void *bf, double *bc,
+                            cudaStream_t st);
+cudaError_t launch_mesh_maps(const MeshGeom &g, unsigned char *flags, unsigned char *mult,
+                             cudaStream_t st);
+cudaError_t launch_gru(const Net &net, const void *X, void *h, void *d, int P, cudaStream_t st);
+int gru_launch_count(const Net &net);
+
+}  // namespace dnnmg

@@ -1,0 +1,618 @@
+// Stencil, gather and scatter passes of the DNN-MG correction step:
+//   S1 prolongation, S2+S3 residual and patch features, S5 averaging,
+//   S6 right-hand side, S7 restriction, plus the node index maps.
+//
+// Fine node fields are SoA planes [comp][Nf], x fastest.  S2 and S6 are
+// tiled: one CTA owns a 32 x 16 block of fine cells, stages the node values
+// it needs (plus a halo) in shared memory, computes every cell's element
+// contributions once (cell-centric), and then sums them per node (a pull,
+// so there are no atomics and results are bitwise repeatable).
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace dnnmg {
+namespace {
+
+constexpr int TXC = 32;            // fine cells per tile in x
+constexpr int TYC = 16;            // fine cells per tile in y
+constexpr int NXN = TXC + 1;       // tile nodes in x
+constexpr int NYN = TYC + 1;
+constexpr int NTHREADS = 256;
+
+template <typename T> __device__ __forceinline__ T to_real(T v) { return v; }
+template <typename TX, typename T> __device__ __forceinline__ TX store_as(T v) { return (TX)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, float>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ int cell_code(const MeshGeom &g, int I, int J) {
+    // 0: no cell (outside the domain), 1: fluid, 2: solid
+    if (I < 0 || J < 0 || I >= g.nxf || J >= g.nyf) return 0;
+    return g.solid[(size_t)(J >> g.K) * g.nxc + (I >> g.K)] ? 2 : 1;
+}
+
+struct NodeClass {
+    bool dirichlet, inflow, p_active;
+};
+
+// Sec. 6.1 boundary classes of fine node (I, J) from its four cells.
+__device__ __forceinline__ NodeClass classify(int c00, int c10, int c01, int c11, int I, int J,
+                                              int nyf) {
+    bool ts = (c00 == 2) | (c10 == 2) | (c01 == 2) | (c11 == 2);
+    bool tf = (c00 == 1) | (c10 == 1) | (c01 == 1) | (c11 == 1);
+    bool wall = (J == 0) | (J == nyf);
+    NodeClass n;
+    n.dirichlet = wall | (I == 0) | ts;
+    n.inflow = (I == 0) & !wall & !ts;
+    n.p_active = tf;
+    return n;
+}
+
+__device__ __forceinline__ NodeClass classify_global(const MeshGeom &g, int I, int J) {
+    return classify(cell_code(g, I - 1, J - 1), cell_code(g, I, J - 1), cell_code(g, I - 1, J),
+                    cell_code(g, I, J), I, J, g.nyf);
+}
+
+// ------------------------------------------------------------------ S1
+// One thread per fine node; bilinear weights a/r are exact binary fractions.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, double inflow_scale) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y;
+    if (I > g.nxf) return;
+    const int ci = min(I >> g.K, g.nxc - 1), cj = min(J >> g.K, g.nyc - 1);
+    const double a = (double)(I - (ci << g.K)) / g.r;
+    const double b = (double)(J - (cj << g.K)) / g.r;
+    const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
+    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
+    const size_t c00 = (size_t)cj * nc1 + ci;
+    double val[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double *f = xc + c * Nc;
+        val[c] = (1 - a) * (1 - b) * __ldg(f + c00) + a * (1 - b) * __ldg(f + c00 + 1) +
+                 (1 - a) * b * __ldg(f + c00 + nc1) + a * b * __ldg(f + c00 + nc1 + 1);
+    }
+    NodeClass nc = classify_global(g, I, J);
+    if (nc.dirichlet) {
+        const double y = J * g.hyf;
+        val[0] = nc.inflow ? g.u_max * 4.0 * y * (g.ly - y) / (g.ly * g.ly) * inflow_scale : 0.0;
+        val[1] = 0.0;
+    }
+    const size_t node = (size_t)J * nxn + I;
+    xf[node] = (T)val[0];
+    xf[Nf + node] = (T)val[1];
+    xf[2 * Nf + node] = (T)val[2];
+}
+
+// ------------------------------------------------------------------ S2 + S3
+// Shared-memory layout of the residual/feature tile (element counts).
+struct ResLayout {
+    static constexpr int HX = NXN + 4, HY = NYN + 4;           // nodes with 2-node halo
+    static constexpr int CX = TXC + 2, CY = TYC + 2;           // cells with 1-cell halo
+    static constexpr int NCELL = CX * CY;
+    static constexpr int LX = TXC / 2 + 2, LY = TYC / 2 + 2;   // LPS patches touching the tile
+    static constexpr int NLPS = LX * LY;
+    static constexpr int FX = TXC + 4, FY = TYC + 4;           // cell codes with 2-cell halo
+    static constexpr int XS = 3 * HY * HX;
+    static constexpr int BS = 2 * NYN * NXN;
+    static constexpr int CC = 12 * NCELL;
+    static constexpr int LC = 9 * NLPS;
+    static constexpr int RS = 3 * NYN * NXN;
+    template <typename T> static constexpr size_t bytes() {
+        return sizeof(T) * (XS + BS + CC + LC + RS) + FX * FY;
+    }
+};
+
+template <typename T, typename TX>
+__global__ void __launch_bounds__(NTHREADS)
+k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T *__restrict__ bf,
+                    T *__restrict__ rf, TX *__restrict__ X) {
+    using L = ResLayout;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);   // [3][HY][HX]   u, v, p
+    T *bs = xs + L::XS;                        // [2][NYN][NXN] b_u, b_v
+    T *cc = bs + L::BS;                        // [12][NCELL]   cell contributions
+    T *lc = cc + L::CC;                        // [9][NLPS]     LPS contributions
+    T *rs = lc + L::LC;                        // [3][NYN][NXN] residual
+    unsigned char *cf = reinterpret_cast<unsigned char *>(rs + L::RS);  // [FY][FX]
+
+    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
+
+    for (int idx = threadIdx.x; idx < L::XS; idx += blockDim.x) {
+        const int c = idx / (L::HY * L::HX), rem = idx - c * (L::HY * L::HX);
+        const int jj = rem / L::HX, ii = rem - jj * L::HX;
+        const int I = I0 - 2 + ii, J = J0 - 2 + jj;
+        T v = T(0);
+        if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf) v = xf[c * Nf + (size_t)J * nxn + I];
+        xs[idx] = v;
+    }
+    for (int idx = threadIdx.x; idx < L::BS; idx += blockDim.x) {
+        const int c = idx / (NYN * NXN), rem = idx - c * (NYN * NXN);
+        const int jj = rem / NXN, ii = rem - jj * NXN;
+        const int I = I0 + ii, J = J0 + jj;
+        T v = T(0);
+        if (I <= g.nxf && J <= g.nyf) v = bf[c * Nf + (size_t)J * nxn + I];
+        bs[idx] = v;
+    }
+    for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
+        const int jj = idx / L::FX, ii = idx - jj * L::FX;
+        cf[idx] = (unsigned char)cell_code(g, I0 - 2 + ii, J0 - 2 + jj);
+    }
+    __syncthreads();
+
+    // Phase A: element contributions of every fluid cell (cells -1..TXC in x).
+    for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
+        const int ci = cid % L::CX - 1, cj = cid / L::CX - 1;
+        T out[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k] = T(0);
+        if (cf[(cj + 2) * L::FX + ci + 2] == 1) {
+            const int base = (cj + 2) * L::HX + ci + 2;
+            const int off[4] = {0, 1, L::HX, L::HX + 1};
+            T u[4], v[4], p[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                u[b] = xs[base + off[b]];
+                v[b] = xs[L::HY * L::HX + base + off[b]];
+                p[b] = xs[2 * L::HY * L::HX + base + off[b]];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                T au = T(0), av = T(0), ap = T(0);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    au += fc.Av[a][b] * u[b] - fc.Gx[a][b] * p[b];
+                    av += fc.Av[a][b] * v[b] - fc.Gy[a][b] * p[b];
+                    ap += fc.Dx[a][b] * u[b] + fc.Dy[a][b] * v[b];
+                }
+                out[a] = au;
+                out[4 + a] = av;
+                out[8 + a] = ap;
+            }
+            // convection 1/2 (v.grad v, phi_a) by 2x2 Gauss
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                T uq = T(0), vq = T(0), ux = T(0), uy = T(0), vx = T(0), vy = T(0);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    uq += fc.qphi[q][b] * u[b];
+                    vq += fc.qphi[q][b] * v[b];
+                    ux += fc.qdx[q][b] * u[b];
+                    uy += fc.qdy[q][b] * u[b];
+                    vx += fc.qdx[q][b] * v[b];
+                    vy += fc.qdy[q][b] * v[b];
+                }
+                const T cu = T(0.5) * fc.qw * (uq * ux + vq * uy);
+                const T cv = T(0.5) * fc.qw * (uq * vx + vq * vy);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    out[a] += cu * fc.qphi[q][a];
+                    out[4 + a] += cv * fc.qphi[q][a];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) cc[k * L::NCELL + cid] = out[k];
+    }
+    // Phase A': LPS contributions of every 2x2-cell patch touching the tile.
+    for (int lid = threadIdx.x; lid < L::NLPS; lid += blockDim.x) {
+        const int m = lid % L::LX - 1, n = lid / L::LX - 1;
+        T out[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[i] = T(0);
+        if (cf[(2 * n + 2) * L::FX + 2 * m + 2] == 1) {
+            T p9[9];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    p9[3 * b + a] = xs[2 * L::HY * L::HX + (2 * n + b + 2) * L::HX + 2 * m + a + 2];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                T acc = T(0);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc += fc.S9[i][k] * p9[k];
+                out[i] = acc;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lc[i * L::NLPS + lid] = out[i];
+    }
+    __syncthreads();
+
+    // Phase B: residual per tile node (pull from the 4 cells and the LPS patches).
+    for (int nid = threadIdx.x; nid < NXN * NYN; nid += blockDim.x) {
+        const int jj = nid / NXN, ii = nid - jj * NXN;
+        const int I = I0 + ii, J = J0 + jj;
+        T ru = T(0), rv = T(0), rp = T(0);
+        if (I <= g.nxf && J <= g.nyf) {
+            T Au = T(0), Av = T(0), Ap = T(0);
+            // cell (ci, cj) relative -> index (cj + 1) * CX + ci + 1; node is corner a of it
+            const int cells[4] = {jj * L::CX + ii, jj * L::CX + ii + 1, (jj + 1) * L::CX + ii,
+                                  (jj + 1) * L::CX + ii + 1};  // cells SW of node .. NE of node
+            const int corner[4] = {3, 2, 1, 0};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                Au += cc[corner[t] * L::NCELL + cells[t]];
+                Av += cc[(4 + corner[t]) * L::NCELL + cells[t]];
+                Ap += cc[(8 + corner[t]) * L::NCELL + cells[t]];
+            }
+            const int nmx = (ii & 1) ? 1 : 2, nmy = (jj & 1) ? 1 : 2;
+            for (int ty = 0; ty < nmy; ++ty) {
+                const int n = (jj & 1) ? (jj - 1) / 2 : jj / 2 - 1 + ty;
+                const int b = (jj & 1) ? 1 : (ty == 0 ? 2 : 0);
+                for (int tx = 0; tx < nmx; ++tx) {
+                    const int m = (ii & 1) ? (ii - 1) / 2 : ii / 2 - 1 + tx;
+                    const int a = (ii & 1) ? 1 : (tx == 0 ? 2 : 0);
+                    Ap += lc[(3 * b + a) * L::NLPS + (n + 1) * L::LX + m + 1];
+                }
+            }
+            const NodeClass nc = classify(cf[(jj + 1) * L::FX + ii + 1], cf[(jj + 1) * L::FX + ii + 2],
+                                          cf[(jj + 2) * L::FX + ii + 1], cf[(jj + 2) * L::FX + ii + 2],
+                                          I, J, g.nyf);
+            if (!nc.dirichlet) {
+                ru = bs[jj * NXN + ii] - Au;
+                rv = bs[NYN * NXN + jj * NXN + ii] - Av;
+            }
+            if (nc.p_active) rp = -Ap;
+            if (rf) {
+                const size_t node = (size_t)J * nxn + I;
+                rf[node] = ru;
+                rf[Nf + node] = rv;
+                rf[2 * Nf + node] = rp;
+            }
+        }
+        rs[nid] = ru;
+        rs[NYN * NXN + nid] = rv;
+        rs[2 * NYN * NXN + nid] = rp;
+    }
+    __syncthreads();
+
+    // Phase C: one feature row per fluid patch of the tile (Sec. 5.2 inputs).
+    const int S = g.S, S1 = S + 1, s1 = g.s + 1, nf = g.nf, nc = g.nc;
+    const int tpx = TXC / S, tpy = TYC / S;
+    const int pi0 = I0 / S, pj0 = J0 / S;
+    const int total = tpx * tpy * g.ldx;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int tp = e / g.ldx, c = e - tp * g.ldx;
+        const int lpy = tp / tpx, lpx = tp - lpy * tpx;
+        const int pi = pi0 + lpx, pj = pj0 + lpy;
+        if (pi >= g.npx || pj >= g.npy) continue;
+        const int id = g.patch_id[pj * g.npx + pi];
+        if (id < 0) continue;
+        T val = T(0);
+        if (c < 3 * nf) {
+            const int comp = c / nf, k = c - comp * nf;
+            const int b = k / S1, a = k - b * S1;
+            val = rs[comp * NYN * NXN + (lpy * S + b) * NXN + lpx * S + a];
+        } else if (c < 3 * nf + 3 * nc) {
+            const int k0 = c - 3 * nf, comp = k0 / nc, k = k0 - comp * nc;
+            const int b = k / s1, a = k - b * s1;
+            const int hi = lpx * S + a * g.r + 2, hj = lpy * S + b * g.r + 2;
+            const T u = xs[hj * L::HX + hi], v = xs[L::HY * L::HX + hj * L::HX + hi];
+            val = comp == 0 ? u : (comp == 1 ? v : fc.q_over_nu * sqrt(u * u + v * v));
+        } else if (c < g.n_in) {
+            val = fc.geo[c - 3 * nf - 3 * nc];
+        }
+        X[(size_t)id * g.ldx + c] = store_as<TX, T>(val);
+    }
+}
+
+// ------------------------------------------------------------------ S5
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, T *__restrict__ vc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y;
+    if (I > g.nxf) return;
+    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
+    const size_t node = (size_t)J * nxn + I;
+    T u = xf[node], v = xf[Nf + node];
+    const NodeClass nc = classify_global(g, I, J);
+    if (!nc.dirichlet) {
+        const int S = g.S;
+        int pis[2], pjs[2], npi = 0, npj = 0;
+        if (I % S == 0) {
+            if (I / S - 1 >= 0) pis[npi++] = I / S - 1;
+            if (I / S < g.npx) pis[npi++] = I / S;
+        } else {
+            pis[npi++] = I / S;
+        }
+        if (J % S == 0) {
+            if (J / S - 1 >= 0) pjs[npj++] = J / S - 1;
+            if (J / S < g.npy) pjs[npj++] = J / S;
+        } else {
+            pjs[npj++] = J / S;
+        }
+        T su = T(0), sv = T(0);
+        int cnt = 0;
+        for (int tj = 0; tj < npj; ++tj)
+            for (int ti = 0; ti < npi; ++ti) {
+                const int id = g.patch_id[pjs[tj] * g.npx + pis[ti]];
+                if (id < 0) continue;
+                const int k = (J - pjs[tj] * S) * (S + 1) + (I - pis[ti] * S);
+                su += d[(size_t)id * g.n_out + k];
+                sv += d[(size_t)id * g.n_out + g.nf + k];
+                ++cnt;
+            }
+        if (cnt) {
+            u += su / T(cnt);
+            v += sv / T(cnt);
+        }
+    }
+    vc[node] = u;
+    vc[Nf + node] = v;
+}
+
+// ------------------------------------------------------------------ S6
+struct RhsLayout {
+    static constexpr int HX = NXN + 2, HY = NYN + 2;   // nodes with 1-node halo
+    static constexpr int CX = TXC + 2, CY = TYC + 2;   // cells -1..TXC
+    static constexpr int NCELL = CX * CY;
+    static constexpr int VS = 2 * HY * HX;
+    static constexpr int CC = 8 * NCELL;
+    template <typename T> static constexpr size_t bytes() {
+        return sizeof(T) * (VS + CC) + NCELL;
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf) {
+    using L = RhsLayout;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *vs = reinterpret_cast<T *>(smem_raw);   // [2][HY][HX]
+    T *cc = vs + L::VS;                        // [8][NCELL]
+    unsigned char *cf = reinterpret_cast<unsigned char *>(cc + L::CC);  // [CY][CX]
+    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
+
+    for (int idx = threadIdx.x; idx < L::VS; idx += blockDim.x) {
+        const int c = idx / (L::HY * L::HX), rem = idx - c * (L::HY * L::HX);
+        const int jj = rem / L::HX, ii = rem - jj * L::HX;
+        const int I = I0 - 1 + ii, J = J0 - 1 + jj;
+        T v = T(0);
+        if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf) v = vcorr[c * Nf + (size_t)J * nxn + I];
+        vs[idx] = v;
+    }
+    for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
+        const int jj = idx / L::CX, ii = idx - jj * L::CX;
+        cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
+    }
+    __syncthreads();
+
+    for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
+        T out[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[k] = T(0);
+        if (cf[cid] == 1) {
+            const int ci = cid % L::CX, cj = cid / L::CX;   // halo-relative node of SW corner
+            const int base = cj * L::HX + ci;
+            const int off[4] = {0, 1, L::HX, L::HX + 1};
+            T u[4], v[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                u[b] = vs[base + off[b]];
+                v[b] = vs[L::HY * L::HX + base + off[b]];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                T bu = T(0), bv = T(0);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    bu += fc.Bv[a][b] * u[b];
+                    bv += fc.Bv[a][b] * v[b];
+                }
+                out[a] = bu;
+                out[4 + a] = bv;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                T uq = T(0), vq = T(0), ux = T(0), uy = T(0), vx = T(0), vy = T(0);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    uq += fc.qphi[q][b] * u[b];
+                    vq += fc.qphi[q][b] * v[b];
+                    ux += fc.qdx[q][b] * u[b];
+                    uy += fc.qdy[q][b] * u[b];
+                    vx += fc.qdx[q][b] * v[b];
+                    vy += fc.qdy[q][b] * v[b];
+                }
+                const T cu = T(0.5) * fc.qw * (uq * ux + vq * uy);
+                const T cv = T(0.5) * fc.qw * (uq * vx + vq * vy);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    out[a] -= cu * fc.qphi[q][a];
+                    out[4 + a] -= cv * fc.qphi[q][a];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cc[k * L::NCELL + cid] = out[k];
+    }
+    __syncthreads();
+
+    for (int nid = threadIdx.x; nid < NXN * NYN; nid += blockDim.x) {
+        const int jj = nid / NXN, ii = nid - jj * NXN;
+        const int I = I0 + ii, J = J0 + jj;
+        if (I > g.nxf || J > g.nyf) continue;
+        const int cells[4] = {jj * L::CX + ii, jj * L::CX + ii + 1, (jj + 1) * L::CX + ii,
+                              (jj + 1) * L::CX + ii + 1};
+        const int corner[4] = {3, 2, 1, 0};
+        T bu = T(0), bv = T(0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            bu += cc[corner[t] * L::NCELL + cells[t]];
+            bv += cc[(4 + corner[t]) * L::NCELL + cells[t]];
+        }
+        const NodeClass nc = classify(cf[cells[0]], cf[cells[1]], cf[cells[2]], cf[cells[3]], I, J,
+                                      g.nyf);
+        if (nc.dirichlet) bu = bv = T(0);
+        const size_t node = (size_t)J * nxn + I;
+        bf[node] = bu;
+        bf[Nf + node] = bv;
+    }
+}
+
+// ------------------------------------------------------------------ S7
+// One thread per coarse node: b_c(J) = sum_i hat_J(x_i) b_f(i) in double.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cj = blockIdx.y;
+    if (ci > g.nxc) return;
+    const int r = g.r;
+    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
+    const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
+    const int Ic = ci * r, Jc = cj * r;
+    double su = 0.0, sv = 0.0;
+    for (int dj = -(r - 1); dj <= r - 1; ++dj) {
+        const int J = Jc + dj;
+        if (J < 0 || J > g.nyf) continue;
+        double ru = 0.0, rv = 0.0;
+        for (int di = -(r - 1); di <= r - 1; ++di) {
+            const int I = Ic + di;
+            if (I < 0 || I > g.nxf) continue;
+            const double wx = (double)(r - abs(di)) / r;
+            ru += wx * (double)bf[(size_t)J * nxn + I];
+            rv += wx * (double)bf[Nf + (size_t)J * nxn + I];
+        }
+        const double wy = (double)(r - abs(dj)) / r;
+        su += wy * ru;
+        sv += wy * rv;
+    }
+    bool ts = false;
+    for (int dj = -1; dj <= 0; ++dj)
+        for (int di = -1; di <= 0; ++di) {
+            const int i = ci + di, j = cj + dj;
+            if (i >= 0 && j >= 0 && i < g.nxc && j < g.nyc && g.solid[(size_t)j * g.nxc + i]) ts = true;
+        }
+    if (ts || ci == 0 || cj == 0 || cj == g.nyc) su = sv = 0.0;
+    const size_t node = (size_t)cj * nc1 + ci;
+    bc[node] = su;
+    bc[Nc + node] = sv;
+    bc[2 * Nc + node] = 0.0;
+}
+
+// ------------------------------------------------------------------ maps
+__global__ void k_mesh_maps(MeshGeom g, unsigned char *flags, unsigned char *mult) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y;
+    if (I > g.nxf) return;
+    const size_t node = (size_t)J * ((size_t)g.nxf + 1) + I;
+    if (flags) {
+        const NodeClass nc = classify_global(g, I, J);
+        flags[node] = (unsigned char)((nc.dirichlet ? 1 : 0) | (nc.inflow ? 2 : 0) | (nc.p_active ? 4 : 0));
+    }
+    if (mult) {
+        const int S = g.S;
+        int cnt = 0;
+        for (int pj = (J - 1) / S; pj <= J / S; ++pj)
+            for (int pi = (I - 1) / S; pi <= I / S; ++pi) {
+                if (pi < 0 || pj < 0 || pi >= g.npx || pj >= g.npy) continue;
+                if (I < pi * S || I > (pi + 1) * S || J < pj * S || J > (pj + 1) * S) continue;
+                if (g.patch_id[pj * g.npx + pi] >= 0) ++cnt;
+            }
+        mult[node] = (unsigned char)cnt;
+    }
+}
+
+dim3 node_grid(const MeshGeom &g) {
+    return dim3((unsigned)((g.nxf + 1 + NTHREADS - 1) / NTHREADS), (unsigned)(g.nyf + 1));
+}
+dim3 tile_grid(const MeshGeom &g) {
+    return dim3((unsigned)((g.nxf + TXC - 1) / TXC), (unsigned)((g.nyf + TYC - 1) / TYC));
+}
+
+template <typename KernelT>
+cudaError_t set_smem(KernelT k, size_t bytes) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, void *xf, double t,
+                              cudaStream_t st) {
+    double w = 1.0;
+    if (g.ramp) w = t <= 0.5 ? 0.5 - 0.5 * cos(2.0 * 3.14159265358979323846 * t) : 1.0;
+    if (prec == DNNMG_F64)
+        k_prolongate<double><<<node_grid(g), NTHREADS, 0, st>>>(g, xc, (double *)xf, w);
+    else
+        k_prolongate<float><<<node_grid(g), NTHREADS, 0, st>>>(g, xc, (float *)xf, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<double> &f64,
+                                     const FemCoef<float> &f32, const void *xf, const void *bf,
+                                     void *rf, void *X, cudaStream_t st) {
+    cudaError_t e;
+    if (prec == DNNMG_F64) {
+        auto k = k_residual_features<double, double>;
+        const size_t sm = ResLayout::bytes<double>();
+        if ((e = set_smem(k, sm)) != cudaSuccess) return e;
+        k<<<tile_grid(g), NTHREADS, sm, st>>>(g, f64, (const double *)xf, (const double *)bf,
+                                              (double *)rf, (double *)X);
+    } else if (prec == DNNMG_F32) {
+        auto k = k_residual_features<float, float>;
+        const size_t sm = ResLayout::bytes<float>();
+        if ((e = set_smem(k, sm)) != cudaSuccess) return e;
+        k<<<tile_grid(g), NTHREADS, sm, st>>>(g, f32, (const float *)xf, (const float *)bf,
+                                              (float *)rf, (float *)X);
+    } else {
+        auto k = k_residual_features<float, __nv_bfloat16>;
+        const size_t sm = ResLayout::bytes<float>();
+        if ((e = set_smem(k, sm)) != cudaSuccess) return e;
+        k<<<tile_grid(g), NTHREADS, sm, st>>>(g, f32, (const float *)xf, (const float *)bf,
+                                              (float *)rf, (__nv_bfloat16 *)X);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf,
+                               void *vcorr, cudaStream_t st) {
+    if (prec == DNNMG_F64)
+        k_scatter_avg<double><<<node_grid(g), NTHREADS, 0, st>>>(g, (const double *)d,
+                                                                 (const double *)xf, (double *)vcorr);
+    else
+        k_scatter_avg<float><<<node_grid(g), NTHREADS, 0, st>>>(g, (const float *)d,
+                                                                (const float *)xf, (float *)vcorr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
+                       const FemCoef<float> &f32, const void *vcorr, void *bf, cudaStream_t st) {
+    cudaError_t e;
+    if (prec == DNNMG_F64) {
+        const size_t sm = RhsLayout::bytes<double>();
+        if ((e = set_smem(k_rhs<double>, sm)) != cudaSuccess) return e;
+        k_rhs<double><<<tile_grid(g), NTHREADS, sm, st>>>(g, f64, (const double *)vcorr, (double *)bf);
+    } else {
+        const size_t sm = RhsLayout::bytes<float>();
+        if ((e = set_smem(k_rhs<float>, sm)) != cudaSuccess) return e;
+        k_rhs<float><<<tile_grid(g), NTHREADS, sm, st>>>(g, f32, (const float *)vcorr, (float *)bf);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const MeshGeom &g, int prec, const void *bf, double *bc,
+                            cudaStream_t st) {
+    dim3 grid((unsigned)((g.nxc + 1 + NTHREADS - 1) / NTHREADS), (unsigned)(g.nyc + 1));
+    if (prec == DNNMG_F64)
+        k_restrict<double><<<grid, NTHREADS, 0, st>>>(g, (const double *)bf, bc);
+    else
+        k_restrict<float><<<grid, NTHREADS, 0, st>>>(g, (const float *)bf, bc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mesh_maps(const MeshGeom &g, unsigned char *flags, unsigned char *mult,
+                             cudaStream_t st) {
+    k_mesh_maps<<<node_grid(g), NTHREADS, 0, st>>>(g, flags, mult);
+    return cudaGetLastError();
+}
+
+}  // namespace dnnmg

@@ -1,0 +1,292 @@
+"""Thin Python binding of libdnnmg (include/dnnmg.h) over ctypes.
+
+Argument marshalling only: every step of the correction runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors (device memory and streams come
+from PyTorch); the functions check dtype, device, contiguity and size, then
+pass raw pointers and the current stream.  If the shared library is missing
+the import fails loudly -- there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdnnmg.so")
+
+F64, F32, BF16NET = 0, 1, 2
+PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16NET}
+_REAL = {F64: torch.float64, F32: torch.float32, BF16NET: torch.float32}
+_FEAT = {F64: torch.float64, F32: torch.float32, BF16NET: torch.bfloat16}
+
+STATUS = {0: "DNNMG_OK", 1: "DNNMG_EINVAL", 2: "DNNMG_ECUDA", 3: "DNNMG_EUNSUPPORTED", 4: "DNNMG_ENOMEM"}
+
+
+class DnnmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nxc", ctypes.c_int), ("nyc", ctypes.c_int), ("K", ctypes.c_int), ("s", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("obst_cx", ctypes.c_double), ("obst_cy", ctypes.c_double),
+                ("obst_ax", ctypes.c_double), ("obst_ay", ctypes.c_double),
+                ("solid", ctypes.POINTER(ctypes.c_ubyte)),
+                ("nu", ctypes.c_double), ("k", ctypes.c_double), ("alpha0", ctypes.c_double),
+                ("u_max", ctypes.c_double), ("ramp", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("nxc", ctypes.c_int), ("nyc", ctypes.c_int), ("nxf", ctypes.c_int), ("nyf", ctypes.c_int),
+                ("K", ctypes.c_int), ("s", ctypes.c_int), ("npx", ctypes.c_int), ("npy", ctypes.c_int),
+                ("Nc", ctypes.c_longlong), ("Nf", ctypes.c_longlong), ("P", ctypes.c_int),
+                ("nf", ctypes.c_int), ("nc", ctypes.c_int), ("n_in", ctypes.c_int), ("n_out", ctypes.c_int),
+                ("ldx", ctypes.c_int), ("n_solid_coarse", ctypes.c_int), ("precision", ctypes.c_int),
+                ("real_bytes", ctypes.c_int), ("feature_bytes", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2008_11520_gb300.build.build() "
+                          "(or __graft_entry__.build()); there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "dnnmg_mesh_query": [ctypes.POINTER(MeshDesc), ctypes.POINTER(MeshInfo)],
+        "dnnmg_mesh_create": [ctypes.POINTER(MeshDesc), ctypes.POINTER(P)],
+        "dnnmg_mesh_destroy": [P],
+        "dnnmg_mesh_get_info": [P, ctypes.POINTER(MeshInfo)],
+        "dnnmg_mesh_maps": [P, P, P, P, P],
+        "dnnmg_net_create": [I, I, I, P, P, P, I, ctypes.POINTER(P)],
+        "dnnmg_net_destroy": [P],
+        "dnnmg_prolongate": [P, P, P, D, P],
+        "dnnmg_patch_features": [P, P, P, P, P, P],
+        "dnnmg_gru_step": [P, P, P, P, I, P],
+        "dnnmg_scatter_avg": [P, P, P, P, P],
+        "dnnmg_rhs_restrict": [P, P, P, P, P],
+        "dnnmg_step": [P, P, P, P, P, P, P, S, D, P],
+        "dnnmg_step_host": [P, P, P, P, P, P, P, S, D, P],
+        "dnnmg_step_launches": [P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.dnnmg_last_error.argtypes = []
+    lib.dnnmg_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    """The loaded ctypes library."""
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise DnnmgError(code, _lib.dnnmg_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, numel, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, {numel} expected")
+
+
+def make_desc(nxc, nyc, K, s, ellipse=None, precision="f64", solid=None, lx=2.2, ly=0.41,
+              nu=1e-3, k=0.01, alpha0=0.1, u_max=1.5, ramp=False):
+    d = MeshDesc()
+    d.nxc, d.nyc, d.K, d.s = nxc, nyc, K, s
+    d.lx, d.ly = lx, ly
+    cx, cy, ax, ay = ellipse if ellipse is not None else (0.0, 0.0, 0.0, 0.0)
+    d.obst_cx, d.obst_cy, d.obst_ax, d.obst_ay = cx, cy, ax, ay
+    d._solid_keep = None
+    if solid is not None:
+        arr = np.ascontiguousarray(solid, dtype=np.uint8)
+        d._solid_keep = arr
+        d.solid = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+    d.nu, d.k, d.alpha0, d.u_max = nu, k, alpha0, u_max
+    d.ramp = 1 if ramp else 0
+    d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return d
+
+
+def dnnmg_mesh_query(desc):
+    info = MeshInfo()
+    _check(_lib.dnnmg_mesh_query(ctypes.byref(desc), ctypes.byref(info)))
+    return info
+
+
+class Mesh:
+    """Owning wrapper of a dnnmg_mesh_t created on the current CUDA device."""
+
+    def __init__(self, desc):
+        self.desc = desc
+        h = ctypes.c_void_p()
+        _check(_lib.dnnmg_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
+        self.handle = h
+        self.info = MeshInfo()
+        _check(_lib.dnnmg_mesh_get_info(h, ctypes.byref(self.info)))
+        self.real = _REAL[self.info.precision]
+        self.feat = _FEAT[self.info.precision]
+
+    def close(self):
+        if self.handle:
+            _lib.dnnmg_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # convenience allocators (device memory from torch)
+    def fine(self, ncomp, device="cuda"):
+        return torch.zeros(ncomp, self.info.Nf, dtype=self.real, device=device)
+
+    def coarse(self, ncomp=3, device="cuda"):
+        return torch.zeros(ncomp, self.info.Nc, dtype=torch.float64, device=device)
+
+    def features(self, device="cuda"):
+        return torch.zeros(self.info.P, self.info.ldx, dtype=self.feat, device=device)
+
+    def workspace(self, device="cuda"):
+        return torch.empty(self.info.workspace_bytes, dtype=torch.uint8, device=device)
+
+
+class Net:
+    """Owning wrapper of a dnnmg_net_t (weights uploaded in the given precision)."""
+
+    def __init__(self, Wx, Uh, Wfc, precision="f64"):
+        Wx, Uh, Wfc = (np.ascontiguousarray(a, dtype=np.float64) for a in (Wx, Uh, Wfc))
+        G, n_in = Wx.shape
+        H = Uh.shape[1]
+        n_out = Wfc.shape[0]
+        if G != 3 * H or Uh.shape != (3 * H, H) or Wfc.shape != (n_out, H):
+            raise ValueError("weight shapes must be Wx [3H][n_in], Uh [3H][H], Wfc [n_out][H]")
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        _check(_lib.dnnmg_net_create(n_in, H, n_out, Wx.ctypes.data, Uh.ctypes.data, Wfc.ctypes.data,
+                                     self.precision, ctypes.byref(h)))
+        self.handle = h
+        self.n_in, self.H, self.n_out = n_in, H, n_out
+        self.real = _REAL[self.precision]
+        self.feat = _FEAT[self.precision]
+
+    def close(self):
+        if self.handle:
+            _lib.dnnmg_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dnnmg_mesh_maps(mesh, patch_cell=None, node_flags=None, node_mult=None, stream=None):
+    I = mesh.info
+    if patch_cell is not None:
+        _need(patch_cell, torch.int32, I.P, "patch_cell")
+    if node_flags is not None:
+        _need(node_flags, torch.uint8, I.Nf, "node_flags")
+    if node_mult is not None:
+        _need(node_mult, torch.uint8, I.Nf, "node_mult")
+    _check(_lib.dnnmg_mesh_maps(mesh.handle, _ptr(patch_cell), _ptr(node_flags), _ptr(node_mult),
+                                _stream(stream)))
+
+
+def dnnmg_prolongate(mesh, xc, xf, t, stream=None):
+    I = mesh.info
+    _need(xc, torch.float64, 3 * I.Nc, "xc")
+    _need(xf, mesh.real, 3 * I.Nf, "xf")
+    _check(_lib.dnnmg_prolongate(mesh.handle, _ptr(xc), _ptr(xf), float(t), _stream(stream)))
+
+
+def dnnmg_patch_features(mesh, xf, bf, X, rf=None, stream=None):
+    I = mesh.info
+    _need(xf, mesh.real, 3 * I.Nf, "xf")
+    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(X, mesh.feat, I.P * I.ldx, "X")
+    if rf is not None:
+        _need(rf, mesh.real, 3 * I.Nf, "rf")
+    _check(_lib.dnnmg_patch_features(mesh.handle, _ptr(xf), _ptr(bf), _ptr(rf), _ptr(X), _stream(stream)))
+
+
+def dnnmg_gru_step(net, X, h, d, P, stream=None):
+    ldx = (net.n_in + 15) // 16 * 16
+    _need(X, net.feat, P * ldx, "X")
+    _need(h, net.real, P * net.H, "h")
+    _need(d, net.real, P * net.n_out, "d")
+    _check(_lib.dnnmg_gru_step(net.handle, _ptr(X), _ptr(h), _ptr(d), int(P), _stream(stream)))
+
+
+def dnnmg_scatter_avg(mesh, d, xf, vcorr, stream=None):
+    I = mesh.info
+    _need(d, mesh.real, I.P * I.n_out, "d")
+    _need(xf, mesh.real, 3 * I.Nf, "xf")
+    _need(vcorr, mesh.real, 2 * I.Nf, "vcorr")
+    _check(_lib.dnnmg_scatter_avg(mesh.handle, _ptr(d), _ptr(xf), _ptr(vcorr), _stream(stream)))
+
+
+def dnnmg_rhs_restrict(mesh, vcorr, bf, bc, stream=None):
+    I = mesh.info
+    _need(vcorr, mesh.real, 2 * I.Nf, "vcorr")
+    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(bc, torch.float64, 3 * I.Nc, "bc")
+    _check(_lib.dnnmg_rhs_restrict(mesh.handle, _ptr(vcorr), _ptr(bf), _ptr(bc), _stream(stream)))
+
+
+def dnnmg_step(mesh, net, xc, h, bf, bc, workspace, t, stream=None):
+    I = mesh.info
+    _need(xc, torch.float64, 3 * I.Nc, "xc")
+    _need(h, mesh.real, I.P * net.H, "h")
+    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(bc, torch.float64, 3 * I.Nc, "bc")
+    if workspace.dtype != torch.uint8 or not workspace.is_cuda:
+        raise TypeError("workspace must be a CUDA uint8 tensor")
+    _check(_lib.dnnmg_step(mesh.handle, net.handle, _ptr(xc), _ptr(h), _ptr(bf), _ptr(bc),
+                           _ptr(workspace), workspace.numel(), float(t), _stream(stream)))
+
+
+def dnnmg_step_host(mesh, net, xc_host, h, bf, bc_host, workspace, t, stream=None):
+    """xc_host / bc_host: CPU float64 tensors [3][Nc] (pinned for asynchronous copies)."""
+    I = mesh.info
+    for name, a in (("xc_host", xc_host), ("bc_host", bc_host)):
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != 3 * I.Nc:
+            raise TypeError(f"{name} must be a contiguous CPU float64 tensor of {3 * I.Nc} elements")
+    _need(h, mesh.real, I.P * net.H, "h")
+    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _check(_lib.dnnmg_step_host(mesh.handle, net.handle, _ptr(xc_host), _ptr(h), _ptr(bf), _ptr(bc_host),
+                                _ptr(workspace), workspace.numel(), float(t), _stream(stream)))
+
+
+def dnnmg_step_launches(mesh, net):
+    return _lib.dnnmg_step_launches(mesh.handle, net.handle)

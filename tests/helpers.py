@@ -1,0 +1,78 @@
+"""Shared helpers of the parity tests: cases, seeded inputs, error measures."""
+
+import numpy as np
+
+from oracle.mesh import Mesh as OMesh, Params
+from paper_2008_11520_gb300 import synth
+
+# Tolerances on the relative L2 error against the FP64 oracle.
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 2e-2}
+
+# Small cases: several 32 x 16 fine-cell tiles, ragged tails, every K and s,
+# an obstacle-free channel and explicit masks with fully solid patches.
+CASES = {
+    "plain_f64": dict(nxc=32, nyc=8, K=1, s=1, H=32, prec="f64", ellipse=(0.2, 0.2, 0.04, 0.06)),
+    "ragged_f32": dict(nxc=38, nyc=10, K=1, s=2, H=16, prec="f32", ellipse=(0.3, 0.2, 0.1, 0.08)),
+    "k2_f32": dict(nxc=40, nyc=10, K=2, s=1, H=24, prec="f32", ellipse=(0.2, 0.2, 0.05, 0.04)),
+    "k2s2_bf16": dict(nxc=48, nyc=12, K=2, s=2, H=32, prec="bf16", ellipse=(0.25, 0.2, 0.08, 0.06)),
+    "k3_f64": dict(nxc=12, nyc=6, K=3, s=1, H=8, prec="f64", ellipse=(0.5, 0.2, 0.2, 0.1)),
+    "k2s2_f32_channel": dict(nxc=20, nyc=6, K=2, s=2, H=8, prec="f32", ellipse=None),
+    "k1s2_f64_mask": dict(nxc=24, nyc=8, K=1, s=2, H=8, prec="f64", ellipse=None, mask_seed=3),
+}
+
+
+def mask_for(case):
+    if "mask_seed" not in case:
+        return None
+    rng = np.random.default_rng(case["mask_seed"])
+    m = rng.random((case["nyc"], case["nxc"])) < 0.15
+    m[2:6, 4:8] = True          # a fully solid block covering whole 2 x 2 patches
+    m[:, 0] = False
+    return m
+
+
+def oracle_mesh(case, window=None):
+    return OMesh(case["nxc"], case["nyc"], case["K"], case["s"], ellipse=case.get("ellipse"),
+                 solid=mask_for(case), window=window)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def np_dtype(prec):
+    return np.float64 if prec == "f64" else np.float32
+
+
+def spec_for(case, seed=11):
+    ell = case.get("ellipse") or (0.2, 0.2, 0.0, 0.0)
+    return synth.FlowSpec.from_seed(seed, ell)
+
+
+def coarse_input(case, t=0.0, seed=11):
+    return synth.coarse_state(spec_for(case, seed), case["nxc"], case["nyc"], t)
+
+
+def fine_velocity(case, seed=11, perturb=5, t=0.0):
+    nxf, nyf = case["nxc"] << case["K"], case["nyc"] << case["K"]
+    x = synth.fine_state(spec_for(case, seed), nxf, nyf, t, perturb_seed=perturb)
+    return x
+
+
+def rhs_like(case, seed=13):
+    """A seeded stand-in for a fine right-hand side, scaled like (1/k) (v, phi)."""
+    nxf, nyf = case["nxc"] << case["K"], case["nyc"] << case["K"]
+    hx, hy = 2.2 / nxf, 0.41 / nyf
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, 1.0, (2, (nxf + 1) * (nyf + 1))) * hx * hy / 0.01
+
+
+def weights(case, n_in, n_out, seed=17):
+    return synth.net_weights(n_in, case["H"], n_out, seed)
+
+
+__all__ = ["CASES", "TOL", "Params", "oracle_mesh", "rel_l2", "np_dtype", "coarse_input",
+           "fine_velocity", "rhs_like", "weights", "mask_for", "spec_for"]

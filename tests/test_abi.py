@@ -1,0 +1,86 @@
+"""Host-side checks of the C-ABI library: it loads, exports every symbol its
+header declares, and its host-only size query agrees with the oracle's mesh."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_11520_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2008_11520_gb300 import dnnmg
+    return dnnmg
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:int|const char \*)\s*(dnnmg_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_symbols()
+    for n in ("dnnmg_prolongate", "dnnmg_patch_features", "dnnmg_gru_step", "dnnmg_scatter_avg",
+              "dnnmg_rhs_restrict", "dnnmg_step", "dnnmg_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in declared_symbols() if not hasattr(so, n)]
+    assert not missing
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(nxc=32, nyc=8, K=1, s=1, ellipse=(0.2, 0.2, 0.04, 0.06)),
+    dict(nxc=64, nyc=16, K=2, s=2, ellipse=(0.2, 0.2, 0.05, 0.04)),
+    dict(nxc=38, nyc=10, K=1, s=2, ellipse=(0.3, 0.2, 0.1, 0.08)),
+    dict(nxc=16, nyc=8, K=3, s=1, ellipse=None),
+])
+def test_mesh_query_matches_oracle(lib, cfg):
+    from oracle.mesh import Mesh
+    om = Mesh(cfg["nxc"], cfg["nyc"], cfg["K"], cfg["s"], ellipse=cfg["ellipse"])
+    info = lib.dnnmg_mesh_query(lib.make_desc(cfg["nxc"], cfg["nyc"], cfg["K"], cfg["s"], cfg["ellipse"]))
+    assert (info.P, info.nf, info.nc, info.n_in, info.n_out) == (om.P, om.nf, om.nc, om.n_in, om.n_out)
+    assert (info.Nf, info.Nc) == (om.Nf, om.Nc)
+    assert info.n_solid_coarse == int(om.solid_coarse.sum())
+    assert info.ldx % 16 == 0 and info.ldx >= info.n_in
+
+
+def test_mesh_query_explicit_mask(lib):
+    from oracle.mesh import Mesh
+    rng = np.random.default_rng(0)
+    mask = rng.random((8, 16)) < 0.3
+    om = Mesh(16, 8, 1, 2, solid=mask)
+    info = lib.dnnmg_mesh_query(lib.make_desc(16, 8, 1, 2, solid=mask))
+    assert info.P == om.P and info.n_solid_coarse == int(mask.sum())
+
+
+@pytest.mark.parametrize("bad", [dict(nxc=31), dict(K=0), dict(K=4), dict(s=3), dict(nxc=30, s=4),
+                                 dict(precision=7)])
+def test_mesh_query_rejects_invalid(lib, bad):
+    args = dict(nxc=32, nyc=8, K=1, s=1)
+    prec = bad.pop("precision", "f64")
+    args.update(bad)
+    with pytest.raises(lib.DnnmgError) as e:
+        lib.dnnmg_mesh_query(lib.make_desc(args["nxc"], args["nyc"], args["K"], args["s"], precision=prec))
+    assert e.value.code in (1, 3) and str(e.value)
+
+
+def test_mesh_query_rejects_oversize(lib):
+    with pytest.raises(lib.DnnmgError) as e:
+        lib.dnnmg_mesh_query(lib.make_desc(1024, 16384, 2, 1))
+    assert e.value.code == 3

@@ -1,0 +1,297 @@
+"""GPU parity of every step of the correction against the CPU FP64 oracle.
+
+Each stage is called through the C ABI on the same seeded inputs the oracle
+gets, on meshes that span several 32 x 16 fine-cell tiles with ragged tails;
+index maps must match bit for bit, floating point within the tolerance of its
+precision (FP64 1e-12, FP32 1e-5, BF16 network 2e-2 relative L2).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import (CASES, TOL, Params, coarse_input, fine_velocity, mask_for, np_dtype, oracle_mesh,
+                     rel_l2, rhs_like, weights)
+from oracle import average, features, fem, gru, step, transfer
+
+pytestmark = pytest.mark.gpu
+
+PRM = Params()
+
+
+@pytest.fixture(scope="module")
+def dn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_11520_gb300 import dnnmg
+    return dnnmg
+
+
+def gpu_mesh(dn, case):
+    return dn.Mesh(dn.make_desc(case["nxc"], case["nyc"], case["K"], case["s"], case.get("ellipse"),
+                                precision=case["prec"], solid=mask_for(case)))
+
+
+def cuda(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda().contiguous()
+
+
+def host(t):
+    return t.detach().float().cpu().numpy().astype(np.float64) if t.dtype == torch.bfloat16 \
+        else t.detach().cpu().numpy().astype(np.float64)
+
+
+def as_real(case, a):
+    """The input as the GPU sees it (rounded to the fine real type), in float64."""
+    return np.asarray(a, dtype=np_dtype(case["prec"])).astype(np.float64)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_index_maps_bit_exact(dn, name):
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    I = m.info
+    assert I.P == om.P
+    pc = torch.zeros(I.P, dtype=torch.int32, device="cuda")
+    fl = torch.zeros(I.Nf, dtype=torch.uint8, device="cuda")
+    mu = torch.zeros(I.Nf, dtype=torch.uint8, device="cuda")
+    dn.dnnmg_mesh_maps(m, pc, fl, mu)
+    torch.cuda.synchronize()
+    exp_pc = om.patches[:, 1] * om.npx + om.patches[:, 0]
+    assert np.array_equal(pc.cpu().numpy(), exp_pc)
+    assert np.array_equal(fl.cpu().numpy(), om.fine_node_flags().ravel())
+    assert np.array_equal(mu.cpu().numpy(), om.multiplicity.ravel())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_prolongate(dn, name):
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    xc = coarse_input(case, t=0.3)
+    xf = m.fine(3)
+    dn.dnnmg_prolongate(m, cuda(xc, torch.float64), xf, 0.3)
+    ref = transfer.prolongate(om, PRM, xc, 0.3)
+    got = host(xf).reshape(3, -1)
+    tol = 1e-14 if case["prec"] == "f64" else 1e-7
+    assert rel_l2(got, ref) <= tol
+    # Dirichlet values are set exactly as the oracle sets them
+    mask = om.dirichlet.ravel()
+    assert np.allclose(got[:2, mask], ref[:2, mask], rtol=1e-7 if case["prec"] != "f64" else 1e-15, atol=0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_features(dn, name):
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    xf = as_real(case, fine_velocity(case))
+    bf = as_real(case, rhs_like(case))
+    X = m.features()
+    rf = m.fine(3)
+    dn.dnnmg_patch_features(m, cuda(xf, m.real), cuda(bf, m.real), X, rf=rf)
+    r_ref = fem.residual(om, PRM, xf, bf)
+    X_ref = features.patch_features(om, PRM, xf, r_ref)
+    r_got = host(rf).reshape(3, -1)
+    tol_r = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
+    for c in range(3):
+        assert rel_l2(r_got[c], r_ref[c]) <= tol_r, c
+    # exact zeros on Dirichlet / inactive rows
+    assert np.all(r_got[:2, om.dirichlet.ravel()] == 0)
+    assert np.all(r_got[2, ~om.p_active.ravel()] == 0)
+    Xg = host(X).reshape(m.info.P, m.info.ldx)
+    assert np.all(Xg[:, om.n_in:] == 0)
+    tol_x = TOL[case["prec"]] if case["prec"] != "bf16" else 1e-2
+    nf = om.nf
+    blocks = [(0, nf), (nf, 2 * nf), (2 * nf, 3 * nf), (3 * nf, om.n_in)]
+    for a, b in blocks:
+        assert rel_l2(Xg[:, a:b], X_ref[:, a:b]) <= tol_x, (a, b)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_gru_step(dn, name):
+    case = CASES[name]
+    om = oracle_mesh(case)
+    rng = np.random.default_rng(21)
+    P, n_in, n_out, H = om.P, om.n_in, om.n_out, case["H"]
+    Wx, Uh, Wfc = weights(case, n_in, n_out)
+    X = rng.normal(0.0, 1.0, (P, n_in))
+    h = rng.uniform(-0.5, 0.5, (P, H))
+    net = dn.Net(Wx, Uh, Wfc, case["prec"])
+    ldx = (n_in + 15) // 16 * 16
+    Xp = np.zeros((P, ldx))
+    Xp[:, :n_in] = X
+    Xcpu = torch.as_tensor(Xp).to(net.feat)   # rounded on the host (bf16 for BF16)
+    Xq = Xcpu.to(torch.float64).numpy()[:, :n_in]
+    Xt = Xcpu.cuda().contiguous()
+    hq = as_real(case, h)
+    ht = cuda(hq, net.real)
+    d = torch.zeros(P, n_out, dtype=net.real, device="cuda")
+    dn.dnnmg_gru_step(net, Xt, ht, d, P)
+    h_ref, d_ref = gru.gru_step(Xq, hq, Wx, Uh, Wfc)
+    tol = TOL[case["prec"]]
+    assert rel_l2(host(ht), h_ref) <= tol
+    assert rel_l2(host(d), d_ref) <= tol
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_scatter_avg(dn, name):
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    rng = np.random.default_rng(23)
+    d = as_real(case, rng.normal(0.0, 0.3, (om.P, om.n_out)))
+    xf = as_real(case, fine_velocity(case))
+    vc = m.fine(2)
+    dn.dnnmg_scatter_avg(m, cuda(d, m.real), cuda(xf, m.real), vc)
+    ref = average.scatter_average(om, d, xf)
+    tol = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
+    assert rel_l2(host(vc).reshape(2, -1), ref) <= tol
+    # Dirichlet nodes keep the prolongated values bit for bit
+    mask = om.dirichlet.ravel()
+    assert np.array_equal(host(vc).reshape(2, -1)[:, mask], xf[:2, mask])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_constant_correction_is_exact(dn, name):
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    xf = as_real(case, fine_velocity(case))
+    d = np.full((om.P, om.n_out), 0.375)
+    vc = m.fine(2)
+    dn.dnnmg_scatter_avg(m, cuda(d, m.real), cuda(xf, m.real), vc)
+    got = host(vc).reshape(2, -1)
+    free = ~om.dirichlet.ravel()
+    exp = (xf[:2, free].astype(np_dtype(case["prec"])) + np_dtype(case["prec"])(0.375)).astype(np.float64)
+    assert np.array_equal(got[:, free], exp)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_restrict(dn, name):
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    v = as_real(case, fine_velocity(case)[:2])
+    bf = m.fine(2)
+    bc = m.coarse(3)
+    dn.dnnmg_rhs_restrict(m, cuda(v, m.real), bf, bc)
+    b_ref = fem.rhs(om, PRM, v)
+    tol = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
+    bfg = host(bf).reshape(2, -1)
+    assert rel_l2(bfg, b_ref) <= tol
+    assert np.all(bfg[:, om.dirichlet.ravel()] == 0)
+    assert rel_l2(host(bc).reshape(3, -1), transfer.restrict(om, b_ref)) <= tol
+
+
+def run_steps(dn, case, nsteps, seed=31):
+    """Both sides run nsteps corrections on identical inputs; returns per-step errors."""
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
+    net = dn.Net(Wx, Uh, Wfc, case["prec"])
+    rng = np.random.default_rng(seed)
+    h0 = as_real(case, rng.uniform(-0.5, 0.5, (om.P, case["H"])))
+    v0 = as_real(case, fine_velocity(case)[:2])
+    # initial right-hand side: each side assembles its own from v0
+    bf_g = m.fine(2)
+    bc_g = m.coarse(3)
+    dn.dnnmg_rhs_restrict(m, cuda(v0, m.real), bf_g, bc_g)
+    bf_o = fem.rhs(om, PRM, v0)
+    h_g = cuda(h0, m.real)
+    h_o = h0.copy()
+    ws = m.workspace()
+    errs = []
+    for n in range(nsteps):
+        t = n * PRM.k
+        xc = coarse_input(case, t=t)
+        dn.dnnmg_step(m, net, cuda(xc, torch.float64), h_g, bf_g, bc_g, ws, t)
+        out = step.dnnmg_step(om, PRM, (Wx, Uh, Wfc), xc, h_o, bf_o, t)
+        h_o, bf_o = out["h"], out["bf"]
+        errs.append({"h": rel_l2(host(h_g), out["h"]), "bf": rel_l2(host(bf_g).reshape(2, -1), out["bf"]),
+                     "bc": rel_l2(host(bc_g).reshape(3, -1), out["bc"])})
+    return errs
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_matches_oracle(dn, name):
+    case = CASES[name]
+    errs = run_steps(dn, case, 3)
+    tol = TOL[case["prec"]]
+    for n, e in enumerate(errs):
+        for k, v in e.items():
+            assert v <= tol, (n, k, v)
+
+
+def test_plain_config_ten_steps(dn):
+    # the single plain instance (32 x 8, K = 1, H = 32, FP64) over its 10 steps
+    errs = run_steps(dn, CASES["plain_f64"], 10)
+    assert max(max(e.values()) for e in errs) <= TOL["f64"]
+
+
+def test_step_is_deterministic_and_host_variant_agrees(dn):
+    case = CASES["k2s2_bf16"]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
+    net = dn.Net(Wx, Uh, Wfc, case["prec"])
+    xc = coarse_input(case, t=0.0)
+    h0 = torch.rand(om.P, case["H"], device="cuda") - 0.5
+    bf0 = m.fine(2)
+    bcs = []
+    for variant in range(3):
+        h, bf = h0.clone(), bf0.clone()
+        bc = m.coarse(3)
+        ws = m.workspace()
+        if variant < 2:
+            dn.dnnmg_step(m, net, cuda(xc, torch.float64), h, bf, bc, ws, 0.0)
+        else:
+            xch = torch.as_tensor(xc).pin_memory()
+            bch = torch.zeros(3 * m.info.Nc, dtype=torch.float64).pin_memory()
+            dn.dnnmg_step_host(m, net, xch, h, bf, bch, ws, 0.0)
+            torch.cuda.synchronize()
+            bc = bch.cuda()
+        torch.cuda.synchronize()
+        bcs.append((bc.cpu().numpy().ravel(), h.cpu().numpy(), bf.cpu().numpy()))
+    for k in range(3):
+        assert np.array_equal(bcs[0][k], bcs[1][k])
+        assert np.array_equal(bcs[0][k], bcs[2][k])
+
+
+def test_zero_network_reduces_to_prolongated_rhs(dn):
+    # with W_fc = 0 the correction vanishes, so v_corr = v~ and the step
+    # returns R Rhs(P x_c) (Algorithm 2 without the network)
+    case = CASES["ragged_f32"]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
+    net = dn.Net(Wx, Uh, np.zeros_like(Wfc), "f32")
+    xc = coarse_input(case, t=0.0)
+    h = torch.zeros(om.P, case["H"], device="cuda")
+    bf, bc, ws = m.fine(2), m.coarse(3), m.workspace()
+    dn.dnnmg_step(m, net, cuda(xc, torch.float64), h, bf, bc, ws, 0.0)
+    xf = m.fine(3)
+    dn.dnnmg_prolongate(m, cuda(xc, torch.float64), xf, 0.0)
+    bf2, bc2 = m.fine(2), m.coarse(3)
+    dn.dnnmg_rhs_restrict(m, xf[:2].contiguous(), bf2, bc2)
+    torch.cuda.synchronize()
+    assert torch.equal(bf, bf2) and torch.equal(bc, bc2)
+
+
+def test_invalid_arguments_raise(dn):
+    case = CASES["ragged_f32"]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
+    net64 = dn.Net(Wx, Uh, Wfc, "f64")
+    h = torch.zeros(om.P, case["H"], device="cuda")
+    with pytest.raises(dn.DnnmgError):   # precision mismatch between mesh and net
+        dn.dnnmg_step(m, net64, m.coarse(3), h, m.fine(2), m.coarse(3), m.workspace(), 0.0)
+    net = dn.Net(Wx, Uh, Wfc, "f32")
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dn.DnnmgError):   # workspace too small
+        dn.dnnmg_step(m, net, m.coarse(3), h, m.fine(2), m.coarse(3), small, 0.0)
+    with pytest.raises(dn.DnnmgError):   # aliasing output
+        v = m.fine(2)
+        dn.dnnmg_rhs_restrict(m, v, v, m.coarse(3))
