@@ -188,6 +188,16 @@ int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *b
                        cudaStream_t stream);
 
 /*
+ * S7 alone, Algorithm 2 line 9: bc = R bf with R = P^T (the transpose of the
+ * bilinear prolongation across the K levels), coarse Dirichlet velocity rows
+ * and all pressure rows zero.  Float input is accumulated with error-free
+ * float-pair arithmetic (about 2^-44 relative to the sum of magnitudes) and
+ * stored in double; double input is accumulated in double.
+ *   bf [2][Nf] real (in), bc [3][Nc] double (out).
+ */
+int dnnmg_restrict(dnnmg_mesh_t mesh, const void *bf, double *bc, cudaStream_t stream);
+
+/*
  * S1-S7 in order (Algorithm 2 lines 6-9) on one stream.
  *   xc [3][Nc] double (in), h [P][H] (in/out), bf [2][Nf] (in: this step's
  *   fine right-hand side; out: the next step's), bc [3][Nc] double (out),
@@ -208,6 +218,19 @@ int dnnmg_step(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, vo
 int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, void *h,
                     void *bf, double *bc_host, void *workspace, size_t workspace_bytes,
                     double t, cudaStream_t stream);
+
+/*
+ * Device status word of a network (synchronous): bit 0 (DNNMG_DEVERR_TIMEOUT)
+ * is set if a kernel's bounded wait on its own pipeline ran out of time (the
+ * kernel then returns without finishing its tile).  reset != 0 clears it.
+ */
+#define DNNMG_DEVERR_TIMEOUT 1
+int dnnmg_net_status(dnnmg_net_t net, int *status, int reset);
+
+/* 1 if the network's GRU step runs on the tensor cores (BF16 networks whose
+ * shapes the tcgen05 kernel supports and DNNMG_GRU_KERNEL != "simt" in the
+ * environment at creation), else 0. */
+int dnnmg_net_uses_tensor_cores(dnnmg_net_t net);
 
 /* Number of kernel launches one dnnmg_step enqueues for this mesh/net. */
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net);

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -350,6 +351,20 @@ int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out) {
     g.solid = m->d_solid;
     g.patch_id = m->d_patch_id;
     g.patch_cell = m->d_patch_cell;
+    std::vector<int> tab((size_t)I.ldx);
+    feature_table(g, tab.data());
+    m->d_feat_tab = nullptr;
+    if (cudaMalloc(&m->d_feat_tab, tab.size() * sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(m->d_feat_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(m->d_solid);
+        cudaFree(m->d_patch_id);
+        cudaFree(m->d_patch_cell);
+        cudaFree(m->d_feat_tab);
+        delete m;
+        cudaGetLastError();
+        return fail(DNNMG_ENOMEM, "device allocation of the feature table failed");
+    }
+    g.feat_tab = m->d_feat_tab;
     fem_coefficients(*desc, &m->fem64);
     to_float(m->fem64, &m->fem32);
     *out = m;
@@ -362,6 +377,7 @@ int dnnmg_mesh_destroy(dnnmg_mesh_t mesh) {
     cudaFree(mesh->d_solid);
     cudaFree(mesh->d_patch_id);
     cudaFree(mesh->d_patch_cell);
+    cudaFree(mesh->d_feat_tab);
     delete mesh;
     return DNNMG_OK;
 }
@@ -403,8 +419,16 @@ int dnnmg_net_create(int n_in, int hidden, int n_out, const double *Wx, const do
     n->n_out = n_out;
     n->precision = precision;
     n->WxT = n->UhT = n->WfcT = n->tc_weights = nullptr;
+    n->tc = nullptr;
+    n->d_status = nullptr;
     n->tc_bytes = 0;
     cudaGetDevice(&n->device);
+    if (cudaMalloc(&n->d_status, sizeof(int)) != cudaSuccess || cudaMemset(n->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(n->d_status);
+        delete n;
+        cudaGetLastError();
+        return fail(DNNMG_ENOMEM, "device allocation of the status word failed");
+    }
     const int G = 3 * hidden;
     std::vector<double> wx((size_t)n->ldx * G, 0.0), uh((size_t)hidden * G), wfc((size_t)hidden * n_out);
     for (int j = 0; j < G; ++j)
@@ -436,9 +460,16 @@ int dnnmg_net_create(int n_in, int hidden, int n_out, const double *Wx, const do
         cudaFree(n->WxT);
         cudaFree(n->UhT);
         cudaFree(n->WfcT);
+        cudaFree(n->d_status);
         delete n;
         cudaGetLastError();
         return fail(e, "uploading the network weights failed");
+    }
+    // BF16 networks run on the tensor cores when the shapes allow it;
+    // DNNMG_GRU_KERNEL=simt selects the CUDA-core kernel (same arithmetic).
+    const char *which = getenv("DNNMG_GRU_KERNEL");
+    if (precision == DNNMG_BF16NET && !(which && strcmp(which, "simt") == 0)) {
+        if (!tc_prepare(*n, Wx, Uh, Wfc)) cudaGetLastError();
     }
     *out = n;
     return DNNMG_OK;
@@ -451,6 +482,8 @@ int dnnmg_net_destroy(dnnmg_net_t net) {
     cudaFree(net->UhT);
     cudaFree(net->WfcT);
     cudaFree(net->tc_weights);
+    cudaFree(net->d_status);
+    tc_release(*net);
     delete net;
     return DNNMG_OK;
 }
@@ -480,6 +513,8 @@ int dnnmg_gru_step(dnnmg_net_t net, const void *X, void *h, void *d, int P, cuda
     if (P < 0) return fail(DNNMG_EINVAL, "P=%d < 0", P);
     if (P == 0) return DNNMG_OK;
     if (!X || !h || !d) return fail(DNNMG_EINVAL, "NULL array");
+    if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(h) % 16)
+        return fail(DNNMG_EINVAL, "X and h must be 16-byte aligned");
     DNNMG_CUDA_TRY(launch_gru(*net, X, h, d, P, stream));
     return DNNMG_OK;
 }
@@ -503,6 +538,25 @@ int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *b
     DNNMG_CUDA_TRY(launch_restrict(mesh->g, mesh->info.precision, bf, bc, stream));
     return DNNMG_OK;
 }
+
+int dnnmg_restrict(dnnmg_mesh_t mesh, const void *bf, double *bc, cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if (!bf || !bc) return fail(DNNMG_EINVAL, "NULL array");
+    DNNMG_CUDA_TRY(launch_restrict(mesh->g, mesh->info.precision, bf, bc, stream));
+    return DNNMG_OK;
+}
+
+int dnnmg_net_status(dnnmg_net_t net, int *status, int reset) {
+    clear_error();
+    if (!net || !status) return fail(DNNMG_EINVAL, "NULL argument");
+    if (int e = check_device(net->device)) return e;
+    DNNMG_CUDA_TRY(cudaMemcpy(status, net->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (reset) DNNMG_CUDA_TRY(cudaMemset(net->d_status, 0, sizeof(int)));
+    return DNNMG_OK;
+}
+
+int dnnmg_net_uses_tensor_cores(dnnmg_net_t net) { return net && net->tc ? 1 : 0; }
 
 static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, void *workspace,
                        size_t workspace_bytes) {
@@ -567,6 +621,7 @@ int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net) {
 
 namespace dnnmg {
 cudaError_t launch_gru(const Net &net, const void *X, void *h, void *d, int P, cudaStream_t st) {
+    if (net.tc) return launch_gru_tc(net, X, h, d, P, st);
     return launch_gru_cuda_core(net, X, h, d, P, st);
 }
 int gru_launch_count(const Net &) { return 1; }

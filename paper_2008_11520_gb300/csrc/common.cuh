@@ -45,6 +45,7 @@ struct MeshGeom {
     const uint8_t *solid;         // device [nyc][nxc], 1 = solid coarse cell
     const int *patch_id;          // device [npy][npx], fluid patch number or -1
     const int *patch_cell;        // device [P], pj npx + pi
+    const int *feat_tab;          // device [ldx], source of each feature column (stencil.cu)
 };
 
 // Element constants of one fine cell (local nodes SW, SE, NW, NE) and of one
@@ -76,11 +77,14 @@ struct Mesh {
     uint8_t *d_solid;
     int *d_patch_id;
     int *d_patch_cell;
+    int *d_feat_tab;
 };
 
 struct Net {
     int n_in, ldx, H, n_out, precision;
     int device;
+    int *d_status;                // device status word (DNNMG_DEVERR_* bits)
+    void *tc;                     // tensor-core schedule (gru_tc.cu), null if not used
     // transposed weights for the CUDA-core kernel: WxT [ldx][3H], UhT [H][3H], WfcT [H][n_out]
     void *WxT, *UhT, *WfcT;
     // K-major bf16 operands for the tensor-core kernel (BF16NET only, may be null)
@@ -108,5 +112,11 @@ cudaError_t launch_mesh_maps(const MeshGeom &g, unsigned char *flags, unsigned c
                              cudaStream_t st);
 cudaError_t launch_gru(const Net &net, const void *X, void *h, void *d, int P, cudaStream_t st);
 int gru_launch_count(const Net &net);
+cudaError_t launch_gru_cuda_core(const Net &n, const void *X, void *h, void *d, int P, cudaStream_t st);
+cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, cudaStream_t st);
+bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc);
+void tc_release(Net &n);
+// Per feature column: (kind << 24) | offset into the residual / node tiles of stencil.cu.
+void feature_table(const MeshGeom &g, int *tab);
 
 }  // namespace dnnmg

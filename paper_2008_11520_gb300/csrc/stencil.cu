@@ -55,36 +55,52 @@ __device__ __forceinline__ NodeClass classify_global(const MeshGeom &g, int I, i
 }
 
 // ------------------------------------------------------------------ S1
-// One thread per fine node; bilinear weights a/r are exact binary fractions.
+// A CTA owns 64 x 16 fine nodes; the coarse nodes they need are converted to
+// the fine type once and staged in shared memory, so the interpolation runs
+// in the fine arithmetic type (FP64 throughput on GB300 is 1/64 of FP32).
+constexpr int PTX = 64, PTY = 16;
+constexpr int PCX = PTX / 2 + 2, PCY = PTY / 2 + 2;   // coarse nodes of a tile for r >= 2
+
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
 k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, double inflow_scale) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y;
-    if (I > g.nxf) return;
-    const int ci = min(I >> g.K, g.nxc - 1), cj = min(J >> g.K, g.nyc - 1);
-    const double a = (double)(I - (ci << g.K)) / g.r;
-    const double b = (double)(J - (cj << g.K)) / g.r;
+    __shared__ T cs[3][PCY][PCX];
+    const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
+    const int ci0 = min(I0 >> g.K, g.nxc - 1), cj0 = min(J0 >> g.K, g.nyc - 1);
     const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
+    for (int e = threadIdx.x; e < 3 * PCY * PCX; e += blockDim.x) {
+        const int c = e / (PCY * PCX), rem = e - c * (PCY * PCX);
+        const int jj = rem / PCX, ii = rem - jj * PCX;
+        const int ci = ci0 + ii, cj = cj0 + jj;
+        T v = T(0);
+        if (ci <= g.nxc && cj <= g.nyc) v = (T)__ldg(xc + c * Nc + (size_t)cj * nc1 + ci);
+        cs[c][jj][ii] = v;
+    }
+    __syncthreads();
     const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
-    const size_t c00 = (size_t)cj * nc1 + ci;
-    double val[3];
+    const T inv_r = T(1) / T(g.r);   // exact: r is a power of two
+    for (int e = threadIdx.x; e < PTX * PTY; e += blockDim.x) {
+        const int I = I0 + (e % PTX), J = J0 + e / PTX;
+        if (I > g.nxf || J > g.nyf) continue;
+        const int ci = min(I >> g.K, g.nxc - 1), cj = min(J >> g.K, g.nyc - 1);
+        const T a = T(I - (ci << g.K)) * inv_r, b = T(J - (cj << g.K)) * inv_r;
+        const int li = ci - ci0, lj = cj - cj0;
+        T val[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double *f = xc + c * Nc;
-        val[c] = (1 - a) * (1 - b) * __ldg(f + c00) + a * (1 - b) * __ldg(f + c00 + 1) +
-                 (1 - a) * b * __ldg(f + c00 + nc1) + a * b * __ldg(f + c00 + nc1 + 1);
+        for (int c = 0; c < 3; ++c)
+            val[c] = (T(1) - a) * (T(1) - b) * cs[c][lj][li] + a * (T(1) - b) * cs[c][lj][li + 1] +
+                     (T(1) - a) * b * cs[c][lj + 1][li] + a * b * cs[c][lj + 1][li + 1];
+        const NodeClass nc = classify_global(g, I, J);
+        if (nc.dirichlet) {
+            const double y = J * g.hyf;
+            val[0] = nc.inflow ? (T)(g.u_max * 4.0 * y * (g.ly - y) / (g.ly * g.ly) * inflow_scale) : T(0);
+            val[1] = T(0);
+        }
+        const size_t node = (size_t)J * nxn + I;
+        xf[node] = val[0];
+        xf[Nf + node] = val[1];
+        xf[2 * Nf + node] = val[2];
     }
-    NodeClass nc = classify_global(g, I, J);
-    if (nc.dirichlet) {
-        const double y = J * g.hyf;
-        val[0] = nc.inflow ? g.u_max * 4.0 * y * (g.ly - y) / (g.ly * g.ly) * inflow_scale : 0.0;
-        val[1] = 0.0;
-    }
-    const size_t node = (size_t)J * nxn + I;
-    xf[node] = (T)val[0];
-    xf[Nf + node] = (T)val[1];
-    xf[2 * Nf + node] = (T)val[2];
 }
 
 // ------------------------------------------------------------------ S2 + S3
@@ -105,6 +121,8 @@ struct ResLayout {
         return sizeof(T) * (XS + BS + CC + LC + RS) + FX * FY;
     }
 };
+
+enum { FEAT_RES = 0, FEAT_VEL = 1, FEAT_PECLET = 2, FEAT_GEO = 3, FEAT_ZERO = 4 };
 
 template <typename T, typename TX>
 __global__ void __launch_bounds__(NTHREADS)
@@ -273,32 +291,37 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
     __syncthreads();
 
     // Phase C: one feature row per fluid patch of the tile (Sec. 5.2 inputs).
-    const int S = g.S, S1 = S + 1, s1 = g.s + 1, nf = g.nf, nc = g.nc;
+    // feat_tab[c] says where column c comes from relative to the patch origin.
+    const int S = g.S;
     const int tpx = TXC / S, tpy = TYC / S;
     const int pi0 = I0 / S, pj0 = J0 / S;
-    const int total = tpx * tpy * g.ldx;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int tp = e / g.ldx, c = e - tp * g.ldx;
+    for (int tp = 0; tp < tpx * tpy; ++tp) {
         const int lpy = tp / tpx, lpx = tp - lpy * tpx;
         const int pi = pi0 + lpx, pj = pj0 + lpy;
         if (pi >= g.npx || pj >= g.npy) continue;
         const int id = g.patch_id[pj * g.npx + pi];
         if (id < 0) continue;
-        T val = T(0);
-        if (c < 3 * nf) {
-            const int comp = c / nf, k = c - comp * nf;
-            const int b = k / S1, a = k - b * S1;
-            val = rs[comp * NYN * NXN + (lpy * S + b) * NXN + lpx * S + a];
-        } else if (c < 3 * nf + 3 * nc) {
-            const int k0 = c - 3 * nf, comp = k0 / nc, k = k0 - comp * nc;
-            const int b = k / s1, a = k - b * s1;
-            const int hi = lpx * S + a * g.r + 2, hj = lpy * S + b * g.r + 2;
-            const T u = xs[hj * L::HX + hi], v = xs[L::HY * L::HX + hj * L::HX + hi];
-            val = comp == 0 ? u : (comp == 1 ? v : fc.q_over_nu * sqrt(u * u + v * v));
-        } else if (c < g.n_in) {
-            val = fc.geo[c - 3 * nf - 3 * nc];
+        const T *rbase = rs + lpy * S * NXN + lpx * S;
+        const T *xbase = xs + lpy * S * L::HX + lpx * S;
+        TX *row = X + (size_t)id * g.ldx;
+        for (int c = threadIdx.x; c < g.ldx; c += blockDim.x) {
+            const int e = __ldg(g.feat_tab + c);
+            const int kind = e >> 24, off = e & 0xFFFFFF;
+            T val;
+            if (kind == FEAT_RES) {
+                val = rbase[off];
+            } else if (kind == FEAT_VEL) {
+                val = xbase[off];
+            } else if (kind == FEAT_PECLET) {
+                const T u = xbase[off], v = xbase[off + L::HY * L::HX];
+                val = fc.q_over_nu * sqrt(u * u + v * v);
+            } else if (kind == FEAT_GEO) {
+                val = fc.geo[off];
+            } else {
+                val = T(0);
+            }
+            row[c] = store_as<TX, T>(val);
         }
-        X[(size_t)id * g.ldx + c] = store_as<TX, T>(val);
     }
 }
 
@@ -459,44 +482,108 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
 }
 
 // ------------------------------------------------------------------ S7
-// One thread per coarse node: b_c(J) = sum_i hat_J(x_i) b_f(i) in double.
-template <typename T>
+// b_c(J) = sum_i hat_J(x_i) b_f(i), separable: first along x within each fine
+// row, then along y.  A CTA owns (128/r) x (32/r) coarse nodes and stages the
+// fine rows they need.  Single-precision data are accumulated with error-free
+// transformations (a float hi/lo pair: TwoProd by FMA and TwoSum, Dekker /
+// Knuth), i.e. to about 2^-44 relative of the sum of magnitudes, and the
+// result is stored in FP64; FP64 data are accumulated in FP64.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_fma(DF &acc, float w, float x) {
+    const float p = __fmul_rn(w, x);
+    const float pe = __fmaf_rn(w, x, -p);              // exact product error
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ void df_fma(DF &acc, float w, DF x) {
+    df_fma(acc, w, x.hi);
+    acc.lo = __fmaf_rn(w, x.lo, acc.lo);
+}
+
+struct RestrictAcc32 {
+    using Row = DF;
+    static __device__ __forceinline__ Row zero() { return DF{0.f, 0.f}; }
+    static __device__ __forceinline__ void add(Row &a, float w, float x) { df_fma(a, w, x); }
+    static __device__ __forceinline__ void add(Row &a, float w, Row x) { df_fma(a, w, x); }
+    static __device__ __forceinline__ double out(Row a) { return (double)a.hi + (double)a.lo; }
+};
+struct RestrictAcc64 {
+    using Row = double;
+    static __device__ __forceinline__ Row zero() { return 0.0; }
+    static __device__ __forceinline__ void add(Row &a, double w, double x) { a += w * x; }
+    static __device__ __forceinline__ double out(Row a) { return a; }
+};
+
+template <typename T, typename Acc>
 __global__ void __launch_bounds__(NTHREADS)
 k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
-    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cj = blockIdx.y;
-    if (ci > g.nxc) return;
+    using Row = typename Acc::Row;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int r = g.r;
+    const int TCX = 128 / r, TCY = 32 / r;           // coarse nodes per tile
+    const int FW = TCX * r + r - 1, FH = TCY * r + r - 1;   // fine nodes staged
+    T *fs = reinterpret_cast<T *>(smem_raw);         // [2][FH][FW]
+    Row *rs = reinterpret_cast<Row *>(fs + 2 * FH * FW);   // [2][FH][TCX] x-restricted rows
+    const int ci0 = blockIdx.x * TCX, cj0 = blockIdx.y * TCY;
+    const int I0 = ci0 * r - (r - 1), J0 = cj0 * r - (r - 1);
     const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
-    const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
-    const int Ic = ci * r, Jc = cj * r;
-    double su = 0.0, sv = 0.0;
-    for (int dj = -(r - 1); dj <= r - 1; ++dj) {
-        const int J = Jc + dj;
-        if (J < 0 || J > g.nyf) continue;
-        double ru = 0.0, rv = 0.0;
-        for (int di = -(r - 1); di <= r - 1; ++di) {
-            const int I = Ic + di;
-            if (I < 0 || I > g.nxf) continue;
-            const double wx = (double)(r - abs(di)) / r;
-            ru += wx * (double)bf[(size_t)J * nxn + I];
-            rv += wx * (double)bf[Nf + (size_t)J * nxn + I];
-        }
-        const double wy = (double)(r - abs(dj)) / r;
-        su += wy * ru;
-        sv += wy * rv;
+    for (int e = threadIdx.x; e < 2 * FH * FW; e += blockDim.x) {
+        const int c = e / (FH * FW), rem = e - c * (FH * FW);
+        const int jj = rem / FW, ii = rem - jj * FW;
+        const int I = I0 + ii, J = J0 + jj;
+        T v = T(0);
+        if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf) v = bf[c * Nf + (size_t)J * nxn + I];
+        fs[e] = v;
     }
-    bool ts = false;
-    for (int dj = -1; dj <= 0; ++dj)
-        for (int di = -1; di <= 0; ++di) {
-            const int i = ci + di, j = cj + dj;
-            if (i >= 0 && j >= 0 && i < g.nxc && j < g.nyc && g.solid[(size_t)j * g.nxc + i]) ts = true;
+    __syncthreads();
+    const T inv_r = T(1) / T(r);
+    for (int e = threadIdx.x; e < 2 * FH * TCX; e += blockDim.x) {
+        const int c = e / (FH * TCX), rem = e - c * (FH * TCX);
+        const int jj = rem / TCX, ci = rem - jj * TCX;
+        const T *row = fs + c * FH * FW + jj * FW + ci * r;   // fine nodes ci*r-(r-1) .. ci*r+(r-1)
+        Row acc = Acc::zero();
+        for (int d = 0; d < 2 * r - 1; ++d) Acc::add(acc, T(r - abs(d - (r - 1))) * inv_r, row[d]);
+        rs[e] = acc;
+    }
+    __syncthreads();
+    const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
+    for (int e = threadIdx.x; e < TCX * TCY; e += blockDim.x) {
+        const int lj = e / TCX, li = e - lj * TCX;
+        const int ci = ci0 + li, cj = cj0 + lj;
+        if (ci > g.nxc || cj > g.nyc) continue;
+        double out[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            Row acc = Acc::zero();
+            for (int d = 0; d < 2 * r - 1; ++d)
+                Acc::add(acc, T(r - abs(d - (r - 1))) * inv_r, rs[c * FH * TCX + (lj * r + d) * TCX + li]);
+            out[c] = Acc::out(acc);
         }
-    if (ts || ci == 0 || cj == 0 || cj == g.nyc) su = sv = 0.0;
-    const size_t node = (size_t)cj * nc1 + ci;
-    bc[node] = su;
-    bc[Nc + node] = sv;
-    bc[2 * Nc + node] = 0.0;
+        bool ts = false;
+        for (int dj = -1; dj <= 0; ++dj)
+            for (int di = -1; di <= 0; ++di) {
+                const int i = ci + di, j = cj + dj;
+                if (i >= 0 && j >= 0 && i < g.nxc && j < g.nyc && g.solid[(size_t)j * g.nxc + i]) ts = true;
+            }
+        if (ts || ci == 0 || cj == 0 || cj == g.nyc) out[0] = out[1] = 0.0;
+        const size_t node = (size_t)cj * nc1 + ci;
+        bc[node] = out[0];
+        bc[Nc + node] = out[1];
+        bc[2 * Nc + node] = 0.0;
+    }
+}
+
+template <typename T, typename Acc>
+size_t restrict_smem(int r) {
+    const int FW = 128 + r - 1, FH = 32 + r - 1;
+    return 2 * FH * FW * sizeof(T) + 2 * FH * (128 / r) * sizeof(typename Acc::Row);
 }
 
 // ------------------------------------------------------------------ maps
@@ -536,14 +623,35 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 
 }  // namespace
 
+// Column sources of a feature row, in the order of Sec. 5.2 inputs:
+// residual (u, v, p) on the fine patch nodes, v~ (u, v) and the Peclet number
+// on the coarse patch nodes, 12 geometry values, zero padding to ldx.
+void feature_table(const MeshGeom &g, int *tab) {
+    using L = ResLayout;
+    const int S1 = g.S + 1, s1 = g.s + 1;
+    int c = 0;
+    for (int comp = 0; comp < 3; ++comp)
+        for (int b = 0; b < S1; ++b)
+            for (int a = 0; a < S1; ++a) tab[c++] = (FEAT_RES << 24) | (comp * NYN * NXN + b * NXN + a);
+    for (int comp = 0; comp < 3; ++comp)
+        for (int b = 0; b < s1; ++b)
+            for (int a = 0; a < s1; ++a) {
+                const int off = (b * g.r + 2) * L::HX + a * g.r + 2;
+                tab[c++] = comp < 2 ? (FEAT_VEL << 24) | (comp * L::HY * L::HX + off) : (FEAT_PECLET << 24) | off;
+            }
+    for (int k = 0; k < 12; ++k) tab[c++] = (FEAT_GEO << 24) | k;
+    while (c < g.ldx) tab[c++] = FEAT_ZERO << 24;
+}
+
 cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, void *xf, double t,
                               cudaStream_t st) {
     double w = 1.0;
     if (g.ramp) w = t <= 0.5 ? 0.5 - 0.5 * cos(2.0 * 3.14159265358979323846 * t) : 1.0;
+    const dim3 grid((unsigned)((g.nxf + PTX) / PTX), (unsigned)((g.nyf + PTY) / PTY));
     if (prec == DNNMG_F64)
-        k_prolongate<double><<<node_grid(g), NTHREADS, 0, st>>>(g, xc, (double *)xf, w);
+        k_prolongate<double><<<grid, NTHREADS, 0, st>>>(g, xc, (double *)xf, w);
     else
-        k_prolongate<float><<<node_grid(g), NTHREADS, 0, st>>>(g, xc, (float *)xf, w);
+        k_prolongate<float><<<grid, NTHREADS, 0, st>>>(g, xc, (float *)xf, w);
     return cudaGetLastError();
 }
 
@@ -601,11 +709,18 @@ cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
 
 cudaError_t launch_restrict(const MeshGeom &g, int prec, const void *bf, double *bc,
                             cudaStream_t st) {
-    dim3 grid((unsigned)((g.nxc + 1 + NTHREADS - 1) / NTHREADS), (unsigned)(g.nyc + 1));
-    if (prec == DNNMG_F64)
-        k_restrict<double><<<grid, NTHREADS, 0, st>>>(g, (const double *)bf, bc);
-    else
-        k_restrict<float><<<grid, NTHREADS, 0, st>>>(g, (const float *)bf, bc);
+    const int TCX = 128 / g.r, TCY = 32 / g.r;
+    const dim3 grid((unsigned)((g.nxc + TCX) / TCX), (unsigned)((g.nyc + TCY) / TCY));
+    cudaError_t e;
+    if (prec == DNNMG_F64) {
+        const size_t sm = restrict_smem<double, RestrictAcc64>(g.r);
+        if ((e = set_smem(k_restrict<double, RestrictAcc64>, sm)) != cudaSuccess) return e;
+        k_restrict<double, RestrictAcc64><<<grid, NTHREADS, sm, st>>>(g, (const double *)bf, bc);
+    } else {
+        const size_t sm = restrict_smem<float, RestrictAcc32>(g.r);
+        if ((e = set_smem(k_restrict<float, RestrictAcc32>, sm)) != cudaSuccess) return e;
+        k_restrict<float, RestrictAcc32><<<grid, NTHREADS, sm, st>>>(g, (const float *)bf, bc);
+    }
     return cudaGetLastError();
 }
 

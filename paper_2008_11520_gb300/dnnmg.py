@@ -75,6 +75,9 @@ def _load():
         "dnnmg_step": [P, P, P, P, P, P, P, S, D, P],
         "dnnmg_step_host": [P, P, P, P, P, P, P, S, D, P],
         "dnnmg_step_launches": [P, P],
+        "dnnmg_restrict": [P, P, P, P],
+        "dnnmg_net_status": [P, ctypes.POINTER(ctypes.c_int), I],
+        "dnnmg_net_uses_tensor_cores": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -262,6 +265,24 @@ def dnnmg_rhs_restrict(mesh, vcorr, bf, bc, stream=None):
     _need(bf, mesh.real, 2 * I.Nf, "bf")
     _need(bc, torch.float64, 3 * I.Nc, "bc")
     _check(_lib.dnnmg_rhs_restrict(mesh.handle, _ptr(vcorr), _ptr(bf), _ptr(bc), _stream(stream)))
+
+
+def dnnmg_restrict(mesh, bf, bc, stream=None):
+    I = mesh.info
+    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(bc, torch.float64, 3 * I.Nc, "bc")
+    _check(_lib.dnnmg_restrict(mesh.handle, _ptr(bf), _ptr(bc), _stream(stream)))
+
+
+def dnnmg_net_status(net, reset=False):
+    """Device status word of the network (0 = no kernel wait ran out of time)."""
+    st = ctypes.c_int(0)
+    _check(_lib.dnnmg_net_status(net.handle, ctypes.byref(st), 1 if reset else 0))
+    return st.value
+
+
+def dnnmg_net_uses_tensor_cores(net):
+    return bool(_lib.dnnmg_net_uses_tensor_cores(net.handle))
 
 
 def dnnmg_step(mesh, net, xc, h, bf, bc, workspace, t, stream=None):

@@ -1,0 +1,123 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (dnnmg_step on the whole mesh).
+
+* 256 x 64 coarse cells, K = 2, H = 64 (FP32 and BF16 networks): the oracle
+  runs on the whole mesh.
+* 2048 x 512 coarse cells, K = 2, 2 x 2-cell patches, H = 128, BF16: the
+  oracle computes sampled outputs -- it runs on windows of the global mesh
+  (obstacle, inflow, outflow corner, interior), and results are compared
+  where the window's cut edges cannot reach within the steps taken.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import TOL, Params, rel_l2
+from oracle import fem, step as ostep
+from oracle.mesh import Mesh as OMesh
+from paper_2008_11520_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+PRM = Params()
+
+
+@pytest.fixture(scope="module")
+def dn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_11520_gb300 import dnnmg
+    return dnnmg
+
+
+def gpu_run(dn, c, prec, steps, xc_t, v0, h0):
+    mesh = dn.Mesh(dn.make_desc(c["nxc"], c["nyc"], c["K"], c["s"], c["ellipse"], precision=prec))
+    I = mesh.info
+    W = synth.net_weights(I.n_in, c["H"], I.n_out, seed=c["seed"])
+    net = dn.Net(*W, precision=prec)
+    real = mesh.real
+    bf = mesh.fine(2)
+    bc = mesh.coarse(3)
+    dn.dnnmg_rhs_restrict(mesh, torch.as_tensor(v0).to(real).cuda().contiguous(), bf, bc)
+    h = torch.as_tensor(h0).to(real).cuda().contiguous()
+    ws = mesh.workspace()
+    for n in range(steps):
+        dn.dnnmg_step(mesh, net, torch.as_tensor(xc_t[n]).cuda().contiguous(), h, bf, bc, ws, n * PRM.k)
+    torch.cuda.synchronize()
+    out = {"h": h.double().cpu().numpy(), "bf": bf.double().cpu().numpy(), "bc": bc.cpu().numpy()}
+    assert dn.dnnmg_net_status(net) == 0
+    return mesh, W, out
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_channel256_whole_mesh(dn, prec):
+    c = synth.config("channel256")
+    spec = synth.FlowSpec.from_seed(c["seed"], c["ellipse"])
+    om = OMesh(c["nxc"], c["nyc"], c["K"], c["s"], ellipse=c["ellipse"])
+    steps = 2
+    xc_t = [synth.coarse_state(spec, c["nxc"], c["nyc"], n * PRM.k) for n in range(steps)]
+    v0 = synth.fine_state(spec, om.nxf, om.nyf, 0.0, perturb_seed=3)[:2].astype(np.float32).astype(np.float64)
+    h0 = synth.hidden_state(om.P, c["H"], seed=5).astype(np.float32).astype(np.float64)
+    mesh, W, got = gpu_run(dn, c, prec, steps, xc_t, v0, h0)
+    assert mesh.info.P == om.P
+    h, bf = h0, fem.rhs(om, PRM, v0)
+    for n in range(steps):
+        out = ostep.dnnmg_step(om, PRM, W, xc_t[n], h, bf, n * PRM.k)
+        h, bf = out["h"], out["bf"]
+    tol = TOL[prec]
+    assert rel_l2(got["h"], out["h"]) <= tol
+    assert rel_l2(got["bf"].reshape(2, -1), out["bf"]) <= tol
+    assert rel_l2(got["bc"].reshape(3, -1), out["bc"]) <= tol
+
+
+WINDOWS = {  # coarse-cell windows of the 2048 x 512 mesh (multiples of the patch size)
+    "obstacle": (216, 236, 248, 268),     # straddles the ellipse edge x = 0.25
+    "inflow": (0, 100, 32, 132),
+    "outflow_corner": (2016, 480, 2048, 512),
+    "interior": (1000, 200, 1032, 232),
+}
+
+
+def test_large_sampled_windows(dn):
+    c = synth.config("large")
+    spec = synth.FlowSpec.from_seed(c["seed"], c["ellipse"])
+    r = 2 ** c["K"]
+    steps = 2
+    full = OMesh(c["nxc"], c["nyc"], c["K"], c["s"], ellipse=c["ellipse"])
+    xc_t = [synth.coarse_state(spec, c["nxc"], c["nyc"], n * PRM.k) for n in range(steps)]
+    v0 = synth.fine_state(spec, full.nxf, full.nyf, 0.0)[:2].astype(np.float32).astype(np.float64)
+    h0 = synth.hidden_state(full.P, c["H"], seed=7).astype(np.float32).astype(np.float64)
+    mesh, W, got = gpu_run(dn, c, "bf16", steps, xc_t, v0, h0)
+    assert mesh.info.P == full.P
+    nxn_c, nxn_f = c["nxc"] + 1, full.nxf + 1
+    bc_g = got["bc"].reshape(3, c["nyc"] + 1, nxn_c)
+    bf_g = got["bf"].reshape(2, full.nyf + 1, nxn_f)
+    margin_c = 8                                   # coarse nodes away from cut edges
+    for name, win in WINDOWS.items():
+        om = OMesh(c["nxc"], c["nyc"], c["K"], c["s"], ellipse=c["ellipse"], window=win)
+        ci0, cj0, ci1, cj1 = win
+        xcw = [x.reshape(3, c["nyc"] + 1, nxn_c)[:, cj0:cj1 + 1, ci0:ci1 + 1].reshape(3, -1) for x in xc_t]
+        v0w = v0.reshape(2, full.nyf + 1, nxn_f)[:, cj0 * r:cj1 * r + 1, ci0 * r:ci1 * r + 1].reshape(2, -1)
+        gidx = full.patch_global_index[om.patches[:, 1], om.patches[:, 0]]
+        h, bf = h0[gidx], fem.rhs(om, PRM, v0w)
+        for n in range(steps):
+            out = ostep.dnnmg_step(om, PRM, W, xcw[n], h, bf, n * PRM.k)
+            h, bf = out["h"], out["bf"]
+        # exact region: cut edges need a margin, domain edges do not
+        lo_i = 0 if ci0 == 0 else margin_c
+        lo_j = 0 if cj0 == 0 else margin_c
+        hi_i = (ci1 - ci0) + 1 - (0 if ci1 == c["nxc"] else margin_c)
+        hi_j = (cj1 - cj0) + 1 - (0 if cj1 == c["nyc"] else margin_c)
+        ref = out["bc"].reshape(3, cj1 - cj0 + 1, ci1 - ci0 + 1)[:2, lo_j:hi_j, lo_i:hi_i]
+        gbc = bc_g[:2, cj0 + lo_j:cj0 + hi_j, ci0 + lo_i:ci0 + hi_i]
+        assert rel_l2(gbc, ref) <= TOL["bf16"], name
+        fref = out["bf"].reshape(2, om.wyf + 1, om.wxf + 1)[:, lo_j * r:(hi_j - 1) * r + 1, lo_i * r:(hi_i - 1) * r + 1]
+        gbf = bf_g[:, cj0 * r + lo_j * r:cj0 * r + (hi_j - 1) * r + 1, ci0 * r + lo_i * r:ci0 * r + (hi_i - 1) * r + 1]
+        assert rel_l2(gbf, fref) <= TOL["bf16"], name
+        # hidden state of patches whose dependence stays inside the window
+        pi, pj = om.patches[:, 0], om.patches[:, 1]
+        s = c["s"]
+        inner = ((pi * s >= ci0 + lo_i) & ((pi + 1) * s <= ci0 + hi_i - 1)
+                 & (pj * s >= cj0 + lo_j) & ((pj + 1) * s <= cj0 + hi_j - 1))
+        assert inner.sum() > 0
+        assert rel_l2(got["h"][gidx[inner]], out["h"][inner]) <= TOL["bf16"], name

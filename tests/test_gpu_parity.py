@@ -295,3 +295,56 @@ def test_invalid_arguments_raise(dn):
     with pytest.raises(dn.DnnmgError):   # aliasing output
         v = m.fine(2)
         dn.dnnmg_rhs_restrict(m, v, v, m.coarse(3))
+
+
+@pytest.mark.parametrize("name", ["ragged_f32", "k2_f32", "k2s2_bf16", "k3_f64"])
+def test_restrict_fp64_class_accuracy(dn, name):
+    # R applied to the same single-precision vector: the GPU's float-pair
+    # accumulation must agree with the oracle's FP64 restriction to ~1e-13
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    bf = as_real(case, rhs_like(case, seed=41))
+    bc = m.coarse(3)
+    dn.dnnmg_restrict(m, cuda(bf, m.real), bc)
+    ref = transfer.restrict(om, bf)
+    assert rel_l2(host(bc).reshape(3, -1), ref) <= 1e-13
+
+
+GRU_SHAPES = [(51, 32, 18), (99, 64, 50), (99, 96, 50), (282, 128, 162), (60, 32, 40)]
+
+
+@pytest.mark.parametrize("shape", GRU_SHAPES)
+@pytest.mark.parametrize("P", [1, 127, 128, 300, 1000])
+def test_gru_tensor_cores_match_cuda_cores(dn, shape, P, monkeypatch):
+    # same BF16-operand arithmetic on the tcgen05 kernel and on CUDA cores;
+    # only the FP32 summation order differs
+    n_in, H, n_out = shape
+    rng = np.random.default_rng(P + H)
+    Wx, Uh, Wfc = (rng.normal(0, 0.1, s) for s in ((3 * H, n_in), (3 * H, H), (n_out, H)))
+    ldx = (n_in + 15) // 16 * 16
+    X = np.zeros((P, ldx))
+    X[:, :n_in] = rng.normal(0, 1.0, (P, n_in))
+    h0 = rng.uniform(-0.5, 0.5, (P, H))
+    tc = dn.Net(Wx, Uh, Wfc, "bf16")
+    assert dn.dnnmg_net_uses_tensor_cores(tc)
+    monkeypatch.setenv("DNNMG_GRU_KERNEL", "simt")
+    simt = dn.Net(Wx, Uh, Wfc, "bf16")
+    assert not dn.dnnmg_net_uses_tensor_cores(simt)
+    Xt = torch.as_tensor(X).to(torch.bfloat16).cuda()
+    outs = []
+    for net in (tc, simt):
+        h = torch.as_tensor(h0, dtype=torch.float32).cuda()
+        d = torch.full((P, n_out), float("nan"), dtype=torch.float32, device="cuda")
+        dn.dnnmg_gru_step(net, Xt, h, d, P)
+        torch.cuda.synchronize()
+        outs.append((h.cpu().numpy(), d.cpu().numpy()))
+    assert dn.dnnmg_net_status(tc) == 0
+    assert np.isfinite(outs[0][1]).all()
+    assert rel_l2(outs[0][0], outs[1][0]) <= 2e-3
+    assert rel_l2(outs[0][1], outs[1][1]) <= 2e-3
+    # and against the FP64 oracle within the BF16 tolerance
+    Xq = torch.as_tensor(X).to(torch.bfloat16).to(torch.float64).numpy()[:, :n_in]
+    h_ref, d_ref = gru.gru_step(Xq, h0.astype(np.float32).astype(np.float64), Wx, Uh, Wfc)
+    assert rel_l2(outs[0][0], h_ref) <= TOL["bf16"]
+    assert rel_l2(outs[0][1], d_ref) <= TOL["bf16"]
