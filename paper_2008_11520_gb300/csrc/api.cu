@@ -253,6 +253,28 @@ void fem_coefficients(const dnnmg_mesh_desc &d, FemCoef<double> *out) {
         f.geo[8 + c] = std::acos((ax * bx + ay * by) / (std::hypot(ax, ay) * std::hypot(bx, by)));
     }
     f.q_over_nu = d.s * std::fmax(d.lx / d.nxc, d.ly / d.nyc) / d.nu;
+    // node stencils: sum the element rows of the 4 cells around a node
+    auto stencil = [](const double E[4][4], double S[3][3]) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) S[i][j] = 0.0;
+        for (int cy = -1; cy <= 0; ++cy)
+            for (int cx = -1; cx <= 0; ++cx) {
+                const int a = -cx + 2 * (-cy);
+                for (int b = 0; b < 4; ++b) S[cy + (b >> 1) + 1][cx + (b & 1) + 1] += E[a][b];
+            }
+    };
+    stencil(f.Av, f.nA);
+    stencil(f.Bv, f.nB);
+    stencil(f.Gx, f.nGx);
+    stencil(f.Gy, f.nGy);
+    stencil(f.Dx, f.nDx);
+    stencil(f.Dy, f.nDy);
+    f.cg0 = gp[0];
+    f.cg1 = gp[1];
+    f.inv_hx = 1.0 / hx;
+    f.inv_hy = 1.0 / hy;
+    f.cwg0 = 0.5 * f.qw * gp[0];
+    f.cwg1 = 0.5 * f.qw * gp[1];
     (void)kPi;
 }
 

@@ -65,6 +65,13 @@ struct FemCoef {
     T qw;           // Gauss weight hx hy / 4
     T geo[12];      // patch geometry features
     T q_over_nu;    // Peclet scale: longest patch edge / nu
+    // node stencils [dy+1][dx+1] of interior nodes (4 fluid cells), assembled
+    // from the element matrices above
+    T nA[3][3], nB[3][3], nGx[3][3], nGy[3][3], nDx[3][3], nDy[3][3];
+    // tensor-product 2x2 Gauss evaluation of the convection term
+    T cg0, cg1;       // Gauss points on [0, 1]
+    T inv_hx, inv_hy;
+    T cwg0, cwg1;     // (qw / 2) * Gauss point
 };
 
 struct Mesh {

@@ -104,6 +104,73 @@ k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, doub
 }
 
 // ------------------------------------------------------------------ S2 + S3
+// 1/2 (v.grad v_c, phi_a) of one cell for its corners a = SW, SE, NW, NE, by
+// 2x2 Gauss in tensor-product form: values and derivatives at the 4 points
+// from edge interpolants, then the test-function sums one direction at a time.
+template <typename T>
+__device__ __forceinline__ void convection(const FemCoef<T> &fc, const T (&u)[4], const T (&v)[4], T (&cu)[4],
+                                           T (&cv)[4]) {
+    const T g0 = fc.cg0, g1 = fc.cg1;
+    // along x on the bottom (0, 1) and top (2, 3) edges
+    const T dub = u[1] - u[0], dut = u[3] - u[2], dvb = v[1] - v[0], dvt = v[3] - v[2];
+    const T ub[2] = {u[0] + g0 * dub, u[0] + g1 * dub}, ut[2] = {u[2] + g0 * dut, u[2] + g1 * dut};
+    const T vb[2] = {v[0] + g0 * dvb, v[0] + g1 * dvb}, vt[2] = {v[2] + g0 * dvt, v[2] + g1 * dvt};
+    // x-derivatives depend on eta only, y-derivatives on xi only
+    const T ux[2] = {dub + g0 * (dut - dub), dub + g1 * (dut - dub)};
+    const T vx[2] = {dvb + g0 * (dvt - dvb), dvb + g1 * (dvt - dvb)};
+    const T uy[2] = {ut[0] - ub[0], ut[1] - ub[1]};
+    const T vy[2] = {vt[0] - vb[0], vt[1] - vb[1]};
+    T c_u[2][2], c_v[2][2];   // [eta index j][xi index i]
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const T gj = j ? g1 : g0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const T U = (ub[i] + gj * uy[i]) * fc.inv_hx;
+            const T V = (vb[i] + gj * vy[i]) * fc.inv_hy;
+            c_u[j][i] = U * ux[j] + V * uy[i];
+            c_v[j][i] = U * vx[j] + V * vy[i];
+        }
+    }
+    // test with l_0(g) = 1 - g, l_1(g) = g (1 - g0 = g1), weights (qw / 2)
+    T su[2][2], sv[2][2];   // [j][ax]
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        su[j][0] = g1 * c_u[j][0] + g0 * c_u[j][1];
+        su[j][1] = g0 * c_u[j][0] + g1 * c_u[j][1];
+        sv[j][0] = g1 * c_v[j][0] + g0 * c_v[j][1];
+        sv[j][1] = g0 * c_v[j][0] + g1 * c_v[j][1];
+    }
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        cu[ax] = fc.cwg1 * su[0][ax] + fc.cwg0 * su[1][ax];
+        cu[2 + ax] = fc.cwg0 * su[0][ax] + fc.cwg1 * su[1][ax];
+        cv[ax] = fc.cwg1 * sv[0][ax] + fc.cwg0 * sv[1][ax];
+        cv[2 + ax] = fc.cwg0 * sv[0][ax] + fc.cwg1 * sv[1][ax];
+    }
+}
+
+// Stage rows of a node-field window into shared memory: rows `nrows` of width
+// `w` starting at global node (I0, J0), component planes of Nf nodes; zero
+// outside the mesh.  One warp per row keeps the index arithmetic per row.
+template <typename T>
+__device__ __forceinline__ void stage_rows(const MeshGeom &g, const T *__restrict__ src, size_t Nf, int ncomp,
+                                           int I0, int J0, int w, int nrows, T *dst) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const size_t nxn = (size_t)g.nxf + 1;
+    for (int rr = warp; rr < ncomp * nrows; rr += nw) {
+        const int c = rr / nrows, jj = rr - c * nrows;
+        const int J = J0 + jj;
+        T *d = dst + (size_t)rr * w;
+        const bool rowok = J >= 0 && J <= g.nyf;
+        const T *row = src + c * Nf + (size_t)(rowok ? J : 0) * nxn;
+        for (int ii = lane; ii < w; ii += 32) {
+            const int I = I0 + ii;
+            d[ii] = (rowok && I >= 0 && I <= g.nxf) ? row[I] : T(0);
+        }
+    }
+}
+
 // Shared-memory layout of the residual/feature tile (element counts).
 struct ResLayout {
     static constexpr int HX = NXN + 4, HY = NYN + 4;           // nodes with 2-node halo
@@ -140,29 +207,20 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
     const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
 
-    for (int idx = threadIdx.x; idx < L::XS; idx += blockDim.x) {
-        const int c = idx / (L::HY * L::HX), rem = idx - c * (L::HY * L::HX);
-        const int jj = rem / L::HX, ii = rem - jj * L::HX;
-        const int I = I0 - 2 + ii, J = J0 - 2 + jj;
-        T v = T(0);
-        if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf) v = xf[c * Nf + (size_t)J * nxn + I];
-        xs[idx] = v;
-    }
-    for (int idx = threadIdx.x; idx < L::BS; idx += blockDim.x) {
-        const int c = idx / (NYN * NXN), rem = idx - c * (NYN * NXN);
-        const int jj = rem / NXN, ii = rem - jj * NXN;
-        const int I = I0 + ii, J = J0 + jj;
-        T v = T(0);
-        if (I <= g.nxf && J <= g.nyf) v = bf[c * Nf + (size_t)J * nxn + I];
-        bs[idx] = v;
-    }
+    stage_rows(g, xf, Nf, 3, I0 - 2, J0 - 2, L::HX, L::HY, xs);
+    stage_rows(g, bf, Nf, 2, I0, J0, NXN, NYN, bs);
+    bool all_fluid = true;
     for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
         const int jj = idx / L::FX, ii = idx - jj * L::FX;
-        cf[idx] = (unsigned char)cell_code(g, I0 - 2 + ii, J0 - 2 + jj);
+        const int code = cell_code(g, I0 - 2 + ii, J0 - 2 + jj);
+        cf[idx] = (unsigned char)code;
+        all_fluid &= code == 1;
     }
-    __syncthreads();
+    // Fast tiles: every cell within two of the tile is fluid and exists, so
+    // no tile node is a boundary node and node stencils apply everywhere.
+    const bool fast = __syncthreads_and(all_fluid);
 
-    // Phase A: element contributions of every fluid cell (cells -1..TXC in x).
+    // Phase A: cell contributions (fast tiles: convection only)
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
         const int ci = cid % L::CX - 1, cj = cid / L::CX - 1;
         T out[12];
@@ -171,50 +229,42 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
         if (cf[(cj + 2) * L::FX + ci + 2] == 1) {
             const int base = (cj + 2) * L::HX + ci + 2;
             const int off[4] = {0, 1, L::HX, L::HX + 1};
-            T u[4], v[4], p[4];
+            T u[4], v[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 u[b] = xs[base + off[b]];
                 v[b] = xs[L::HY * L::HX + base + off[b]];
-                p[b] = xs[2 * L::HY * L::HX + base + off[b]];
             }
+            T cu[4], cv[4];
+            convection(fc, u, v, cu, cv);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                T au = T(0), av = T(0), ap = T(0);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    au += fc.Av[a][b] * u[b] - fc.Gx[a][b] * p[b];
-                    av += fc.Av[a][b] * v[b] - fc.Gy[a][b] * p[b];
-                    ap += fc.Dx[a][b] * u[b] + fc.Dy[a][b] * v[b];
-                }
-                out[a] = au;
-                out[4 + a] = av;
-                out[8 + a] = ap;
+                out[a] = cu[a];
+                out[4 + a] = cv[a];
             }
-            // convection 1/2 (v.grad v, phi_a) by 2x2 Gauss
+            if (!fast) {
+                T p[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                T uq = T(0), vq = T(0), ux = T(0), uy = T(0), vx = T(0), vy = T(0);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    uq += fc.qphi[q][b] * u[b];
-                    vq += fc.qphi[q][b] * v[b];
-                    ux += fc.qdx[q][b] * u[b];
-                    uy += fc.qdy[q][b] * u[b];
-                    vx += fc.qdx[q][b] * v[b];
-                    vy += fc.qdy[q][b] * v[b];
-                }
-                const T cu = T(0.5) * fc.qw * (uq * ux + vq * uy);
-                const T cv = T(0.5) * fc.qw * (uq * vx + vq * vy);
+                for (int b = 0; b < 4; ++b) p[b] = xs[2 * L::HY * L::HX + base + off[b]];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    out[a] += cu * fc.qphi[q][a];
-                    out[4 + a] += cv * fc.qphi[q][a];
+                    T au = T(0), av = T(0), ap = T(0);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        au += fc.Av[a][b] * u[b] - fc.Gx[a][b] * p[b];
+                        av += fc.Av[a][b] * v[b] - fc.Gy[a][b] * p[b];
+                        ap += fc.Dx[a][b] * u[b] + fc.Dy[a][b] * v[b];
+                    }
+                    out[a] += au;
+                    out[4 + a] += av;
+                    out[8 + a] = ap;
                 }
             }
         }
+        const int nk = fast ? 8 : 12;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) cc[k * L::NCELL + cid] = out[k];
+        for (int k = 0; k < 12; ++k)
+            if (k < nk) cc[k * L::NCELL + cid] = out[k];
     }
     // Phase A': LPS contributions of every 2x2-cell patch touching the tile.
     for (int lid = threadIdx.x; lid < L::NLPS; lid += blockDim.x) {
@@ -248,16 +298,31 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
         const int I = I0 + ii, J = J0 + jj;
         T ru = T(0), rv = T(0), rp = T(0);
         if (I <= g.nxf && J <= g.nyf) {
-            T Au = T(0), Av = T(0), Ap = T(0);
-            // cell (ci, cj) relative -> index (cj + 1) * CX + ci + 1; node is corner a of it
             const int cells[4] = {jj * L::CX + ii, jj * L::CX + ii + 1, (jj + 1) * L::CX + ii,
-                                  (jj + 1) * L::CX + ii + 1};  // cells SW of node .. NE of node
+                                  (jj + 1) * L::CX + ii + 1};   // cells SW, SE, NW, NE of the node
             const int corner[4] = {3, 2, 1, 0};
+            T Au = T(0), Av = T(0), Ap = T(0);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 Au += cc[corner[t] * L::NCELL + cells[t]];
                 Av += cc[(4 + corner[t]) * L::NCELL + cells[t]];
-                Ap += cc[(8 + corner[t]) * L::NCELL + cells[t]];
+            }
+            if (fast) {
+                const T *pu = xs + (jj + 1) * L::HX + ii + 1;      // node (ii-1, jj-1)
+                const T *pv = pu + L::HY * L::HX;
+                const T *pp = pv + L::HY * L::HX;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const T u = pu[dy * L::HX + dx], v = pv[dy * L::HX + dx], p = pp[dy * L::HX + dx];
+                        Au += fc.nA[dy][dx] * u - fc.nGx[dy][dx] * p;
+                        Av += fc.nA[dy][dx] * v - fc.nGy[dy][dx] * p;
+                        Ap += fc.nDx[dy][dx] * u + fc.nDy[dy][dx] * v;
+                    }
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) Ap += cc[(8 + corner[t]) * L::NCELL + cells[t]];
             }
             const int nmx = (ii & 1) ? 1 : 2, nmy = (jj & 1) ? 1 : 2;
             for (int ty = 0; ty < nmy; ++ty) {
@@ -269,15 +334,22 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
                     Ap += lc[(3 * b + a) * L::NLPS + (n + 1) * L::LX + m + 1];
                 }
             }
-            const NodeClass nc = classify(cf[(jj + 1) * L::FX + ii + 1], cf[(jj + 1) * L::FX + ii + 2],
-                                          cf[(jj + 2) * L::FX + ii + 1], cf[(jj + 2) * L::FX + ii + 2],
-                                          I, J, g.nyf);
-            if (!nc.dirichlet) {
+            bool dirichlet = false, p_active = true;
+            if (!fast) {
+                const NodeClass nc = classify(cf[(jj + 1) * L::FX + ii + 1], cf[(jj + 1) * L::FX + ii + 2],
+                                              cf[(jj + 2) * L::FX + ii + 1], cf[(jj + 2) * L::FX + ii + 2],
+                                              I, J, g.nyf);
+                dirichlet = nc.dirichlet;
+                p_active = nc.p_active;
+            }
+            if (!dirichlet) {
                 ru = bs[jj * NXN + ii] - Au;
                 rv = bs[NYN * NXN + jj * NXN + ii] - Av;
             }
-            if (nc.p_active) rp = -Ap;
-            if (rf) {
+            if (p_active) rp = -Ap;
+            // a node on the tile's right/top edge belongs to the next tile
+            // (which may take the other path): write owned nodes only
+            if (rf && (ii < TXC || I == g.nxf) && (jj < TYC || J == g.nyf)) {
                 const size_t node = (size_t)J * nxn + I;
                 rf[node] = ru;
                 rf[Nf + node] = rv;
@@ -290,12 +362,14 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
     }
     __syncthreads();
 
-    // Phase C: one feature row per fluid patch of the tile (Sec. 5.2 inputs).
+    // Phase C: one feature row per fluid patch of the tile (Sec. 5.2 inputs);
     // feat_tab[c] says where column c comes from relative to the patch origin.
+    // One warp per patch row; lanes write consecutive columns.
     const int S = g.S;
     const int tpx = TXC / S, tpy = TYC / S;
     const int pi0 = I0 / S, pj0 = J0 / S;
-    for (int tp = 0; tp < tpx * tpy; ++tp) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int tp = warp; tp < tpx * tpy; tp += nw) {
         const int lpy = tp / tpx, lpx = tp - lpy * tpx;
         const int pi = pi0 + lpx, pj = pj0 + lpy;
         if (pi >= g.npx || pj >= g.npy) continue;
@@ -304,7 +378,7 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
         const T *rbase = rs + lpy * S * NXN + lpx * S;
         const T *xbase = xs + lpy * S * L::HX + lpx * S;
         TX *row = X + (size_t)id * g.ldx;
-        for (int c = threadIdx.x; c < g.ldx; c += blockDim.x) {
+        for (int c = lane; c < g.ldx; c += 32) {
             const int e = __ldg(g.feat_tab + c);
             const int kind = e >> 24, off = e & 0xFFFFFF;
             T val;
@@ -394,19 +468,15 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
     const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
 
-    for (int idx = threadIdx.x; idx < L::VS; idx += blockDim.x) {
-        const int c = idx / (L::HY * L::HX), rem = idx - c * (L::HY * L::HX);
-        const int jj = rem / L::HX, ii = rem - jj * L::HX;
-        const int I = I0 - 1 + ii, J = J0 - 1 + jj;
-        T v = T(0);
-        if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf) v = vcorr[c * Nf + (size_t)J * nxn + I];
-        vs[idx] = v;
-    }
+    stage_rows(g, vcorr, Nf, 2, I0 - 1, J0 - 1, L::HX, L::HY, vs);
+    bool all_fluid = true;
     for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
         const int jj = idx / L::CX, ii = idx - jj * L::CX;
-        cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
+        const int code = cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
+        cf[idx] = (unsigned char)code;
+        all_fluid &= code == 1;
     }
-    __syncthreads();
+    const bool fast = __syncthreads_and(all_fluid);
 
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
         T out[8];
@@ -422,35 +492,24 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
                 u[b] = vs[base + off[b]];
                 v[b] = vs[L::HY * L::HX + base + off[b]];
             }
+            T cu[4], cv[4];
+            convection(fc, u, v, cu, cv);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                T bu = T(0), bv = T(0);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    bu += fc.Bv[a][b] * u[b];
-                    bv += fc.Bv[a][b] * v[b];
-                }
-                out[a] = bu;
-                out[4 + a] = bv;
+                out[a] = -cu[a];
+                out[4 + a] = -cv[a];
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                T uq = T(0), vq = T(0), ux = T(0), uy = T(0), vx = T(0), vy = T(0);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    uq += fc.qphi[q][b] * u[b];
-                    vq += fc.qphi[q][b] * v[b];
-                    ux += fc.qdx[q][b] * u[b];
-                    uy += fc.qdy[q][b] * u[b];
-                    vx += fc.qdx[q][b] * v[b];
-                    vy += fc.qdy[q][b] * v[b];
-                }
-                const T cu = T(0.5) * fc.qw * (uq * ux + vq * uy);
-                const T cv = T(0.5) * fc.qw * (uq * vx + vq * vy);
+            if (!fast) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    out[a] -= cu * fc.qphi[q][a];
-                    out[4 + a] -= cv * fc.qphi[q][a];
+                    T bu = T(0), bv = T(0);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        bu += fc.Bv[a][b] * u[b];
+                        bv += fc.Bv[a][b] * v[b];
+                    }
+                    out[a] += bu;
+                    out[4 + a] += bv;
                 }
             }
         }
@@ -463,6 +522,8 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
         const int jj = nid / NXN, ii = nid - jj * NXN;
         const int I = I0 + ii, J = J0 + jj;
         if (I > g.nxf || J > g.nyf) continue;
+        // a node on the tile's right/top edge belongs to the next tile
+        if ((ii == TXC && I < g.nxf) || (jj == TYC && J < g.nyf)) continue;
         const int cells[4] = {jj * L::CX + ii, jj * L::CX + ii + 1, (jj + 1) * L::CX + ii,
                               (jj + 1) * L::CX + ii + 1};
         const int corner[4] = {3, 2, 1, 0};
@@ -472,9 +533,20 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
             bu += cc[corner[t] * L::NCELL + cells[t]];
             bv += cc[(4 + corner[t]) * L::NCELL + cells[t]];
         }
-        const NodeClass nc = classify(cf[cells[0]], cf[cells[1]], cf[cells[2]], cf[cells[3]], I, J,
-                                      g.nyf);
-        if (nc.dirichlet) bu = bv = T(0);
+        if (fast) {
+            const T *pu = vs + jj * L::HX + ii;   // node (ii-1, jj-1)
+            const T *pv = pu + L::HY * L::HX;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    bu += fc.nB[dy][dx] * pu[dy * L::HX + dx];
+                    bv += fc.nB[dy][dx] * pv[dy * L::HX + dx];
+                }
+        } else {
+            const NodeClass nc = classify(cf[cells[0]], cf[cells[1]], cf[cells[2]], cf[cells[3]], I, J, g.nyf);
+            if (nc.dirichlet) bu = bv = T(0);
+        }
         const size_t node = (size_t)J * nxn + I;
         bf[node] = bu;
         bf[Nf + node] = bv;
