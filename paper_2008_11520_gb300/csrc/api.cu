@@ -535,8 +535,9 @@ int dnnmg_gru_step(dnnmg_net_t net, const void *X, void *h, void *d, int P, cuda
     if (P < 0) return fail(DNNMG_EINVAL, "P=%d < 0", P);
     if (P == 0) return DNNMG_OK;
     if (!X || !h || !d) return fail(DNNMG_EINVAL, "NULL array");
-    if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(h) % 16)
-        return fail(DNNMG_EINVAL, "X and h must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(h) % 16 ||
+        reinterpret_cast<uintptr_t>(d) % 16)
+        return fail(DNNMG_EINVAL, "X, h and d must be 16-byte aligned");
     DNNMG_CUDA_TRY(launch_gru(*net, X, h, d, P, stream));
     return DNNMG_OK;
 }

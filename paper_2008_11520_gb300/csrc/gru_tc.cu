@@ -11,11 +11,15 @@
 //   phase 3:  D3 = h' W_fc^T                         (reuses the D1 columns)
 //   epilogue: d <- D3
 //
-// Warp roles (320 threads): warp 0 lane 0 issues the TMA load of the X tile
-// and streams the weights; warp 1 owns the tensor memory and one lane issues
-// every MMA; warps 2..9 are the epilogue, two warps per TMEM lane quadrant,
-// each owning half of the state columns of its 32 rows.  The epilogue keeps
-// its rows of h (FP32) in registers for the whole tile.
+// Warp roles (320 threads): warp 0 lane 0 issues the TMA loads of the X and
+// h tiles and streams the weights; warp 1 owns the tensor memory and one lane
+// issues every MMA; warps 2..9 are the epilogue, two warps per TMEM lane
+// quadrant, each owning half of the state columns of its 32 rows.  The
+// epilogue keeps its rows of h (FP32) in registers for the whole tile.
+// Global traffic is whole tiles: h arrives by TMA (swizzled 32-column boxes
+// placed in the last weight-ring stages before the weights need them), h'
+// leaves by TMA from the X region (idle after phase 1), and d is staged
+// row-major in the idle weight ring and leaves by one bulk store.
 //
 // Operands live in shared memory in the canonical K-major 128-byte-swizzle
 // layout (8-row x 128-byte atoms): X arrives by a 2D tensor copy that applies
@@ -56,7 +60,7 @@ struct TcItem {
 };
 
 struct TcParams {
-    int n_in, ldx, H, n_out, nfc, nxc, nhc, nitems, end1, end2, first_h, tmem_cols;
+    int n_in, ldx, H, n_out, nfc, nxc, nhc, nxs, nitems, end1, end2, first_h, tmem_cols;
     const uint8_t *wblob;
     int *status;
     TcItem items[MAX_ITEMS];
@@ -113,6 +117,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"(map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NTH - 64) : "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -174,17 +190,17 @@ __device__ __forceinline__ void store_h16(uint8_t *sAh, int row, int c0, const f
 
 template <int H>
 __global__ void __launch_bounds__(NTH, 1)
-k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap tmX, float *__restrict__ h,
-         float *__restrict__ d, int P) {
+k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap tmX,
+         const __grid_constant__ CUtensorMap tmH, float *__restrict__ h, float *__restrict__ d, int P) {
     constexpr int NH = H / 2;           // state columns per epilogue thread
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sX = base;                                   // nxc chunks
-    uint8_t *sAh = sX + p.nxc * CHUNK;                    // nhc chunks
+    uint8_t *sX = base;                                   // max(nxc, H/32) chunks
+    uint8_t *sAh = sX + p.nxs * CHUNK;                    // nhc chunks
     uint8_t *sW = sAh + p.nhc * CHUNK;                    // NSTAGE stages
     uint64_t *bars = reinterpret_cast<uint64_t *>(sW + NSTAGE * CHUNK);
-    // barriers: full[NSTAGE], empty[NSTAGE], x_full, ah, d1, rh, d2, hn, d3, drain
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 8);
+    // barriers: full[NSTAGE], empty[NSTAGE], x_full, ah, d1, rh, d2, hn, d3, drain, h_full
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 9);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -193,7 +209,9 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSTAGE);
     const uint32_t x_full = smem_u32(bars + 2 * NSTAGE), ah_bar = x_full + 8, d1_bar = x_full + 16,
                    rh_bar = x_full + 24, d2_bar = x_full + 32, hn_bar = x_full + 40, d3_bar = x_full + 48,
-                   drain_bar = x_full + 56;
+                   drain_bar = x_full + 56, h_full = x_full + 64;
+    constexpr int HB = H / 32;                 // 32-column boxes of the FP32 state
+    uint8_t *sH = sW + (NSTAGE - HB) * CHUNK;  // the state arrives in the last HB ring stages
     constexpr int NEPI = NTH - 64;   // epilogue threads
 
     if (tid == 0) {
@@ -209,6 +227,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         mbar_init(hn_bar, NEPI);
         mbar_init(d3_bar, 1);
         mbar_init(drain_bar, 1);
+        mbar_init(h_full, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -228,11 +247,16 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         // ---------------- producer: X tile by TMA, weights through the ring
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(&tmX) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&tmH) : "memory");
             expect_tx(x_full, (uint32_t)(p.nxc * CHUNK));
             for (int kc = 0; kc < p.nxc; ++kc) tma_load_2d(sX_u + kc * CHUNK, &tmX, kc * KC, p0, x_full);
+            expect_tx(h_full, (uint32_t)(HB * CHUNK));
+            for (int q = 0; q < HB; ++q) tma_load_2d(smem_u32(sH) + q * CHUNK, &tmH, 32 * q, p0, h_full);
             int issued = 0;
             for (int i = 0; i < p.nitems; ++i) {
                 const int s = i % NSTAGE;
+                // the last HB stages hold the state until the epilogue has read it
+                if (i == NSTAGE - HB && !mbar_wait(ah_bar, 0, abort_flag)) break;
                 if (i >= NSTAGE && !mbar_wait(empty0 + 8 * s, ((i / NSTAGE) - 1) & 1, abort_flag)) break;
                 const TcItem &it = p.items[i];
                 expect_tx(full0 + 8 * s, (uint32_t)(it.rows * 128));
@@ -243,6 +267,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
                 // let every started copy land before the CTA may exit
                 volatile int no_abort = 0;
                 mbar_wait(x_full, 0, &no_abort);
+                mbar_wait(h_full, 0, &no_abort);
                 for (int i = issued - NSTAGE < 0 ? 0 : issued - NSTAGE; i < issued; ++i)
                     mbar_wait(full0 + 8 * (i % NSTAGE), (i / NSTAGE) & 1, &no_abort);
             }
@@ -287,12 +312,13 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         const int c0 = half * NH;                 // first state column of this thread
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         float hv[NH];
-        // h (FP32) of this row segment -> registers and -> bf16 operand
+        bool ok = __all_sync(0xffffffffu, mbar_wait(h_full, 0, abort_flag));
+        // h (FP32, swizzled 32-column boxes) of this row segment -> registers and -> bf16 operand
         {
-            const float4 *src = reinterpret_cast<const float4 *>(h + (size_t)gp * H + c0);
 #pragma unroll
             for (int i = 0; i < NH / 4; ++i) {
-                const float4 t = valid ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int c = c0 + 4 * i;
+                const float4 t = *reinterpret_cast<const float4 *>(sH + (c / 32) * CHUNK + swz(row, (c % 32) / 4));
                 hv[4 * i] = t.x; hv[4 * i + 1] = t.y; hv[4 * i + 2] = t.z; hv[4 * i + 3] = t.w;
             }
 #pragma unroll
@@ -305,7 +331,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
             fence_async_smem();
             mbar_arrive(ah_bar);
         }
-        bool ok = __all_sync(0xffffffffu, mbar_wait(d1_bar, 0, abort_flag));
+        ok = ok && __all_sync(0xffffffffu, mbar_wait(d1_bar, 0, abort_flag));
         tc_after_sync();
         if (ok) {
             // r * h -> operand
@@ -337,33 +363,58 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
                 }
                 store_h16(sAh, row, c0 + 16 * b, hv + 16 * b);
             }
+            // h' (FP32) -> swizzled boxes in the X region (free since phase 1) for a TMA store
+#pragma unroll
+            for (int i = 0; i < NH / 4; ++i) {
+                const int c = c0 + 4 * i;
+                *reinterpret_cast<float4 *>(sX + (c / 32) * CHUNK + swz(row, (c % 32) / 4)) =
+                    make_float4(hv[4 * i], hv[4 * i + 1], hv[4 * i + 2], hv[4 * i + 3]);
+            }
             fence_async_smem();
             tc_before_sync();
             mbar_arrive(hn_bar);
-            if (valid) {
-                float4 *dst = reinterpret_cast<float4 *>(h + (size_t)gp * H + c0);
-#pragma unroll
-                for (int i = 0; i < NH / 4; ++i)
-                    dst[i] = make_float4(hv[4 * i], hv[4 * i + 1], hv[4 * i + 2], hv[4 * i + 3]);
-            }
+        }
+        // named barriers are passed by every epilogue warp, whatever its state
+        epilogue_sync();
+        if (ok && warp == 2 && lane == 0 && !*abort_flag) {
+            for (int q = 0; q < HB; ++q) tma_store_2d(&tmH, 32 * q, p0, sX_u + q * CHUNK);
+            bulk_commit();
+        }
+        if (ok) {
             ok = __all_sync(0xffffffffu, mbar_wait(d3_bar, 0, abort_flag));
             tc_after_sync();
         }
+        const int nv = min(TM, P - p0);
+        const int rb = 4 * p.n_out, g16 = rb % 16 == 0 ? 1 : (rb % 8 == 0 ? 2 : 4);
+        const int nbulk = nv - nv % g16;
         if (ok) {
-            // d = W_fc h': blocks of 16 output columns split between the two halves
+            // d = W_fc h': blocks of 16 output columns split between the two halves,
+            // staged row-major in the (now idle) weight ring, then one bulk store
+            // of the tile's contiguous rows; rows past a 16-byte multiple go direct
             const int nb = p.nfc / 16;
             const int b0 = half ? (nb + 1) / 2 : 0, b1 = half ? nb : (nb + 1) / 2;
+            float *stage = reinterpret_cast<float *>(sW) + (size_t)row * p.n_out;
             float *drow = d + (size_t)gp * p.n_out;
             for (int b = b0; b < b1; ++b) {
                 float dv[16];
                 tmem_ld16(tl + 16 * b, dv);
-                if (valid) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (16 * b + i < p.n_out) drow[16 * b + i] = dv[i];
+                for (int i = 0; i < 16; i += 2) {
+                    const int c = 16 * b + i;
+                    if (c < p.n_out) {
+                        if (row < nbulk) *reinterpret_cast<float2 *>(stage + c) = make_float2(dv[i], dv[i + 1]);
+                        else if (valid) { drow[c] = dv[i]; drow[c + 1] = dv[i + 1]; }
+                    }
                 }
             }
+            fence_async_smem();
         }
+        epilogue_sync();
+        if (warp == 2 && lane == 0 && nbulk > 0 && !*abort_flag) {
+            bulk_store(d + (size_t)p0 * p.n_out, sW_u, (uint32_t)(nbulk * rb));
+            bulk_commit();
+        }
+        if (warp == 2 && lane == 0) bulk_wait_read();   // shared memory must outlive the stores
     }
 
     // ---------------- teardown
@@ -382,7 +433,7 @@ inline size_t swz_host(int row, int k) {
 }
 
 size_t smem_bytes(const TcParams &p) {
-    return (size_t)(p.nxc + p.nhc + NSTAGE) * CHUNK + 1024 + 256;
+    return (size_t)(p.nxs + p.nhc + NSTAGE) * CHUNK + 1024 + 256;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -411,10 +462,12 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
     const int nfc = round_up(n_out, 16);
     const int nxc = (ldx + KC - 1) / KC, nhc = (H + KC - 1) / KC;
     if (!(H == 32 || H == 64 || H == 96 || H == 128) || nfc > 2 * H) return false;
+    if ((size_t)TM * n_out * 4 > (size_t)NSTAGE * CHUNK || n_out % 2) return false;   // d staging in the ring
     if (!encode_fn()) return false;
     TcParams p;
     memset(&p, 0, sizeof p);
     p.n_in = n_in; p.ldx = ldx; p.H = H; p.n_out = n_out; p.nfc = nfc; p.nxc = nxc; p.nhc = nhc;
+    p.nxs = nxc > H / 32 ? nxc : H / 32;
     std::vector<TcItem> items;
     std::vector<uint8_t> blob;
     // one chunk: rows [r0, r0 + rows) of a B matrix, K columns kc*64 .. kc*64+63
@@ -514,6 +567,15 @@ cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, 
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // h [P][H] fp32: boxes of 32 columns x 128 rows, 128-byte swizzle (load and store)
+    CUtensorMap th;
+    const cuuint64_t hdims[2] = {(cuuint64_t)p.H, (cuuint64_t)P};
+    const cuuint64_t hstrides[1] = {(cuuint64_t)p.H * 4};
+    const cuuint32_t hbox[2] = {32, (cuuint32_t)TM};
+    r = encode_fn()(&th, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h, hdims, hstrides, hbox, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const size_t smem = smem_bytes(p);
     const int grid = (P + TM - 1) / TM;
     cudaError_t e;
@@ -521,7 +583,7 @@ cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, 
     case HH:                                                                                                 \
         e = cudaFuncSetAttribute(k_gru_tc<HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
         if (e != cudaSuccess) return e;                                                                      \
-        k_gru_tc<HH><<<grid, NTH, smem, st>>>(p, tm, (float *)h, (float *)d, P);                             \
+        k_gru_tc<HH><<<grid, NTH, smem, st>>>(p, tm, th, (float *)h, (float *)d, P);                         \
         break;
     switch (p.H) {
         DNNMG_LAUNCH_H(32)

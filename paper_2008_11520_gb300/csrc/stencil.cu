@@ -150,9 +150,19 @@ __device__ __forceinline__ void convection(const FemCoef<T> &fc, const T (&u)[4]
     }
 }
 
+// Asynchronous 4- or 8-byte copy global -> shared; src_bytes = 0 writes zero.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Stage rows of a node-field window into shared memory: rows `nrows` of width
 // `w` starting at global node (I0, J0), component planes of Nf nodes; zero
-// outside the mesh.  One warp per row keeps the index arithmetic per row.
+// outside the mesh.  One warp per row; the copies are asynchronous so every
+// thread keeps many loads in flight (complete with cp_async_wait_all()).
 template <typename T>
 __device__ __forceinline__ void stage_rows(const MeshGeom &g, const T *__restrict__ src, size_t Nf, int ncomp,
                                            int I0, int J0, int w, int nrows, T *dst) {
@@ -166,7 +176,8 @@ __device__ __forceinline__ void stage_rows(const MeshGeom &g, const T *__restric
         const T *row = src + c * Nf + (size_t)(rowok ? J : 0) * nxn;
         for (int ii = lane; ii < w; ii += 32) {
             const int I = I0 + ii;
-            d[ii] = (rowok && I >= 0 && I <= g.nxf) ? row[I] : T(0);
+            const bool ok = rowok && I >= 0 && I <= g.nxf;
+            cp_async<sizeof(T)>(d + ii, ok ? row + I : src, ok ? (int)sizeof(T) : 0);
         }
     }
 }
@@ -210,12 +221,14 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
     stage_rows(g, xf, Nf, 3, I0 - 2, J0 - 2, L::HX, L::HY, xs);
     stage_rows(g, bf, Nf, 2, I0, J0, NXN, NYN, bs);
     bool all_fluid = true;
+#pragma unroll 3
     for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
         const int jj = idx / L::FX, ii = idx - jj * L::FX;
         const int code = cell_code(g, I0 - 2 + ii, J0 - 2 + jj);
         cf[idx] = (unsigned char)code;
         all_fluid &= code == 1;
     }
+    cp_async_wait_all();
     // Fast tiles: every cell within two of the tile is fluid and exists, so
     // no tile node is a boundary node and node stencils apply everywhere.
     const bool fast = __syncthreads_and(all_fluid);
@@ -470,12 +483,14 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
 
     stage_rows(g, vcorr, Nf, 2, I0 - 1, J0 - 1, L::HX, L::HY, vs);
     bool all_fluid = true;
+#pragma unroll 3
     for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
         const int jj = idx / L::CX, ii = idx - jj * L::CX;
         const int code = cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
         cf[idx] = (unsigned char)code;
         all_fluid &= code == 1;
     }
+    cp_async_wait_all();
     const bool fast = __syncthreads_and(all_fluid);
 
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
@@ -606,14 +621,8 @@ k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
     const int ci0 = blockIdx.x * TCX, cj0 = blockIdx.y * TCY;
     const int I0 = ci0 * r - (r - 1), J0 = cj0 * r - (r - 1);
     const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
-    for (int e = threadIdx.x; e < 2 * FH * FW; e += blockDim.x) {
-        const int c = e / (FH * FW), rem = e - c * (FH * FW);
-        const int jj = rem / FW, ii = rem - jj * FW;
-        const int I = I0 + ii, J = J0 + jj;
-        T v = T(0);
-        if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf) v = bf[c * Nf + (size_t)J * nxn + I];
-        fs[e] = v;
-    }
+    stage_rows(g, bf, Nf, 2, I0, J0, FW, FH, fs);
+    cp_async_wait_all();
     __syncthreads();
     const T inv_r = T(1) / T(r);
     for (int e = threadIdx.x; e < 2 * FH * TCX; e += blockDim.x) {
