@@ -21,10 +21,14 @@
  *    ends in _host.  The library never frees caller memory and allocates
  *    device memory only in *_create.  Compute calls are asynchronous on the
  *    given stream and never synchronise.
- *  - Node fields are planes [component][Nf] with Nf = (nxf+1)(nyf+1) fine
- *    nodes numbered x fastest (node (I, J) at index J (nxf+1) + I), and
- *    likewise [component][Nc] on the coarse level.  The fine "real" type is
- *    double for DNNMG_F64 and float otherwise; coarse vectors are double.
+ *  - Fine node fields are pitched planes [component][nyf+1][pitch]: node
+ *    (I, J) of component c is element c*plane + J*pitch + I, with
+ *    pitch = round_up(nxf+1, 64) and plane = pitch*(nyf+1) (info.pitch,
+ *    info.plane).  Columns nxf+1 .. pitch-1 are padding: kernels may write
+ *    them and never use them.  Fine arrays must be 16-byte aligned.  Coarse
+ *    vectors are unpadded planes [component][Nc], Nc = (nxc+1)(nyc+1), node
+ *    (i, j) at j*(nxc+1) + i.  The fine "real" type is double for DNNMG_F64
+ *    and float otherwise; coarse vectors are double.
  *  - Patch arrays are row-major [P][.] over the fluid patches, numbered
  *    lexicographically over the patch grid, patch-x fastest.
  */
@@ -90,6 +94,8 @@ typedef struct dnnmg_mesh_info {
     int nxc, nyc, nxf, nyf, K, s;
     int npx, npy;          /* patch grid */
     long long Nc, Nf;      /* coarse / fine nodes */
+    int pitch;             /* fine row pitch (elements), round_up(nxf+1, 64) */
+    long long plane;       /* elements per fine component plane, pitch (nyf+1) */
     int P;                 /* fluid patches */
     int nf, nc, n_in, n_out, ldx;
     int n_solid_coarse;    /* solid coarse cells */
@@ -114,9 +120,9 @@ int dnnmg_mesh_get_info(dnnmg_mesh_t mesh, dnnmg_mesh_info *info);
 /*
  * Index maps, for checking (Sec. 5.2 patches; Sec. 6.1 boundary classes):
  *   patch_cell [P] int: patch-grid index pj npx + pi of fluid patch p;
- *   node_flags [Nf] uint8: bit0 velocity Dirichlet, bit1 inflow value,
- *                          bit2 pressure row active (touches a fluid cell);
- *   node_mult  [Nf] uint8: number of fluid patches containing the node.
+ *   node_flags [plane] uint8: bit0 velocity Dirichlet, bit1 inflow value,
+ *                             bit2 pressure row active (touches a fluid cell);
+ *   node_mult  [plane] uint8: number of fluid patches containing the node.
  * Any output may be NULL.  Device pointers; asynchronous.
  */
 int dnnmg_mesh_maps(dnnmg_mesh_t mesh, int *patch_cell, unsigned char *node_flags,
@@ -136,14 +142,14 @@ int dnnmg_net_destroy(dnnmg_net_t net);
 /*
  * S1, Algorithm 2 line 6: xf = P xc on (u, v, p) by bilinear interpolation
  * from level L to L+K, then the fine velocity Dirichlet values at time t.
- *   xc [3][Nc] double (in), xf [3][Nf] real (out).
+ *   xc [3][Nc] double (in), xf [3][plane] real (out).
  */
 int dnnmg_prolongate(dnnmg_mesh_t mesh, const double *xc, void *xf, double t,
                      cudaStream_t stream);
 
 /*
  * S2 + S3, Sec. 5.2 network inputs: the nonlinear residual
- * r = b_f - A(xf) of Eq. nonlinearshort (Q1, 2x2 Gauss, LPS), zero on
+ * r = b_f - A(x~) of Eq. nonlinearshort (Q1, 2x2 Gauss, LPS), zero on
  * Dirichlet velocity rows and inactive pressure rows, and the feature matrix
  *   X [P][ldx] (feature type: double / float / bfloat16 by precision), row
  *   = [r_u(nf), r_v(nf), r_p(nf), u(nc), v(nc), Pe(nc), geometry(12), 0...]
@@ -152,11 +158,15 @@ int dnnmg_prolongate(dnnmg_mesh_t mesh, const double *xc, void *xf, double t,
  * geometry = edge lengths (bottom, right, top, left), aspect ratios
  * (bottom/right, top/left, bottom/top, left/right), corner angles
  * (SW, SE, NE, NW).
- *   xf [3][Nf] real, bf [2][Nf] real (the current fine right-hand side),
- *   rf [3][Nf] real (out, may be NULL), X (out).
+ * x~ is given either as xf [3][plane] real (the output of dnnmg_prolongate;
+ * pass xc = NULL), or as the coarse xc [3][Nc] double with the time t of its
+ * Dirichlet values (pass xf = NULL): S1 is then done inside the kernel and x~
+ * never goes to memory.  Exactly one of xf, xc must be non-NULL.
+ *   bf [2][plane] real (the current fine right-hand side), rf [3][plane]
+ *   real (out, may be NULL), X (out).
  */
-int dnnmg_patch_features(dnnmg_mesh_t mesh, const void *xf, const void *bf, void *rf,
-                         void *X, cudaStream_t stream);
+int dnnmg_patch_features(dnnmg_mesh_t mesh, const void *xf, const double *xc, double t, const void *bf,
+                         void *rf, void *X, cudaStream_t stream);
 
 /*
  * S4, Eq. gru and the output layer, for P patches at once:
@@ -169,23 +179,34 @@ int dnnmg_gru_step(dnnmg_net_t net, const void *X, void *h, void *d, int P,
                    cudaStream_t stream);
 
 /*
- * S5, Sec. 5.2 duplicate predictions averaged: vcorr = xf + mean of the
+ * S5, Sec. 5.2 duplicate predictions averaged: vcorr = v~ + mean of the
  * predictions of the fluid patches containing each node, on velocity
- * unknowns; Dirichlet nodes keep xf.  d row layout [u corr(nf), v corr(nf)].
- *   d [P][n_out] real, xf [3][Nf] real (only u, v read), vcorr [2][Nf] real.
+ * unknowns; Dirichlet nodes keep v~ (their boundary values).  d row layout
+ * [u corr(nf), v corr(nf)].  v~ is given either as xf [3][plane] real (only
+ * u, v read; xc = NULL) or interpolated inside the kernel from xc [3][Nc]
+ * double with boundary values at time t (xf = NULL); exactly one non-NULL.
+ *   d [P][n_out] real, vcorr [2][plane] real (out).
  */
-int dnnmg_scatter_avg(dnnmg_mesh_t mesh, const void *d, const void *xf, void *vcorr,
-                      cudaStream_t stream);
+int dnnmg_scatter_avg(dnnmg_mesh_t mesh, const void *d, const void *xf, const double *xc, double t,
+                      void *vcorr, cudaStream_t stream);
 
 /*
  * S6 + S7, Algorithm 2 lines 8-9: bf = Rhs(vcorr) of Eq. 4cranknicholson3
  * (1/k (v,phi) - 1/2 (v.grad v,phi) - nu/2 (grad v,grad phi), no forcing),
  * zero on Dirichlet rows; then bc = R bf with R = P^T, coarse Dirichlet
  * velocity rows and all pressure rows zero.
- *   vcorr [2][Nf] real (in), bf [2][Nf] real (out), bc [3][Nc] double (out).
+ *   vcorr [2][plane] real (in), bf [2][plane] real (out), bc [3][Nc] double
+ *   (out).
  */
 int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *bc,
                        cudaStream_t stream);
+
+/*
+ * S6 alone, Algorithm 2 line 8: bf = Rhs(vcorr) as in dnnmg_rhs_restrict,
+ * without the restriction.
+ *   vcorr [2][plane] real (in), bf [2][plane] real (out).
+ */
+int dnnmg_rhs(dnnmg_mesh_t mesh, const void *vcorr, void *bf, cudaStream_t stream);
 
 /*
  * S7 alone, Algorithm 2 line 9: bc = R bf with R = P^T (the transpose of the
@@ -193,13 +214,14 @@ int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *b
  * and all pressure rows zero.  Float input is accumulated with error-free
  * float-pair arithmetic (about 2^-44 relative to the sum of magnitudes) and
  * stored in double; double input is accumulated in double.
- *   bf [2][Nf] real (in), bc [3][Nc] double (out).
+ *   bf [2][plane] real (in), bc [3][Nc] double (out).
  */
 int dnnmg_restrict(dnnmg_mesh_t mesh, const void *bf, double *bc, cudaStream_t stream);
 
 /*
- * S1-S7 in order (Algorithm 2 lines 6-9) on one stream.
- *   xc [3][Nc] double (in), h [P][H] (in/out), bf [2][Nf] (in: this step's
+ * S1-S7 in order (Algorithm 2 lines 6-9) on one stream: S2+S3 and S5 with
+ * S1 fused (x~ is formed inside their tiles from xc), then S4, S6, S7.
+ *   xc [3][Nc] double (in), h [P][H] (in/out), bf [2][plane] (in: this step's
  *   fine right-hand side; out: the next step's), bc [3][Nc] double (out),
  *   workspace >= info.workspace_bytes device bytes (scratch, caller-owned,
  *   256-byte aligned), t = t_n for the inflow values.

@@ -97,8 +97,11 @@ int validate_desc(const dnnmg_mesh_desc *d) {
         return fail(DNNMG_EINVAL, "unknown precision %d", d->precision);
     const long long nyf = (long long)d->nyc << d->K, nxf = (long long)d->nxc << d->K;
     if (nyf + 1 > 65535) return fail(DNNMG_EUNSUPPORTED, "nyf=%lld: at most 65534 fine rows", nyf);
-    if ((nxf + 1) * (nyf + 1) > (1LL << 31))
+    if ((nxf + 64) * (nyf + 1) > (1LL << 31))
         return fail(DNNMG_EUNSUPPORTED, "%lld fine nodes: at most 2^31", (nxf + 1) * (nyf + 1));
+    const int S = d->s << d->K, n_in = 3 * (S + 1) * (S + 1) + 3 * (d->s + 1) * (d->s + 1) + 12;
+    if (round_up(n_in, 16) > feature_table_capacity())
+        return fail(DNNMG_EUNSUPPORTED, "%d network inputs: at most %d", n_in, feature_table_capacity());
     return DNNMG_OK;
 }
 
@@ -115,6 +118,8 @@ void fill_info(const dnnmg_mesh_desc &d, int P, int n_solid, dnnmg_mesh_info *in
     I.npy = d.nyc / d.s;
     I.Nc = (long long)(d.nxc + 1) * (d.nyc + 1);
     I.Nf = (long long)(I.nxf + 1) * (I.nyf + 1);
+    I.pitch = round_up(I.nxf + 1, 64);
+    I.plane = (long long)I.pitch * (I.nyf + 1);
     I.P = P;
     const int S = d.s << d.K;
     I.nf = (S + 1) * (S + 1);
@@ -127,30 +132,27 @@ void fill_info(const dnnmg_mesh_desc &d, int P, int n_solid, dnnmg_mesh_info *in
     I.real_bytes = d.precision == DNNMG_F64 ? 8 : 4;
     I.feature_bytes = d.precision == DNNMG_F64 ? 8 : (d.precision == DNNMG_F32 ? 4 : 2);
     size_t ws = 0;
-    ws += align256(3 * (size_t)I.Nf * I.real_bytes);            // x~
     ws += align256((size_t)P * I.ldx * I.feature_bytes);        // X
     ws += align256((size_t)P * I.n_out * I.real_bytes);         // d
-    ws += align256(2 * (size_t)I.Nf * I.real_bytes);            // v_corr
+    ws += align256(2 * (size_t)I.plane * I.real_bytes);         // v_corr
     ws += 2 * align256(3 * (size_t)I.Nc * sizeof(double));      // host-call staging of x_c, b_c
     I.workspace_bytes = ws;
 }
 
 struct Workspace {
-    void *xf, *X, *d, *vc;
+    void *X, *d, *vc;
     double *xc, *bc;
 };
 
 Workspace carve(const dnnmg_mesh_info &I, void *base) {
     Workspace w;
     char *p = static_cast<char *>(base);
-    w.xf = p;
-    p += align256(3 * (size_t)I.Nf * I.real_bytes);
     w.X = p;
     p += align256((size_t)I.P * I.ldx * I.feature_bytes);
     w.d = p;
     p += align256((size_t)I.P * I.n_out * I.real_bytes);
     w.vc = p;
-    p += align256(2 * (size_t)I.Nf * I.real_bytes);
+    p += align256(2 * (size_t)I.plane * I.real_bytes);
     w.xc = reinterpret_cast<double *>(p);
     p += align256(3 * (size_t)I.Nc * sizeof(double));
     w.bc = reinterpret_cast<double *>(p);
@@ -293,6 +295,8 @@ int check_device(int dev) {
     return DNNMG_OK;
 }
 
+bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
 int check_mesh(dnnmg_mesh_t m) {
     if (!m) return fail(DNNMG_EINVAL, "mesh handle is NULL");
     return check_device(m->device);
@@ -365,6 +369,7 @@ int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out) {
     const dnnmg_mesh_info &I = m->info;
     g.nxc = I.nxc; g.nyc = I.nyc; g.K = I.K; g.r = 1 << I.K; g.s = I.s; g.S = I.s << I.K;
     g.nxf = I.nxf; g.nyf = I.nyf; g.npx = I.npx; g.npy = I.npy; g.P = P;
+    g.pitch = I.pitch; g.plane = (size_t)I.plane;
     g.nf = I.nf; g.nc = I.nc; g.n_in = I.n_in; g.n_out = I.n_out; g.ldx = I.ldx;
     g.lx = desc->lx; g.ly = desc->ly;
     g.hxc = desc->lx / I.nxc; g.hyc = desc->ly / I.nyc;
@@ -514,17 +519,21 @@ int dnnmg_prolongate(dnnmg_mesh_t mesh, const double *xc, void *xf, double t, cu
     clear_error();
     if (int e = check_mesh(mesh)) return e;
     if (!xc || !xf) return fail(DNNMG_EINVAL, "NULL array");
+    if (!aligned16(xf)) return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
     DNNMG_CUDA_TRY(launch_prolongate(mesh->g, mesh->info.precision, xc, xf, t, stream));
     return DNNMG_OK;
 }
 
-int dnnmg_patch_features(dnnmg_mesh_t mesh, const void *xf, const void *bf, void *rf, void *X,
-                         cudaStream_t stream) {
+int dnnmg_patch_features(dnnmg_mesh_t mesh, const void *xf, const double *xc, double t, const void *bf,
+                         void *rf, void *X, cudaStream_t stream) {
     clear_error();
     if (int e = check_mesh(mesh)) return e;
-    if (!xf || !bf || (!X && mesh->info.P)) return fail(DNNMG_EINVAL, "NULL array");
+    if (!bf || (!X && mesh->info.P)) return fail(DNNMG_EINVAL, "NULL array");
+    if ((xf == nullptr) == (xc == nullptr)) return fail(DNNMG_EINVAL, "exactly one of xf and xc must be given");
+    if ((xf && !aligned16(xf)) || !aligned16(bf) || (rf && !aligned16(rf)))
+        return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
     DNNMG_CUDA_TRY(launch_residual_features(mesh->g, mesh->info.precision, mesh->fem64, mesh->fem32,
-                                            xf, bf, rf, X, stream));
+                                            xf, xc, t, bf, rf, X, stream));
     return DNNMG_OK;
 }
 
@@ -542,12 +551,14 @@ int dnnmg_gru_step(dnnmg_net_t net, const void *X, void *h, void *d, int P, cuda
     return DNNMG_OK;
 }
 
-int dnnmg_scatter_avg(dnnmg_mesh_t mesh, const void *d, const void *xf, void *vcorr,
-                      cudaStream_t stream) {
+int dnnmg_scatter_avg(dnnmg_mesh_t mesh, const void *d, const void *xf, const double *xc, double t,
+                      void *vcorr, cudaStream_t stream) {
     clear_error();
     if (int e = check_mesh(mesh)) return e;
-    if ((!d && mesh->info.P) || !xf || !vcorr) return fail(DNNMG_EINVAL, "NULL array");
-    DNNMG_CUDA_TRY(launch_scatter_avg(mesh->g, mesh->info.precision, d, xf, vcorr, stream));
+    if ((!d && mesh->info.P) || !vcorr) return fail(DNNMG_EINVAL, "NULL array");
+    if ((xf == nullptr) == (xc == nullptr)) return fail(DNNMG_EINVAL, "exactly one of xf and xc must be given");
+    if ((xf && !aligned16(xf)) || !aligned16(vcorr)) return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
+    DNNMG_CUDA_TRY(launch_scatter_avg(mesh->g, mesh->info.precision, d, xf, xc, t, vcorr, stream));
     return DNNMG_OK;
 }
 
@@ -557,8 +568,19 @@ int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *b
     if (int e = check_mesh(mesh)) return e;
     if (!vcorr || !bf || !bc) return fail(DNNMG_EINVAL, "NULL array");
     if (vcorr == bf) return fail(DNNMG_EINVAL, "vcorr and bf must not alias");
+    if (!aligned16(vcorr) || !aligned16(bf)) return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
     DNNMG_CUDA_TRY(launch_rhs(mesh->g, mesh->info.precision, mesh->fem64, mesh->fem32, vcorr, bf, stream));
     DNNMG_CUDA_TRY(launch_restrict(mesh->g, mesh->info.precision, bf, bc, stream));
+    return DNNMG_OK;
+}
+
+int dnnmg_rhs(dnnmg_mesh_t mesh, const void *vcorr, void *bf, cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if (!vcorr || !bf) return fail(DNNMG_EINVAL, "NULL array");
+    if (vcorr == bf) return fail(DNNMG_EINVAL, "vcorr and bf must not alias");
+    if (!aligned16(vcorr) || !aligned16(bf)) return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
+    DNNMG_CUDA_TRY(launch_rhs(mesh->g, mesh->info.precision, mesh->fem64, mesh->fem32, vcorr, bf, stream));
     return DNNMG_OK;
 }
 
@@ -566,6 +588,7 @@ int dnnmg_restrict(dnnmg_mesh_t mesh, const void *bf, double *bc, cudaStream_t s
     clear_error();
     if (int e = check_mesh(mesh)) return e;
     if (!bf || !bc) return fail(DNNMG_EINVAL, "NULL array");
+    if (!aligned16(bf)) return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
     DNNMG_CUDA_TRY(launch_restrict(mesh->g, mesh->info.precision, bf, bc, stream));
     return DNNMG_OK;
 }
@@ -593,6 +616,7 @@ static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, vo
         return fail(DNNMG_EINVAL, "network precision %d differs from mesh precision %d",
                     net->precision, I.precision);
     if (!h || !bf || !workspace) return fail(DNNMG_EINVAL, "NULL array");
+    if (!aligned16(bf) || !aligned16(h)) return fail(DNNMG_EINVAL, "bf and h must be 16-byte aligned");
     if (workspace_bytes < I.workspace_bytes)
         return fail(DNNMG_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, I.workspace_bytes);
     if (reinterpret_cast<uintptr_t>(workspace) % 256)
@@ -604,10 +628,11 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
                      double *bc, const Workspace &w, double t, cudaStream_t s) {
     const int prec = mesh->info.precision;
     const MeshGeom &g = mesh->g;
-    DNNMG_CUDA_TRY(launch_prolongate(g, prec, xc, w.xf, t, s));
-    DNNMG_CUDA_TRY(launch_residual_features(g, prec, mesh->fem64, mesh->fem32, w.xf, bf, nullptr, w.X, s));
+    // S1 is fused into S2+S3 and S5: both interpolate x~ from xc inside their
+    // tiles, so x~ never goes to memory
+    DNNMG_CUDA_TRY(launch_residual_features(g, prec, mesh->fem64, mesh->fem32, nullptr, xc, t, bf, nullptr, w.X, s));
     if (mesh->info.P) DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
-    DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, w.xf, w.vc, s));
+    DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, nullptr, xc, t, w.vc, s));
     DNNMG_CUDA_TRY(launch_rhs(g, prec, mesh->fem64, mesh->fem32, w.vc, bf, s));
     DNNMG_CUDA_TRY(launch_restrict(g, prec, bf, bc, s));
     return DNNMG_OK;
@@ -637,7 +662,7 @@ int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, v
 
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net) {
     if (!mesh || !net) return -1;
-    return 5 + (mesh->info.P ? gru_launch_count(*net) : 0);
+    return 4 + (mesh->info.P ? gru_launch_count(*net) : 0);
 }
 
 }  // extern "C"

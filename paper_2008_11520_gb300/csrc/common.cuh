@@ -38,6 +38,8 @@ void clear_error();
 struct MeshGeom {
     int nxc, nyc, K, r, s, S;     // r = 2^K fine cells per coarse cell, S = s r per patch
     int nxf, nyf, npx, npy, P;
+    int pitch;                    // fine row pitch in elements, round_up(nxf + 1, 64)
+    size_t plane;                 // elements per fine component plane, pitch (nyf + 1)
     int nf, nc, n_in, n_out, ldx;
     double lx, ly, hxc, hyc, hxf, hyf;
     double nu, k, u_max;
@@ -106,11 +108,13 @@ size_t align256(size_t v);
 // All return cudaSuccess or the launch error; `prec` is DNNMG_F64/F32/BF16NET.
 cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, void *xf,
                               double t, cudaStream_t st);
+// xc == NULL: x~ is read from xf; otherwise x~ = P xc (with the Dirichlet
+// values at time t) is formed inside the kernel and xf is not read.
 cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<double> &f64,
-                                     const FemCoef<float> &f32, const void *xf, const void *bf,
-                                     void *rf, void *X, cudaStream_t st);
-cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf,
-                               void *vcorr, cudaStream_t st);
+                                     const FemCoef<float> &f32, const void *xf, const double *xc, double t,
+                                     const void *bf, void *rf, void *X, cudaStream_t st);
+cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf, const double *xc,
+                               double t, void *vcorr, cudaStream_t st);
 cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
                        const FemCoef<float> &f32, const void *vcorr, void *bf, cudaStream_t st);
 cudaError_t launch_restrict(const MeshGeom &g, int prec, const void *bf, double *bc,
@@ -125,5 +129,6 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc);
 void tc_release(Net &n);
 // Per feature column: (kind << 24) | offset into the residual / node tiles of stencil.cu.
 void feature_table(const MeshGeom &g, int *tab);
+int feature_table_capacity();
 
 }  // namespace dnnmg

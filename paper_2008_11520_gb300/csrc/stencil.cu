@@ -2,11 +2,15 @@
 //   S1 prolongation, S2+S3 residual and patch features, S5 averaging,
 //   S6 right-hand side, S7 restriction, plus the node index maps.
 //
-// Fine node fields are SoA planes [comp][Nf], x fastest.  S2 and S6 are
-// tiled: one CTA owns a 32 x 16 block of fine cells, stages the node values
-// it needs (plus a halo) in shared memory, computes every cell's element
-// contributions once (cell-centric), and then sums them per node (a pull,
-// so there are no atomics and results are bitwise repeatable).
+// Fine node fields are pitched SoA planes [comp][nyf+1][pitch], x fastest,
+// pitch = round_up(nxf + 1, 64), so every row starts on a 256-byte boundary
+// and tiles move as aligned 16-byte pieces.  S2 and S6 are tiled: one CTA owns
+// a 32 x 16 block of fine cells, stages the node values it needs (plus a
+// halo) in shared memory with asynchronous copies, computes every cell's
+// element contributions once (cell-centric), and then sums them per node (a
+// pull: no atomics, bitwise repeatable).  A tile writes only the nodes it
+// owns.  Tiles whose whole neighbourhood is fluid (the vast majority) take a
+// fast path with node-level stencils and skip all boundary classification.
 #include <cstdio>
 
 #include "common.cuh"
@@ -20,7 +24,6 @@ constexpr int NXN = TXC + 1;       // tile nodes in x
 constexpr int NYN = TYC + 1;
 constexpr int NTHREADS = 256;
 
-template <typename T> __device__ __forceinline__ T to_real(T v) { return v; }
 template <typename TX, typename T> __device__ __forceinline__ TX store_as(T v) { return (TX)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, float>(float v) {
     return __float2bfloat16_rn(v);
@@ -37,8 +40,7 @@ struct NodeClass {
 };
 
 // Sec. 6.1 boundary classes of fine node (I, J) from its four cells.
-__device__ __forceinline__ NodeClass classify(int c00, int c10, int c01, int c11, int I, int J,
-                                              int nyf) {
+__device__ __forceinline__ NodeClass classify(int c00, int c10, int c01, int c11, int I, int J, int nyf) {
     bool ts = (c00 == 2) | (c10 == 2) | (c01 == 2) | (c11 == 2);
     bool tf = (c00 == 1) | (c10 == 1) | (c01 == 1) | (c11 == 1);
     bool wall = (J == 0) | (J == nyf);
@@ -54,53 +56,152 @@ __device__ __forceinline__ NodeClass classify_global(const MeshGeom &g, int I, i
                     cell_code(g, I, J), I, J, g.nyf);
 }
 
-// ------------------------------------------------------------------ S1
-// A CTA owns 64 x 16 fine nodes; the coarse nodes they need are converted to
-// the fine type once and staged in shared memory, so the interpolation runs
-// in the fine arithmetic type (FP64 throughput on GB300 is 1/64 of FP32).
-constexpr int PTX = 64, PTY = 16;
-constexpr int PCX = PTX / 2 + 2, PCY = PTY / 2 + 2;   // coarse nodes of a tile for r >= 2
+// True (in every thread of the CTA) iff every fine cell in [i0, i1] x [j0, j1]
+// exists and is fluid; the coarse cells covering the range are checked.
+__device__ __forceinline__ bool block_all_fluid(const MeshGeom &g, int i0, int i1, int j0, int j1) {
+    bool ok = i0 >= 0 && j0 >= 0 && i1 < g.nxf && j1 < g.nyf;
+    if (ok) {
+        const int ci0 = i0 >> g.K, ci1 = i1 >> g.K, cj0 = j0 >> g.K, cj1 = j1 >> g.K;
+        const int w = ci1 - ci0 + 1, n = w * (cj1 - cj0 + 1);
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int cj = cj0 + e / w, ci = ci0 + e % w;
+            ok &= g.solid[(size_t)cj * g.nxc + ci] == 0;
+        }
+    }
+    return __syncthreads_and(ok);
+}
 
+// Asynchronous 16-byte copy global -> shared; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage a window of NCOMP component planes: rows J0 .. J0+NROWS-1, columns
+// Ia .. Ia+W-1 (Ia and W multiples of 16 bytes) into dst[c][row][W].  Pieces
+// outside the stored rows are zero; columns past nxf (row padding) carry
+// whatever the padding holds and are never used.  Asynchronous: complete with
+// cp_async_wait_all() and a barrier.  Window sizes are compile-time constants
+// so the piece -> (row, column) split costs a multiply and a shift.
+template <typename T, int NCOMP, int NROWS, int W>
+__device__ __forceinline__ void stage_window(const MeshGeom &g, const T *__restrict__ src, int Ia, int J0, T *dst) {
+    constexpr int EPC = 16 / sizeof(T), CPR = W / EPC, TOTAL = NCOMP * NROWS * CPR;
+    static_assert(W % EPC == 0, "window width must be a multiple of 16 bytes");
+    for (int e = threadIdx.x; e < TOTAL; e += blockDim.x) {
+        const int row = e / CPR, k = e - row * CPR;          // row = c * NROWS + jj
+        const int c = row / NROWS, J = J0 + (row - c * NROWS);
+        const int I = Ia + k * EPC;
+        const bool ok = J >= 0 && J <= g.nyf && I >= 0 && I + EPC <= g.pitch;
+        const T *s = ok ? src + (size_t)c * g.plane + (size_t)J * g.pitch + I : src;
+        cp_async16(dst + row * W + k * EPC, s, ok ? 16 : 0);
+    }
+}
+
+// ------------------------------------------------------------------ S1
+// Coarse nodes that a window of fine nodes [Ilo, Ilo+FW) x [Jlo, Jlo+FH)
+// interpolates from, staged once per CTA in the fine arithmetic type (FP64
+// throughput on GB300 is 1/64 of FP32, so converting per fine node is not an
+// option).  Fine node I lies in coarse cell clamp(I >> K, 0, nxc-1).
+template <int R> struct Log2;
+template <> struct Log2<2> { static constexpr int v = 1; };
+template <> struct Log2<4> { static constexpr int v = 2; };
+template <> struct Log2<8> { static constexpr int v = 3; };
+
+template <typename T, int R, int FW, int FH>
+struct CoarseWin {
+    static constexpr int K = Log2<R>::v;
+    static constexpr int CW = (FW - 1) / R + 3, CH = (FH - 1) / R + 3, N = 3 * CW * CH;
+    T *cs;          // [3][CH][CW] in shared memory
+    int ci0, cj0;   // first staged coarse node
+
+    __device__ __forceinline__ void stage(const MeshGeom &g, const double *__restrict__ xc, int Ilo, int Jlo) {
+        ci0 = min(max(Ilo >> K, 0), g.nxc - 1);
+        cj0 = min(max(Jlo >> K, 0), g.nyc - 1);
+        const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
+        for (int e = threadIdx.x; e < N; e += blockDim.x) {
+            const int c = e / (CW * CH), rem = e - c * (CW * CH);
+            const int b = rem / CW, a = rem - b * CW;
+            const int ci = ci0 + a, cj = cj0 + b;
+            T v = T(0);
+            if (ci <= g.nxc && cj <= g.nyc) v = (T)__ldg(xc + c * Nc + (size_t)cj * nc1 + ci);
+            cs[e] = v;
+        }
+    }
+    // Bilinear value of all three fields at fine node (I, J) (raw P, no BC).
+    __device__ __forceinline__ void interp(const MeshGeom &g, int I, int J, T (&out)[3]) const {
+        constexpr T inv_r = T(1) / T(R);   // exact: R is a power of two
+        const int ci = min(max(I >> K, 0), g.nxc - 1), cj = min(max(J >> K, 0), g.nyc - 1);
+        const T a = T(I - (ci << K)) * inv_r, b = T(J - (cj << K)) * inv_r;
+        const int o = (cj - cj0) * CW + (ci - ci0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T *q = cs + c * CW * CH + o;
+            out[c] = (T(1) - a) * (T(1) - b) * q[0] + a * (T(1) - b) * q[1] + (T(1) - a) * b * q[CW] + a * b * q[CW + 1];
+        }
+    }
+};
+
+// Dirichlet velocity of fine node (I, J) if it has one (Sec. 6.1).
 template <typename T>
+__device__ __forceinline__ bool dirichlet_value(const MeshGeom &g, int I, int J, double inflow_scale, T &u, T &v) {
+    const NodeClass nc = classify_global(g, I, J);
+    if (!nc.dirichlet) return false;
+    const double y = J * g.hyf;
+    u = nc.inflow ? (T)(g.u_max * 4.0 * y * (g.ly - y) / (g.ly * g.ly) * inflow_scale) : T(0);
+    v = T(0);
+    return true;
+}
+
+// Four consecutive nodes as one aligned vector access (16 B for float, two 16 B for double).
+__device__ __forceinline__ void store4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void load4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// A CTA owns 64 x 16 fine nodes, 4 consecutive nodes per thread (one 16-byte
+// store per field and row segment; nodes past nxf land in the row padding).
+constexpr int PTX = 64, PTY = 16;
+
+template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS)
 k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, double inflow_scale) {
-    __shared__ T cs[3][PCY][PCX];
+    using CW = CoarseWin<T, R, PTX, PTY>;
+    __shared__ T cs_mem[CW::N];
     const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
-    const int ci0 = min(I0 >> g.K, g.nxc - 1), cj0 = min(J0 >> g.K, g.nyc - 1);
-    const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
-    for (int e = threadIdx.x; e < 3 * PCY * PCX; e += blockDim.x) {
-        const int c = e / (PCY * PCX), rem = e - c * (PCY * PCX);
-        const int jj = rem / PCX, ii = rem - jj * PCX;
-        const int ci = ci0 + ii, cj = cj0 + jj;
-        T v = T(0);
-        if (ci <= g.nxc && cj <= g.nyc) v = (T)__ldg(xc + c * Nc + (size_t)cj * nc1 + ci);
-        cs[c][jj][ii] = v;
-    }
-    __syncthreads();
-    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
-    const T inv_r = T(1) / T(g.r);   // exact: r is a power of two
-    for (int e = threadIdx.x; e < PTX * PTY; e += blockDim.x) {
-        const int I = I0 + (e % PTX), J = J0 + e / PTX;
-        if (I > g.nxf || J > g.nyf) continue;
-        const int ci = min(I >> g.K, g.nxc - 1), cj = min(J >> g.K, g.nyc - 1);
-        const T a = T(I - (ci << g.K)) * inv_r, b = T(J - (cj << g.K)) * inv_r;
-        const int li = ci - ci0, lj = cj - cj0;
-        T val[3];
+    CW cw;
+    cw.cs = cs_mem;
+    cw.stage(g, xc, I0, J0);
+    // no Dirichlet node in the tile: all cells around its nodes exist and are
+    // fluid (the barrier inside also publishes the staged coarse nodes)
+    const bool fast = block_all_fluid(g, I0 - 1, I0 + PTX, J0 - 1, J0 + PTY);
+    const int J = J0 + threadIdx.x / (PTX / 4);
+    const int Ib = I0 + 4 * (threadIdx.x % (PTX / 4));
+    if (J > g.nyf) return;
+    T val[3][4];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            val[c] = (T(1) - a) * (T(1) - b) * cs[c][lj][li] + a * (T(1) - b) * cs[c][lj][li + 1] +
-                     (T(1) - a) * b * cs[c][lj + 1][li] + a * b * cs[c][lj + 1][li + 1];
-        const NodeClass nc = classify_global(g, I, J);
-        if (nc.dirichlet) {
-            const double y = J * g.hyf;
-            val[0] = nc.inflow ? (T)(g.u_max * 4.0 * y * (g.ly - y) / (g.ly * g.ly) * inflow_scale) : T(0);
-            val[1] = T(0);
-        }
-        const size_t node = (size_t)J * nxn + I;
-        xf[node] = val[0];
-        xf[Nf + node] = val[1];
-        xf[2 * Nf + node] = val[2];
+    for (int q = 0; q < 4; ++q) {
+        const int I = Ib + q;
+        T x[3];
+        cw.interp(g, I, J, x);
+        if (!fast && I <= g.nxf) dirichlet_value(g, I, J, inflow_scale, x[0], x[1]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) val[c][q] = x[c];
     }
+    const size_t node = (size_t)J * g.pitch + Ib;   // 4-aligned in a 64-aligned row
+#pragma unroll
+    for (int c = 0; c < 3; ++c) store4(xf + (size_t)c * g.plane + node, val[c]);
 }
 
 // ------------------------------------------------------------------ S2 + S3
@@ -150,97 +251,96 @@ __device__ __forceinline__ void convection(const FemCoef<T> &fc, const T (&u)[4]
     }
 }
 
-// Asynchronous 4- or 8-byte copy global -> shared; src_bytes = 0 writes zero.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *dst, const void *src, int src_bytes) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Stage rows of a node-field window into shared memory: rows `nrows` of width
-// `w` starting at global node (I0, J0), component planes of Nf nodes; zero
-// outside the mesh.  One warp per row; the copies are asynchronous so every
-// thread keeps many loads in flight (complete with cp_async_wait_all()).
-template <typename T>
-__device__ __forceinline__ void stage_rows(const MeshGeom &g, const T *__restrict__ src, size_t Nf, int ncomp,
-                                           int I0, int J0, int w, int nrows, T *dst) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const size_t nxn = (size_t)g.nxf + 1;
-    for (int rr = warp; rr < ncomp * nrows; rr += nw) {
-        const int c = rr / nrows, jj = rr - c * nrows;
-        const int J = J0 + jj;
-        T *d = dst + (size_t)rr * w;
-        const bool rowok = J >= 0 && J <= g.nyf;
-        const T *row = src + c * Nf + (size_t)(rowok ? J : 0) * nxn;
-        for (int ii = lane; ii < w; ii += 32) {
-            const int I = I0 + ii;
-            const bool ok = rowok && I >= 0 && I <= g.nxf;
-            cp_async<sizeof(T)>(d + ii, ok ? row + I : src, ok ? (int)sizeof(T) : 0);
-        }
-    }
-}
-
-// Shared-memory layout of the residual/feature tile (element counts).
+// Shared-memory layout of the residual/feature tile (element counts).  The
+// node window of x~ spans columns I0-4 .. I0+35 (16-byte aligned; node I0+ii
+// at column ii+4) and rows J0-2 .. J0+18 (node J0+jj at row jj+2).
 struct ResLayout {
-    static constexpr int HX = NXN + 4, HY = NYN + 4;           // nodes with 2-node halo
+    static constexpr int HX = 40, HY = NYN + 4, XO = 4, YO = 2;
+    static constexpr int BX = 36;                              // b_f window: columns I0 .. I0+35
     static constexpr int CX = TXC + 2, CY = TYC + 2;           // cells with 1-cell halo
     static constexpr int NCELL = CX * CY;
     static constexpr int LX = TXC / 2 + 2, LY = TYC / 2 + 2;   // LPS patches touching the tile
     static constexpr int NLPS = LX * LY;
     static constexpr int FX = TXC + 4, FY = TYC + 4;           // cell codes with 2-cell halo
     static constexpr int XS = 3 * HY * HX;
-    static constexpr int BS = 2 * NYN * NXN;
-    static constexpr int CC = 12 * NCELL;
+    static constexpr int BS = 2 * NYN * BX;
+    static constexpr int CC = 8 * NCELL;
     static constexpr int LC = 9 * NLPS;
     static constexpr int RS = 3 * NYN * NXN;
-    template <typename T> static constexpr size_t bytes() {
-        return sizeof(T) * (XS + BS + CC + LC + RS) + FX * FY;
+    static constexpr int MAXCS = 3 * ((HX - 1) / 2 + 3) * ((HY - 1) / 2 + 3);   // coarse window, R = 2
+    static constexpr int MAX_LDX = 1024;                       // feature columns supported
+    template <typename T> static constexpr size_t bytes(bool from_coarse) {
+        return sizeof(T) * (XS + BS + CC + LC + RS + (from_coarse ? MAXCS : 0)) + FX * FY;
     }
 };
 
 enum { FEAT_RES = 0, FEAT_VEL = 1, FEAT_PECLET = 2, FEAT_GEO = 3, FEAT_ZERO = 4 };
 
-template <typename T, typename TX>
+// S2 + S3 for one 32 x 16-cell tile.  R = 0: x~ is read from xf (S1 done by
+// the caller); R = 2, 4, 8: x~ is interpolated from the coarse vector xc
+// inside the tile (S1 fused: x~ never reaches HBM), with the Dirichlet
+// values set where the tile touches a boundary.
+template <typename T, typename TX, int R>
 __global__ void __launch_bounds__(NTHREADS)
-k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T *__restrict__ bf,
-                    T *__restrict__ rf, TX *__restrict__ X) {
+k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const double *__restrict__ xc,
+                    double inflow_scale, const T *__restrict__ bf, T *__restrict__ rf, TX *__restrict__ X) {
     using L = ResLayout;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);   // [3][HY][HX]   u, v, p
-    T *bs = xs + L::XS;                        // [2][NYN][NXN] b_u, b_v
-    T *cc = bs + L::BS;                        // [12][NCELL]   cell contributions
+    T *bs = xs + L::XS;                        // [2][NYN][BX]  b_u, b_v
+    T *cc = bs + L::BS;                        // [8][NCELL]    cell contributions (velocity rows)
     T *lc = cc + L::CC;                        // [9][NLPS]     LPS contributions
     T *rs = lc + L::LC;                        // [3][NYN][NXN] residual
-    unsigned char *cf = reinterpret_cast<unsigned char *>(rs + L::RS);  // [FY][FX]
+    T *csm = rs + L::RS;                       // coarse window (R > 0)
+    unsigned char *cf = reinterpret_cast<unsigned char *>(csm + (R > 0 ? L::MAXCS : 0));   // [FY][FX]
 
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
-    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
-
-    stage_rows(g, xf, Nf, 3, I0 - 2, J0 - 2, L::HX, L::HY, xs);
-    stage_rows(g, bf, Nf, 2, I0, J0, NXN, NYN, bs);
-    bool all_fluid = true;
-#pragma unroll 3
-    for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
-        const int jj = idx / L::FX, ii = idx - jj * L::FX;
-        const int code = cell_code(g, I0 - 2 + ii, J0 - 2 + jj);
-        cf[idx] = (unsigned char)code;
-        all_fluid &= code == 1;
+    stage_window<T, 2, NYN, L::BX>(g, bf, I0, J0, bs);
+    using CWin = CoarseWin<T, (R > 0 ? R : 2), L::HX, L::HY>;
+    CWin cw;
+    cw.cs = csm;
+    if constexpr (R > 0) {
+        static_assert(CWin::N <= L::MAXCS, "coarse window");
+        cw.stage(g, xc, I0 - L::XO, J0 - L::YO);
+    } else {
+        stage_window<T, 3, L::HY, L::HX>(g, xf, I0 - L::XO, J0 - L::YO, xs);
+    }
+    // fast tiles: every cell within two of the tile is fluid and exists, so
+    // no tile node is a boundary node and node stencils apply everywhere
+    const bool fast = block_all_fluid(g, I0 - 2, I0 + TXC + 1, J0 - 2, J0 + TYC + 1);
+    if (!fast) {
+        for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
+            const int jj = idx / L::FX, ii = idx - jj * L::FX;
+            cf[idx] = (unsigned char)cell_code(g, I0 - 2 + ii, J0 - 2 + jj);
+        }
+    }
+    if constexpr (R > 0) {
+        // x~ = P x_c on the window (the barrier in block_all_fluid published the
+        // coarse nodes), then the Dirichlet velocity where a node has one;
+        // fast tiles have none within the cells they use.
+        for (int e = threadIdx.x; e < L::HX * L::HY; e += blockDim.x) {
+            const int jj = e / L::HX, ii = e - jj * L::HX;
+            const int I = I0 - L::XO + ii, J = J0 - L::YO + jj;
+            T x[3];
+            cw.interp(g, I, J, x);
+            if (!fast && I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf)
+                dirichlet_value(g, I, J, inflow_scale, x[0], x[1]);
+            xs[e] = x[0];
+            xs[L::HY * L::HX + e] = x[1];
+            xs[2 * L::HY * L::HX + e] = x[2];
+        }
     }
     cp_async_wait_all();
-    // Fast tiles: every cell within two of the tile is fluid and exists, so
-    // no tile node is a boundary node and node stencils apply everywhere.
-    const bool fast = __syncthreads_and(all_fluid);
+    __syncthreads();
 
-    // Phase A: cell contributions (fast tiles: convection only)
+    // Phase A: velocity-row contributions of every cell (fast tiles: convection only)
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
         const int ci = cid % L::CX - 1, cj = cid / L::CX - 1;
-        T out[12];
+        T out[8];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) out[k] = T(0);
-        if (cf[(cj + 2) * L::FX + ci + 2] == 1) {
-            const int base = (cj + 2) * L::HX + ci + 2;
+        for (int k = 0; k < 8; ++k) out[k] = T(0);
+        if (fast || cf[(cj + 2) * L::FX + ci + 2] == 1) {
+            const int base = (cj + L::YO) * L::HX + ci + L::XO;
             const int off[4] = {0, 1, L::HX, L::HX + 1};
             T u[4], v[4];
 #pragma unroll
@@ -261,23 +361,19 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
                 for (int b = 0; b < 4; ++b) p[b] = xs[2 * L::HY * L::HX + base + off[b]];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    T au = T(0), av = T(0), ap = T(0);
+                    T au = T(0), av = T(0);
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         au += fc.Av[a][b] * u[b] - fc.Gx[a][b] * p[b];
                         av += fc.Av[a][b] * v[b] - fc.Gy[a][b] * p[b];
-                        ap += fc.Dx[a][b] * u[b] + fc.Dy[a][b] * v[b];
                     }
                     out[a] += au;
                     out[4 + a] += av;
-                    out[8 + a] = ap;
                 }
             }
         }
-        const int nk = fast ? 8 : 12;
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-            if (k < nk) cc[k * L::NCELL + cid] = out[k];
+        for (int k = 0; k < 8; ++k) cc[k * L::NCELL + cid] = out[k];
     }
     // Phase A': LPS contributions of every 2x2-cell patch touching the tile.
     for (int lid = threadIdx.x; lid < L::NLPS; lid += blockDim.x) {
@@ -285,13 +381,13 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
         T out[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i] = T(0);
-        if (cf[(2 * n + 2) * L::FX + 2 * m + 2] == 1) {
+        if (fast || cf[(2 * n + 2) * L::FX + 2 * m + 2] == 1) {
             T p9[9];
 #pragma unroll
             for (int b = 0; b < 3; ++b)
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    p9[3 * b + a] = xs[2 * L::HY * L::HX + (2 * n + b + 2) * L::HX + 2 * m + a + 2];
+                    p9[3 * b + a] = xs[2 * L::HY * L::HX + (2 * n + b + L::YO) * L::HX + 2 * m + a + L::XO];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 T acc = T(0);
@@ -320,22 +416,39 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
                 Au += cc[corner[t] * L::NCELL + cells[t]];
                 Av += cc[(4 + corner[t]) * L::NCELL + cells[t]];
             }
+            const T *pu = xs + (jj + L::YO - 1) * L::HX + ii + L::XO - 1;   // node (ii-1, jj-1)
+            const T *pv = pu + L::HY * L::HX;
+            const T *pp = pv + L::HY * L::HX;
             if (fast) {
-                const T *pu = xs + (jj + 1) * L::HX + ii + 1;      // node (ii-1, jj-1)
-                const T *pv = pu + L::HY * L::HX;
-                const T *pp = pv + L::HY * L::HX;
+                // independent partial sums per stencil row keep the FMA chains short
+                T su[3], sv[3], sp[3];
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
+                for (int dy = 0; dy < 3; ++dy) {
+                    su[dy] = sv[dy] = sp[dy] = T(0);
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const T u = pu[dy * L::HX + dx], v = pv[dy * L::HX + dx], p = pp[dy * L::HX + dx];
-                        Au += fc.nA[dy][dx] * u - fc.nGx[dy][dx] * p;
-                        Av += fc.nA[dy][dx] * v - fc.nGy[dy][dx] * p;
-                        Ap += fc.nDx[dy][dx] * u + fc.nDy[dy][dx] * v;
+                        su[dy] += fc.nA[dy][dx] * u - fc.nGx[dy][dx] * p;
+                        sv[dy] += fc.nA[dy][dx] * v - fc.nGy[dy][dx] * p;
+                        sp[dy] += fc.nDx[dy][dx] * u + fc.nDy[dy][dx] * v;
                     }
+                }
+                Au += (su[0] + su[1]) + su[2];
+                Av += (sv[0] + sv[1]) + sv[2];
+                Ap += (sp[0] + sp[1]) + sp[2];
             } else {
+                // divergence rows from the fluid cells around the node
 #pragma unroll
-                for (int t = 0; t < 4; ++t) Ap += cc[(8 + corner[t]) * L::NCELL + cells[t]];
+                for (int t = 0; t < 4; ++t) {
+                    const int cx = t & 1, cy = t >> 1;   // cell SW, SE, NW, NE of the node
+                    if (cf[(jj + 1 + cy) * L::FX + ii + 1 + cx] != 1) continue;
+                    const int a = corner[t];
+                    const T *cu = pu + cy * L::HX + cx, *cvp = pv + cy * L::HX + cx;
+                    const T ub[4] = {cu[0], cu[1], cu[L::HX], cu[L::HX + 1]};
+                    const T vb[4] = {cvp[0], cvp[1], cvp[L::HX], cvp[L::HX + 1]};
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) Ap += fc.Dx[a][b] * ub[b] + fc.Dy[a][b] * vb[b];
+                }
             }
             const int nmx = (ii & 1) ? 1 : 2, nmy = (jj & 1) ? 1 : 2;
             for (int ty = 0; ty < nmy; ++ty) {
@@ -356,17 +469,17 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
                 p_active = nc.p_active;
             }
             if (!dirichlet) {
-                ru = bs[jj * NXN + ii] - Au;
-                rv = bs[NYN * NXN + jj * NXN + ii] - Av;
+                ru = bs[jj * L::BX + ii] - Au;
+                rv = bs[NYN * L::BX + jj * L::BX + ii] - Av;
             }
             if (p_active) rp = -Ap;
             // a node on the tile's right/top edge belongs to the next tile
             // (which may take the other path): write owned nodes only
             if (rf && (ii < TXC || I == g.nxf) && (jj < TYC || J == g.nyf)) {
-                const size_t node = (size_t)J * nxn + I;
+                const size_t node = (size_t)J * g.pitch + I;
                 rf[node] = ru;
-                rf[Nf + node] = rv;
-                rf[2 * Nf + node] = rp;
+                rf[g.plane + node] = rv;
+                rf[2 * g.plane + node] = rp;
             }
         }
         rs[nid] = ru;
@@ -391,6 +504,7 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
         const T *rbase = rs + lpy * S * NXN + lpx * S;
         const T *xbase = xs + lpy * S * L::HX + lpx * S;
         TX *row = X + (size_t)id * g.ldx;
+#pragma unroll 4
         for (int c = lane; c < g.ldx; c += 32) {
             const int e = __ldg(g.feat_tab + c);
             const int kind = e >> 24, off = e & 0xFFFFFF;
@@ -413,30 +527,65 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const T
 }
 
 // ------------------------------------------------------------------ S5
-template <typename T>
+// Same tiling as S1: 4 consecutive nodes per thread.  R = 0: v~ is read from
+// xf; R = 2, 4, 8: v~ is interpolated from xc inside the tile (S1 fused).
+template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS)
-k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, T *__restrict__ vc) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y;
-    if (I > g.nxf) return;
-    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
-    const size_t node = (size_t)J * nxn + I;
-    T u = xf[node], v = xf[Nf + node];
-    const NodeClass nc = classify_global(g, I, J);
-    if (!nc.dirichlet) {
-        const int S = g.S;
-        int pis[2], pjs[2], npi = 0, npj = 0;
+k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, const double *__restrict__ xc,
+              double inflow_scale, T *__restrict__ vc) {
+    using CWin = CoarseWin<T, (R > 0 ? R : 2), PTX, PTY>;
+    __shared__ T cs_mem[R > 0 ? CWin::N : 1];
+    const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
+    CWin cw;
+    cw.cs = cs_mem;
+    if constexpr (R > 0) cw.stage(g, xc, I0, J0);
+    const bool fast = block_all_fluid(g, I0 - 1, I0 + PTX, J0 - 1, J0 + PTY);
+    const int J = J0 + threadIdx.x / (PTX / 4);
+    const int Ib = I0 + 4 * (threadIdx.x % (PTX / 4));
+    if (J > g.nyf) return;
+    const size_t node = (size_t)J * g.pitch + Ib;
+    const int S = g.S;
+    // patch rows containing J: one, or two on a patch edge (lower one first)
+    int pjs[2], npj = 0;
+    if (J % S == 0) {
+        if (J / S - 1 >= 0) pjs[npj++] = J / S - 1;
+        if (J / S < g.npy) pjs[npj++] = J / S;
+    } else {
+        pjs[npj++] = J / S;
+    }
+    T u[4], v[4];
+    if constexpr (R > 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T x[3];
+            cw.interp(g, Ib + q, J, x);
+            u[q] = x[0];
+            v[q] = x[1];
+        }
+    } else {
+        load4(xf + node, u);
+        load4(xf + g.plane + node, v);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int I = Ib + q;
+        if (I > g.nxf) continue;
+        if (!fast) {
+            T uD, vD;
+            if (dirichlet_value(g, I, J, inflow_scale, uD, vD)) {   // keeps v~ = the boundary value
+                if constexpr (R > 0) {
+                    u[q] = uD;
+                    v[q] = vD;
+                }
+                continue;
+            }
+        }
+        int pis[2], npi = 0;
         if (I % S == 0) {
             if (I / S - 1 >= 0) pis[npi++] = I / S - 1;
             if (I / S < g.npx) pis[npi++] = I / S;
         } else {
             pis[npi++] = I / S;
-        }
-        if (J % S == 0) {
-            if (J / S - 1 >= 0) pjs[npj++] = J / S - 1;
-            if (J / S < g.npy) pjs[npj++] = J / S;
-        } else {
-            pjs[npj++] = J / S;
         }
         T su = T(0), sv = T(0);
         int cnt = 0;
@@ -450,17 +599,19 @@ k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, T *
                 ++cnt;
             }
         if (cnt) {
-            u += su / T(cnt);
-            v += sv / T(cnt);
+            u[q] += su / T(cnt);
+            v[q] += sv / T(cnt);
         }
     }
-    vc[node] = u;
-    vc[Nf + node] = v;
+    store4(vc + node, u);
+    store4(vc + g.plane + node, v);
 }
 
 // ------------------------------------------------------------------ S6
+// Node window of v_corr: columns I0-4 .. I0+35 (node I0+ii at column ii+4),
+// rows J0-1 .. J0+17 (node J0+jj at row jj+1).
 struct RhsLayout {
-    static constexpr int HX = NXN + 2, HY = NYN + 2;   // nodes with 1-node halo
+    static constexpr int HX = 40, HY = NYN + 2, XO = 4, YO = 1;
     static constexpr int CX = TXC + 2, CY = TYC + 2;   // cells -1..TXC
     static constexpr int NCELL = CX * CY;
     static constexpr int VS = 2 * HY * HX;
@@ -479,27 +630,25 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
     T *cc = vs + L::VS;                        // [8][NCELL]
     unsigned char *cf = reinterpret_cast<unsigned char *>(cc + L::CC);  // [CY][CX]
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
-    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
 
-    stage_rows(g, vcorr, Nf, 2, I0 - 1, J0 - 1, L::HX, L::HY, vs);
-    bool all_fluid = true;
-#pragma unroll 3
-    for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
-        const int jj = idx / L::CX, ii = idx - jj * L::CX;
-        const int code = cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
-        cf[idx] = (unsigned char)code;
-        all_fluid &= code == 1;
+    stage_window<T, 2, L::HY, L::HX>(g, vcorr, I0 - L::XO, J0 - L::YO, vs);
+    const bool fast = block_all_fluid(g, I0 - 1, I0 + TXC, J0 - 1, J0 + TYC);
+    if (!fast) {
+        for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
+            const int jj = idx / L::CX, ii = idx - jj * L::CX;
+            cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
+        }
     }
     cp_async_wait_all();
-    const bool fast = __syncthreads_and(all_fluid);
+    __syncthreads();
 
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
         T out[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) out[k] = T(0);
-        if (cf[cid] == 1) {
-            const int ci = cid % L::CX, cj = cid / L::CX;   // halo-relative node of SW corner
-            const int base = cj * L::HX + ci;
+        if (fast || cf[cid] == 1) {
+            const int ci = cid % L::CX, cj = cid / L::CX;   // cell (ci-1, cj-1) of the tile
+            const int base = cj * L::HX + ci + L::XO - 1;    // its SW node
             const int off[4] = {0, 1, L::HX, L::HX + 1};
             T u[4], v[4];
 #pragma unroll
@@ -549,22 +698,27 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
             bv += cc[(4 + corner[t]) * L::NCELL + cells[t]];
         }
         if (fast) {
-            const T *pu = vs + jj * L::HX + ii;   // node (ii-1, jj-1)
+            const T *pu = vs + jj * L::HX + ii + L::XO - 1;   // node (ii-1, jj-1)
             const T *pv = pu + L::HY * L::HX;
+            T su[3], sv[3];
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
+            for (int dy = 0; dy < 3; ++dy) {
+                su[dy] = sv[dy] = T(0);
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx) {
-                    bu += fc.nB[dy][dx] * pu[dy * L::HX + dx];
-                    bv += fc.nB[dy][dx] * pv[dy * L::HX + dx];
+                    su[dy] += fc.nB[dy][dx] * pu[dy * L::HX + dx];
+                    sv[dy] += fc.nB[dy][dx] * pv[dy * L::HX + dx];
                 }
+            }
+            bu += (su[0] + su[1]) + su[2];
+            bv += (sv[0] + sv[1]) + sv[2];
         } else {
             const NodeClass nc = classify(cf[cells[0]], cf[cells[1]], cf[cells[2]], cf[cells[3]], I, J, g.nyf);
             if (nc.dirichlet) bu = bv = T(0);
         }
-        const size_t node = (size_t)J * nxn + I;
+        const size_t node = (size_t)J * g.pitch + I;
         bf[node] = bu;
-        bf[Nf + node] = bv;
+        bf[g.plane + node] = bv;
     }
 }
 
@@ -608,29 +762,32 @@ struct RestrictAcc64 {
     static __device__ __forceinline__ double out(Row a) { return a; }
 };
 
-template <typename T, typename Acc>
+// Fine columns staged per tile: ci0 r - 8 .. ci0 r + 135 (16-byte aligned start;
+// covers ci r +- (r-1) for the tile's 128/r coarse columns when r <= 8).
+constexpr int RFW = 128 + 16, RXO = 8;
+
+template <typename T, typename Acc, int R>
 __global__ void __launch_bounds__(NTHREADS)
 k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
     using Row = typename Acc::Row;
+    constexpr int TCX = 128 / R, TCY = 32 / R;              // coarse nodes per tile
+    constexpr int FH = TCY * R + R - 1;                     // fine rows staged
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int r = g.r;
-    const int TCX = 128 / r, TCY = 32 / r;           // coarse nodes per tile
-    const int FW = TCX * r + r - 1, FH = TCY * r + r - 1;   // fine nodes staged
-    T *fs = reinterpret_cast<T *>(smem_raw);         // [2][FH][FW]
-    Row *rs = reinterpret_cast<Row *>(fs + 2 * FH * FW);   // [2][FH][TCX] x-restricted rows
+    T *fs = reinterpret_cast<T *>(smem_raw);                // [2][FH][RFW]
+    Row *rs = reinterpret_cast<Row *>(fs + 2 * FH * RFW);   // [2][FH][TCX] x-restricted rows
     const int ci0 = blockIdx.x * TCX, cj0 = blockIdx.y * TCY;
-    const int I0 = ci0 * r - (r - 1), J0 = cj0 * r - (r - 1);
-    const size_t nxn = (size_t)g.nxf + 1, Nf = nxn * (g.nyf + 1);
-    stage_rows(g, bf, Nf, 2, I0, J0, FW, FH, fs);
+    stage_window<T, 2, FH, RFW>(g, bf, ci0 * R - RXO, cj0 * R - (R - 1), fs);
     cp_async_wait_all();
     __syncthreads();
-    const T inv_r = T(1) / T(r);
+    constexpr T inv_r = T(1) / T(R);
     for (int e = threadIdx.x; e < 2 * FH * TCX; e += blockDim.x) {
         const int c = e / (FH * TCX), rem = e - c * (FH * TCX);
         const int jj = rem / TCX, ci = rem - jj * TCX;
-        const T *row = fs + c * FH * FW + jj * FW + ci * r;   // fine nodes ci*r-(r-1) .. ci*r+(r-1)
+        // fine nodes (ci0+ci) R - (R-1) .. (ci0+ci) R + (R-1), staged from column ci R - (R-1) + RXO
+        const T *row = fs + c * FH * RFW + jj * RFW + ci * R - (R - 1) + RXO;
         Row acc = Acc::zero();
-        for (int d = 0; d < 2 * r - 1; ++d) Acc::add(acc, T(r - abs(d - (r - 1))) * inv_r, row[d]);
+#pragma unroll
+        for (int d = 0; d < 2 * R - 1; ++d) Acc::add(acc, T(R - abs(d - (R - 1))) * inv_r, row[d]);
         rs[e] = acc;
     }
     __syncthreads();
@@ -643,8 +800,9 @@ k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             Row acc = Acc::zero();
-            for (int d = 0; d < 2 * r - 1; ++d)
-                Acc::add(acc, T(r - abs(d - (r - 1))) * inv_r, rs[c * FH * TCX + (lj * r + d) * TCX + li]);
+#pragma unroll
+            for (int d = 0; d < 2 * R - 1; ++d)
+                Acc::add(acc, T(R - abs(d - (R - 1))) * inv_r, rs[c * FH * TCX + (lj * R + d) * TCX + li]);
             out[c] = Acc::out(acc);
         }
         bool ts = false;
@@ -661,10 +819,31 @@ k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
     }
 }
 
+template <typename T, typename Acc, int R>
+size_t restrict_smem() {
+    const size_t FH = (size_t)(32 / R) * R + R - 1;
+    return 2 * FH * RFW * sizeof(T) + 2 * FH * (128 / R) * sizeof(typename Acc::Row);
+}
+
+template <typename T, typename Acc, int R>
+cudaError_t run_restrict(const MeshGeom &g, const T *bf, double *bc, cudaStream_t st) {
+    constexpr int TCX = 128 / R, TCY = 32 / R;
+    const dim3 grid((unsigned)((g.nxc + TCX) / TCX), (unsigned)((g.nyc + TCY) / TCY));
+    const size_t sm = restrict_smem<T, Acc, R>();
+    cudaError_t e = cudaFuncSetAttribute(k_restrict<T, Acc, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_restrict<T, Acc, R><<<grid, NTHREADS, sm, st>>>(g, bf, bc);
+    return cudaGetLastError();
+}
+
 template <typename T, typename Acc>
-size_t restrict_smem(int r) {
-    const int FW = 128 + r - 1, FH = 32 + r - 1;
-    return 2 * FH * FW * sizeof(T) + 2 * FH * (128 / r) * sizeof(typename Acc::Row);
+cudaError_t run_restrict_r(const MeshGeom &g, const T *bf, double *bc, cudaStream_t st) {
+    switch (g.r) {
+        case 2: return run_restrict<T, Acc, 2>(g, bf, bc, st);
+        case 4: return run_restrict<T, Acc, 4>(g, bf, bc, st);
+        case 8: return run_restrict<T, Acc, 8>(g, bf, bc, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // ------------------------------------------------------------------ maps
@@ -672,7 +851,7 @@ __global__ void k_mesh_maps(MeshGeom g, unsigned char *flags, unsigned char *mul
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y;
     if (I > g.nxf) return;
-    const size_t node = (size_t)J * ((size_t)g.nxf + 1) + I;
+    const size_t node = (size_t)J * g.pitch + I;
     if (flags) {
         const NodeClass nc = classify_global(g, I, J);
         flags[node] = (unsigned char)((nc.dirichlet ? 1 : 0) | (nc.inflow ? 2 : 0) | (nc.p_active ? 4 : 0));
@@ -696,6 +875,9 @@ dim3 node_grid(const MeshGeom &g) {
 dim3 tile_grid(const MeshGeom &g) {
     return dim3((unsigned)((g.nxf + TXC - 1) / TXC), (unsigned)((g.nyf + TYC - 1) / TYC));
 }
+dim3 node_tile_grid(const MeshGeom &g) {
+    return dim3((unsigned)((g.nxf + PTX) / PTX), (unsigned)((g.nyf + PTY) / PTY));
+}
 
 template <typename KernelT>
 cudaError_t set_smem(KernelT k, size_t bytes) {
@@ -717,60 +899,90 @@ void feature_table(const MeshGeom &g, int *tab) {
     for (int comp = 0; comp < 3; ++comp)
         for (int b = 0; b < s1; ++b)
             for (int a = 0; a < s1; ++a) {
-                const int off = (b * g.r + 2) * L::HX + a * g.r + 2;
+                const int off = (b * g.r + L::YO) * L::HX + a * g.r + L::XO;
                 tab[c++] = comp < 2 ? (FEAT_VEL << 24) | (comp * L::HY * L::HX + off) : (FEAT_PECLET << 24) | off;
             }
     for (int k = 0; k < 12; ++k) tab[c++] = (FEAT_GEO << 24) | k;
     while (c < g.ldx) tab[c++] = FEAT_ZERO << 24;
 }
 
-cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, void *xf, double t,
-                              cudaStream_t st) {
-    double w = 1.0;
-    if (g.ramp) w = t <= 0.5 ? 0.5 - 0.5 * cos(2.0 * 3.14159265358979323846 * t) : 1.0;
-    const dim3 grid((unsigned)((g.nxf + PTX) / PTX), (unsigned)((g.nyf + PTY) / PTY));
-    if (prec == DNNMG_F64)
-        k_prolongate<double><<<grid, NTHREADS, 0, st>>>(g, xc, (double *)xf, w);
-    else
-        k_prolongate<float><<<grid, NTHREADS, 0, st>>>(g, xc, (float *)xf, w);
-    return cudaGetLastError();
+int feature_table_capacity() { return ResLayout::MAX_LDX; }
+
+double inflow_ramp(const MeshGeom &g, double t) {
+    return g.ramp ? (t <= 0.5 ? 0.5 - 0.5 * cos(2.0 * 3.14159265358979323846 * t) : 1.0) : 1.0;
 }
 
-cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<double> &f64,
-                                     const FemCoef<float> &f32, const void *xf, const void *bf,
-                                     void *rf, void *X, cudaStream_t st) {
-    cudaError_t e;
-    if (prec == DNNMG_F64) {
-        auto k = k_residual_features<double, double>;
-        const size_t sm = ResLayout::bytes<double>();
-        if ((e = set_smem(k, sm)) != cudaSuccess) return e;
-        k<<<tile_grid(g), NTHREADS, sm, st>>>(g, f64, (const double *)xf, (const double *)bf,
-                                              (double *)rf, (double *)X);
-    } else if (prec == DNNMG_F32) {
-        auto k = k_residual_features<float, float>;
-        const size_t sm = ResLayout::bytes<float>();
-        if ((e = set_smem(k, sm)) != cudaSuccess) return e;
-        k<<<tile_grid(g), NTHREADS, sm, st>>>(g, f32, (const float *)xf, (const float *)bf,
-                                              (float *)rf, (float *)X);
-    } else {
-        auto k = k_residual_features<float, __nv_bfloat16>;
-        const size_t sm = ResLayout::bytes<float>();
-        if ((e = set_smem(k, sm)) != cudaSuccess) return e;
-        k<<<tile_grid(g), NTHREADS, sm, st>>>(g, f32, (const float *)xf, (const float *)bf,
-                                              (float *)rf, (__nv_bfloat16 *)X);
+template <typename T>
+cudaError_t run_prolongate(const MeshGeom &g, const double *xc, T *xf, double w, cudaStream_t st) {
+    switch (g.r) {
+        case 2: k_prolongate<T, 2><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, xc, xf, w); break;
+        case 4: k_prolongate<T, 4><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, xc, xf, w); break;
+        case 8: k_prolongate<T, 8><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, xc, xf, w); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf,
-                               void *vcorr, cudaStream_t st) {
-    if (prec == DNNMG_F64)
-        k_scatter_avg<double><<<node_grid(g), NTHREADS, 0, st>>>(g, (const double *)d,
-                                                                 (const double *)xf, (double *)vcorr);
-    else
-        k_scatter_avg<float><<<node_grid(g), NTHREADS, 0, st>>>(g, (const float *)d,
-                                                                (const float *)xf, (float *)vcorr);
+cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, void *xf, double t,
+                              cudaStream_t st) {
+    const double w = inflow_ramp(g, t);
+    if (prec == DNNMG_F64) return run_prolongate(g, xc, (double *)xf, w, st);
+    return run_prolongate(g, xc, (float *)xf, w, st);
+}
+
+template <typename T, typename TX, int R>
+cudaError_t run_residual(const MeshGeom &g, const FemCoef<T> &fc, const void *xf, const double *xc, double w,
+                         const void *bf, void *rf, void *X, cudaStream_t st) {
+    auto k = k_residual_features<T, TX, R>;
+    const size_t sm = ResLayout::bytes<T>(R > 0);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, (const T *)xf, xc, w, (const T *)bf, (T *)rf, (TX *)X);
     return cudaGetLastError();
+}
+
+template <typename T, typename TX>
+cudaError_t run_residual_r(const MeshGeom &g, const FemCoef<T> &fc, const void *xf, const double *xc, double w,
+                           const void *bf, void *rf, void *X, cudaStream_t st) {
+    if (!xc) return run_residual<T, TX, 0>(g, fc, xf, xc, w, bf, rf, X, st);
+    switch (g.r) {
+        case 2: return run_residual<T, TX, 2>(g, fc, xf, xc, w, bf, rf, X, st);
+        case 4: return run_residual<T, TX, 4>(g, fc, xf, xc, w, bf, rf, X, st);
+        case 8: return run_residual<T, TX, 8>(g, fc, xf, xc, w, bf, rf, X, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<double> &f64,
+                                     const FemCoef<float> &f32, const void *xf, const double *xc, double t,
+                                     const void *bf, void *rf, void *X, cudaStream_t st) {
+    const double w = inflow_ramp(g, t);
+    if (prec == DNNMG_F64) return run_residual_r<double, double>(g, f64, xf, xc, w, bf, rf, X, st);
+    if (prec == DNNMG_F32) return run_residual_r<float, float>(g, f32, xf, xc, w, bf, rf, X, st);
+    return run_residual_r<float, __nv_bfloat16>(g, f32, xf, xc, w, bf, rf, X, st);
+}
+
+template <typename T>
+cudaError_t run_scatter(const MeshGeom &g, const T *d, const T *xf, const double *xc, double w, T *vc,
+                        cudaStream_t st) {
+    if (!xc) {
+        k_scatter_avg<T, 0><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc);
+        return cudaGetLastError();
+    }
+    switch (g.r) {
+        case 2: k_scatter_avg<T, 2><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
+        case 4: k_scatter_avg<T, 4><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
+        case 8: k_scatter_avg<T, 8><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf, const double *xc,
+                               double t, void *vcorr, cudaStream_t st) {
+    const double w = inflow_ramp(g, t);
+    if (prec == DNNMG_F64) return run_scatter(g, (const double *)d, (const double *)xf, xc, w, (double *)vcorr, st);
+    return run_scatter(g, (const float *)d, (const float *)xf, xc, w, (float *)vcorr, st);
 }
 
 cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
@@ -790,19 +1002,8 @@ cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
 
 cudaError_t launch_restrict(const MeshGeom &g, int prec, const void *bf, double *bc,
                             cudaStream_t st) {
-    const int TCX = 128 / g.r, TCY = 32 / g.r;
-    const dim3 grid((unsigned)((g.nxc + TCX) / TCX), (unsigned)((g.nyc + TCY) / TCY));
-    cudaError_t e;
-    if (prec == DNNMG_F64) {
-        const size_t sm = restrict_smem<double, RestrictAcc64>(g.r);
-        if ((e = set_smem(k_restrict<double, RestrictAcc64>, sm)) != cudaSuccess) return e;
-        k_restrict<double, RestrictAcc64><<<grid, NTHREADS, sm, st>>>(g, (const double *)bf, bc);
-    } else {
-        const size_t sm = restrict_smem<float, RestrictAcc32>(g.r);
-        if ((e = set_smem(k_restrict<float, RestrictAcc32>, sm)) != cudaSuccess) return e;
-        k_restrict<float, RestrictAcc32><<<grid, NTHREADS, sm, st>>>(g, (const float *)bf, bc);
-    }
-    return cudaGetLastError();
+    if (prec == DNNMG_F64) return run_restrict_r<double, RestrictAcc64>(g, (const double *)bf, bc, st);
+    return run_restrict_r<float, RestrictAcc32>(g, (const float *)bf, bc, st);
 }
 
 cudaError_t launch_mesh_maps(const MeshGeom &g, unsigned char *flags, unsigned char *mult,

@@ -43,7 +43,8 @@ class MeshDesc(ctypes.Structure):
 class MeshInfo(ctypes.Structure):
     _fields_ = [("nxc", ctypes.c_int), ("nyc", ctypes.c_int), ("nxf", ctypes.c_int), ("nyf", ctypes.c_int),
                 ("K", ctypes.c_int), ("s", ctypes.c_int), ("npx", ctypes.c_int), ("npy", ctypes.c_int),
-                ("Nc", ctypes.c_longlong), ("Nf", ctypes.c_longlong), ("P", ctypes.c_int),
+                ("Nc", ctypes.c_longlong), ("Nf", ctypes.c_longlong),
+                ("pitch", ctypes.c_int), ("plane", ctypes.c_longlong), ("P", ctypes.c_int),
                 ("nf", ctypes.c_int), ("nc", ctypes.c_int), ("n_in", ctypes.c_int), ("n_out", ctypes.c_int),
                 ("ldx", ctypes.c_int), ("n_solid_coarse", ctypes.c_int), ("precision", ctypes.c_int),
                 ("real_bytes", ctypes.c_int), ("feature_bytes", ctypes.c_int),
@@ -68,14 +69,15 @@ def _load():
         "dnnmg_net_create": [I, I, I, P, P, P, I, ctypes.POINTER(P)],
         "dnnmg_net_destroy": [P],
         "dnnmg_prolongate": [P, P, P, D, P],
-        "dnnmg_patch_features": [P, P, P, P, P, P],
+        "dnnmg_patch_features": [P, P, P, D, P, P, P, P],
         "dnnmg_gru_step": [P, P, P, P, I, P],
-        "dnnmg_scatter_avg": [P, P, P, P, P],
+        "dnnmg_scatter_avg": [P, P, P, P, D, P, P],
         "dnnmg_rhs_restrict": [P, P, P, P, P],
         "dnnmg_step": [P, P, P, P, P, P, P, S, D, P],
         "dnnmg_step_host": [P, P, P, P, P, P, P, S, D, P],
         "dnnmg_step_launches": [P, P],
         "dnnmg_restrict": [P, P, P, P],
+        "dnnmg_rhs": [P, P, P, P],
         "dnnmg_net_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_net_uses_tensor_cores": [P],
     }
@@ -171,7 +173,23 @@ class Mesh:
 
     # convenience allocators (device memory from torch)
     def fine(self, ncomp, device="cuda"):
-        return torch.zeros(ncomp, self.info.Nf, dtype=self.real, device=device)
+        """A zeroed fine field [ncomp][plane] in the pitched layout."""
+        return torch.zeros(ncomp, self.info.plane, dtype=self.real, device=device)
+
+    def pack(self, a, device="cuda"):
+        """Node-ordered values [ncomp][Nf] (x fastest) -> pitched device field [ncomp][plane]."""
+        I = self.info
+        t = torch.as_tensor(a)
+        ncomp = t.shape[0]
+        out = torch.zeros(ncomp, I.nyf + 1, I.pitch, dtype=self.real)
+        out[:, :, :I.nxf + 1] = t.reshape(ncomp, I.nyf + 1, I.nxf + 1).to(self.real)
+        return out.reshape(ncomp, I.plane).to(device).contiguous()
+
+    def unpack(self, t):
+        """Pitched field [ncomp][plane] -> node-ordered float64 numpy [ncomp][Nf]."""
+        I = self.info
+        a = t.detach().reshape(-1, I.nyf + 1, I.pitch)[:, :, :I.nxf + 1]
+        return a.double().cpu().numpy().reshape(a.shape[0], -1)
 
     def coarse(self, ncomp=3, device="cuda"):
         return torch.zeros(ncomp, self.info.Nc, dtype=torch.float64, device=device)
@@ -219,9 +237,9 @@ def dnnmg_mesh_maps(mesh, patch_cell=None, node_flags=None, node_mult=None, stre
     if patch_cell is not None:
         _need(patch_cell, torch.int32, I.P, "patch_cell")
     if node_flags is not None:
-        _need(node_flags, torch.uint8, I.Nf, "node_flags")
+        _need(node_flags, torch.uint8, I.plane, "node_flags")
     if node_mult is not None:
-        _need(node_mult, torch.uint8, I.Nf, "node_mult")
+        _need(node_mult, torch.uint8, I.plane, "node_mult")
     _check(_lib.dnnmg_mesh_maps(mesh.handle, _ptr(patch_cell), _ptr(node_flags), _ptr(node_mult),
                                 _stream(stream)))
 
@@ -229,18 +247,26 @@ def dnnmg_mesh_maps(mesh, patch_cell=None, node_flags=None, node_mult=None, stre
 def dnnmg_prolongate(mesh, xc, xf, t, stream=None):
     I = mesh.info
     _need(xc, torch.float64, 3 * I.Nc, "xc")
-    _need(xf, mesh.real, 3 * I.Nf, "xf")
+    _need(xf, mesh.real, 3 * I.plane, "xf")
     _check(_lib.dnnmg_prolongate(mesh.handle, _ptr(xc), _ptr(xf), float(t), _stream(stream)))
 
 
-def dnnmg_patch_features(mesh, xf, bf, X, rf=None, stream=None):
+def dnnmg_patch_features(mesh, xf, bf, X, rf=None, xc=None, t=0.0, stream=None):
+    """S2+S3.  Give x~ as xf [3][plane], or pass xf=None and xc [3][Nc] (with t)
+    to form x~ = P xc inside the kernel."""
     I = mesh.info
-    _need(xf, mesh.real, 3 * I.Nf, "xf")
-    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    if (xf is None) == (xc is None):
+        raise ValueError("give exactly one of xf and xc")
+    if xf is not None:
+        _need(xf, mesh.real, 3 * I.plane, "xf")
+    else:
+        _need(xc, torch.float64, 3 * I.Nc, "xc")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
     _need(X, mesh.feat, I.P * I.ldx, "X")
     if rf is not None:
-        _need(rf, mesh.real, 3 * I.Nf, "rf")
-    _check(_lib.dnnmg_patch_features(mesh.handle, _ptr(xf), _ptr(bf), _ptr(rf), _ptr(X), _stream(stream)))
+        _need(rf, mesh.real, 3 * I.plane, "rf")
+    _check(_lib.dnnmg_patch_features(mesh.handle, _ptr(xf), _ptr(xc), float(t), _ptr(bf), _ptr(rf), _ptr(X),
+                                     _stream(stream)))
 
 
 def dnnmg_gru_step(net, X, h, d, P, stream=None):
@@ -251,25 +277,39 @@ def dnnmg_gru_step(net, X, h, d, P, stream=None):
     _check(_lib.dnnmg_gru_step(net.handle, _ptr(X), _ptr(h), _ptr(d), int(P), _stream(stream)))
 
 
-def dnnmg_scatter_avg(mesh, d, xf, vcorr, stream=None):
+def dnnmg_scatter_avg(mesh, d, xf, vcorr, xc=None, t=0.0, stream=None):
+    """S5.  Give v~ as xf [3][plane], or pass xf=None and xc [3][Nc] (with t)."""
     I = mesh.info
+    if (xf is None) == (xc is None):
+        raise ValueError("give exactly one of xf and xc")
     _need(d, mesh.real, I.P * I.n_out, "d")
-    _need(xf, mesh.real, 3 * I.Nf, "xf")
-    _need(vcorr, mesh.real, 2 * I.Nf, "vcorr")
-    _check(_lib.dnnmg_scatter_avg(mesh.handle, _ptr(d), _ptr(xf), _ptr(vcorr), _stream(stream)))
+    if xf is not None:
+        _need(xf, mesh.real, 3 * I.plane, "xf")
+    else:
+        _need(xc, torch.float64, 3 * I.Nc, "xc")
+    _need(vcorr, mesh.real, 2 * I.plane, "vcorr")
+    _check(_lib.dnnmg_scatter_avg(mesh.handle, _ptr(d), _ptr(xf), _ptr(xc), float(t), _ptr(vcorr),
+                                  _stream(stream)))
 
 
 def dnnmg_rhs_restrict(mesh, vcorr, bf, bc, stream=None):
     I = mesh.info
-    _need(vcorr, mesh.real, 2 * I.Nf, "vcorr")
-    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(vcorr, mesh.real, 2 * I.plane, "vcorr")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
     _need(bc, torch.float64, 3 * I.Nc, "bc")
     _check(_lib.dnnmg_rhs_restrict(mesh.handle, _ptr(vcorr), _ptr(bf), _ptr(bc), _stream(stream)))
 
 
+def dnnmg_rhs(mesh, vcorr, bf, stream=None):
+    I = mesh.info
+    _need(vcorr, mesh.real, 2 * I.plane, "vcorr")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
+    _check(_lib.dnnmg_rhs(mesh.handle, _ptr(vcorr), _ptr(bf), _stream(stream)))
+
+
 def dnnmg_restrict(mesh, bf, bc, stream=None):
     I = mesh.info
-    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
     _need(bc, torch.float64, 3 * I.Nc, "bc")
     _check(_lib.dnnmg_restrict(mesh.handle, _ptr(bf), _ptr(bc), _stream(stream)))
 
@@ -289,7 +329,7 @@ def dnnmg_step(mesh, net, xc, h, bf, bc, workspace, t, stream=None):
     I = mesh.info
     _need(xc, torch.float64, 3 * I.Nc, "xc")
     _need(h, mesh.real, I.P * net.H, "h")
-    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
     _need(bc, torch.float64, 3 * I.Nc, "bc")
     if workspace.dtype != torch.uint8 or not workspace.is_cuda:
         raise TypeError("workspace must be a CUDA uint8 tensor")
@@ -304,7 +344,7 @@ def dnnmg_step_host(mesh, net, xc_host, h, bf, bc_host, workspace, t, stream=Non
         if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != 3 * I.Nc:
             raise TypeError(f"{name} must be a contiguous CPU float64 tensor of {3 * I.Nc} elements")
     _need(h, mesh.real, I.P * net.H, "h")
-    _need(bf, mesh.real, 2 * I.Nf, "bf")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
     _check(_lib.dnnmg_step_host(mesh.handle, net.handle, _ptr(xc_host), _ptr(h), _ptr(bf), _ptr(bc_host),
                                 _ptr(workspace), workspace.numel(), float(t), _stream(stream)))
 

@@ -38,13 +38,13 @@ def gpu_run(dn, c, prec, steps, xc_t, v0, h0):
     real = mesh.real
     bf = mesh.fine(2)
     bc = mesh.coarse(3)
-    dn.dnnmg_rhs_restrict(mesh, torch.as_tensor(v0).to(real).cuda().contiguous(), bf, bc)
+    dn.dnnmg_rhs_restrict(mesh, mesh.pack(v0), bf, bc)
     h = torch.as_tensor(h0).to(real).cuda().contiguous()
     ws = mesh.workspace()
     for n in range(steps):
         dn.dnnmg_step(mesh, net, torch.as_tensor(xc_t[n]).cuda().contiguous(), h, bf, bc, ws, n * PRM.k)
     torch.cuda.synchronize()
-    out = {"h": h.double().cpu().numpy(), "bf": bf.double().cpu().numpy(), "bc": bc.cpu().numpy()}
+    out = {"h": h.double().cpu().numpy(), "bf": mesh.unpack(bf), "bc": bc.cpu().numpy()}
     assert dn.dnnmg_net_status(net) == 0
     return mesh, W, out
 

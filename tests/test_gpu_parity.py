@@ -54,14 +54,15 @@ def test_index_maps_bit_exact(dn, name):
     I = m.info
     assert I.P == om.P
     pc = torch.zeros(I.P, dtype=torch.int32, device="cuda")
-    fl = torch.zeros(I.Nf, dtype=torch.uint8, device="cuda")
-    mu = torch.zeros(I.Nf, dtype=torch.uint8, device="cuda")
+    fl = torch.zeros(I.plane, dtype=torch.uint8, device="cuda")
+    mu = torch.zeros(I.plane, dtype=torch.uint8, device="cuda")
     dn.dnnmg_mesh_maps(m, pc, fl, mu)
     torch.cuda.synchronize()
     exp_pc = om.patches[:, 1] * om.npx + om.patches[:, 0]
     assert np.array_equal(pc.cpu().numpy(), exp_pc)
-    assert np.array_equal(fl.cpu().numpy(), om.fine_node_flags().ravel())
-    assert np.array_equal(mu.cpu().numpy(), om.multiplicity.ravel())
+    nodes = lambda t: t.cpu().numpy().reshape(I.nyf + 1, I.pitch)[:, :I.nxf + 1].ravel()
+    assert np.array_equal(nodes(fl), om.fine_node_flags().ravel())
+    assert np.array_equal(nodes(mu), om.multiplicity.ravel())
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -73,7 +74,7 @@ def test_prolongate(dn, name):
     xf = m.fine(3)
     dn.dnnmg_prolongate(m, cuda(xc, torch.float64), xf, 0.3)
     ref = transfer.prolongate(om, PRM, xc, 0.3)
-    got = host(xf).reshape(3, -1)
+    got = m.unpack(xf)
     tol = 1e-14 if case["prec"] == "f64" else 1e-7
     assert rel_l2(got, ref) <= tol
     # Dirichlet values are set exactly as the oracle sets them
@@ -90,10 +91,10 @@ def test_residual_and_features(dn, name):
     bf = as_real(case, rhs_like(case))
     X = m.features()
     rf = m.fine(3)
-    dn.dnnmg_patch_features(m, cuda(xf, m.real), cuda(bf, m.real), X, rf=rf)
+    dn.dnnmg_patch_features(m, m.pack(xf), m.pack(bf), X, rf=rf)
     r_ref = fem.residual(om, PRM, xf, bf)
     X_ref = features.patch_features(om, PRM, xf, r_ref)
-    r_got = host(rf).reshape(3, -1)
+    r_got = m.unpack(rf)
     tol_r = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
     for c in range(3):
         assert rel_l2(r_got[c], r_ref[c]) <= tol_r, c
@@ -144,13 +145,13 @@ def test_scatter_avg(dn, name):
     d = as_real(case, rng.normal(0.0, 0.3, (om.P, om.n_out)))
     xf = as_real(case, fine_velocity(case))
     vc = m.fine(2)
-    dn.dnnmg_scatter_avg(m, cuda(d, m.real), cuda(xf, m.real), vc)
+    dn.dnnmg_scatter_avg(m, cuda(d, m.real), m.pack(xf), vc)
     ref = average.scatter_average(om, d, xf)
     tol = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
-    assert rel_l2(host(vc).reshape(2, -1), ref) <= tol
+    assert rel_l2(m.unpack(vc), ref) <= tol
     # Dirichlet nodes keep the prolongated values bit for bit
     mask = om.dirichlet.ravel()
-    assert np.array_equal(host(vc).reshape(2, -1)[:, mask], xf[:2, mask])
+    assert np.array_equal(m.unpack(vc)[:, mask], xf[:2, mask])
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -161,8 +162,8 @@ def test_constant_correction_is_exact(dn, name):
     xf = as_real(case, fine_velocity(case))
     d = np.full((om.P, om.n_out), 0.375)
     vc = m.fine(2)
-    dn.dnnmg_scatter_avg(m, cuda(d, m.real), cuda(xf, m.real), vc)
-    got = host(vc).reshape(2, -1)
+    dn.dnnmg_scatter_avg(m, cuda(d, m.real), m.pack(xf), vc)
+    got = m.unpack(vc)
     free = ~om.dirichlet.ravel()
     exp = (xf[:2, free].astype(np_dtype(case["prec"])) + np_dtype(case["prec"])(0.375)).astype(np.float64)
     assert np.array_equal(got[:, free], exp)
@@ -176,10 +177,10 @@ def test_rhs_restrict(dn, name):
     v = as_real(case, fine_velocity(case)[:2])
     bf = m.fine(2)
     bc = m.coarse(3)
-    dn.dnnmg_rhs_restrict(m, cuda(v, m.real), bf, bc)
+    dn.dnnmg_rhs_restrict(m, m.pack(v), bf, bc)
     b_ref = fem.rhs(om, PRM, v)
     tol = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
-    bfg = host(bf).reshape(2, -1)
+    bfg = m.unpack(bf)
     assert rel_l2(bfg, b_ref) <= tol
     assert np.all(bfg[:, om.dirichlet.ravel()] == 0)
     assert rel_l2(host(bc).reshape(3, -1), transfer.restrict(om, b_ref)) <= tol
@@ -197,7 +198,7 @@ def run_steps(dn, case, nsteps, seed=31):
     # initial right-hand side: each side assembles its own from v0
     bf_g = m.fine(2)
     bc_g = m.coarse(3)
-    dn.dnnmg_rhs_restrict(m, cuda(v0, m.real), bf_g, bc_g)
+    dn.dnnmg_rhs_restrict(m, m.pack(v0), bf_g, bc_g)
     bf_o = fem.rhs(om, PRM, v0)
     h_g = cuda(h0, m.real)
     h_o = h0.copy()
@@ -209,7 +210,7 @@ def run_steps(dn, case, nsteps, seed=31):
         dn.dnnmg_step(m, net, cuda(xc, torch.float64), h_g, bf_g, bc_g, ws, t)
         out = step.dnnmg_step(om, PRM, (Wx, Uh, Wfc), xc, h_o, bf_o, t)
         h_o, bf_o = out["h"], out["bf"]
-        errs.append({"h": rel_l2(host(h_g), out["h"]), "bf": rel_l2(host(bf_g).reshape(2, -1), out["bf"]),
+        errs.append({"h": rel_l2(host(h_g), out["h"]), "bf": rel_l2(m.unpack(bf_g), out["bf"]),
                      "bc": rel_l2(host(bc_g).reshape(3, -1), out["bc"])})
     return errs
 
@@ -306,7 +307,7 @@ def test_restrict_fp64_class_accuracy(dn, name):
     om = oracle_mesh(case)
     bf = as_real(case, rhs_like(case, seed=41))
     bc = m.coarse(3)
-    dn.dnnmg_restrict(m, cuda(bf, m.real), bc)
+    dn.dnnmg_restrict(m, m.pack(bf), bc)
     ref = transfer.restrict(om, bf)
     assert rel_l2(host(bc).reshape(3, -1), ref) <= 1e-13
 
@@ -348,3 +349,39 @@ def test_gru_tensor_cores_match_cuda_cores(dn, shape, P, monkeypatch):
     h_ref, d_ref = gru.gru_step(Xq, h0.astype(np.float32).astype(np.float64), Wx, Uh, Wfc)
     assert rel_l2(outs[0][0], h_ref) <= TOL["bf16"]
     assert rel_l2(outs[0][1], d_ref) <= TOL["bf16"]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fused_prolongation_forms(dn, name):
+    # S2+S3 and S5 with x~ = P x_c formed inside the kernel equal the oracle's
+    # features / averaging applied to the oracle's prolongation
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    t = 0.2
+    xc = coarse_input(case, t=t)
+    bf = as_real(case, rhs_like(case))
+    X, rf = m.features(), m.fine(3)
+    dn.dnnmg_patch_features(m, None, m.pack(bf), X, rf=rf, xc=cuda(xc, torch.float64), t=t)
+    xf_ref = transfer.prolongate(om, PRM, xc, t)
+    r_ref = fem.residual(om, PRM, xf_ref, bf)
+    X_ref = features.patch_features(om, PRM, xf_ref, r_ref)
+    tol = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
+    assert rel_l2(m.unpack(rf), r_ref) <= tol
+    assert rel_l2(host(X).reshape(m.info.P, m.info.ldx)[:, :om.n_in], X_ref) <= (TOL[case["prec"]] if case["prec"] != "bf16" else 1e-2)
+    rng = np.random.default_rng(29)
+    d = as_real(case, rng.normal(0.0, 0.3, (om.P, om.n_out)))
+    vc = m.fine(2)
+    dn.dnnmg_scatter_avg(m, cuda(d, m.real), None, vc, xc=cuda(xc, torch.float64), t=t)
+    assert rel_l2(m.unpack(vc), average.scatter_average(om, d, xf_ref)) <= tol
+
+
+def test_rhs_alone_equals_rhs_of_rhs_restrict(dn):
+    case = CASES["k2_f32"]
+    m = gpu_mesh(dn, case)
+    v = m.pack(as_real(case, fine_velocity(case)[:2]))
+    b1, b2, bc = m.fine(2), m.fine(2), m.coarse(3)
+    dn.dnnmg_rhs_restrict(m, v, b1, bc)
+    dn.dnnmg_rhs(m, v, b2)
+    torch.cuda.synchronize()
+    assert torch.equal(b1, b2)
