@@ -254,6 +254,31 @@ int dnnmg_net_status(dnnmg_net_t net, int *status, int reset);
  * environment at creation), else 0. */
 int dnnmg_net_uses_tensor_cores(dnnmg_net_t net);
 
+/*
+ * dnnmg_step without a caller-provided workspace.  No counterpart in the
+ * paper: this is a deployment variant of dnnmg_step for callers that cannot
+ * allocate device memory -- a host whose device memory belongs to another
+ * allocator it may not bypass, a loop that must not call the CUDA allocator
+ * once running, or a C caller linking only this library.  The step's scratch
+ * (features, predictions, corrected velocity) lives in a library-owned
+ * static device array of dnnmg_static_scratch_bytes() bytes (64 MiB), which
+ * every GPU that loads the library holds until the process exits.  The
+ * call allocates nothing; meshes whose info.workspace_bytes exceed the array
+ * are rejected with DNNMG_EINVAL and a message (use dnnmg_step then).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls on a device share the one array and it keeps
+ * the last call's contents: calls that can overlap on the GPU (different
+ * streams, different host threads) race on it and must be serialised by
+ * the caller.  Nothing in it needs clearing between calls.  Arguments and
+ * results are those of dnnmg_step.
+ */
+int dnnmg_step_static(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf,
+                      double *bc, double t, cudaStream_t stream);
+
+/* Size in bytes of the static scratch used by dnnmg_step_static. */
+size_t dnnmg_static_scratch_bytes(void);
+
 /* Number of kernel launches one dnnmg_step enqueues for this mesh/net. */
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net);
 

@@ -638,6 +638,20 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
     return DNNMG_OK;
 }
 
+}  // extern "C"
+
+namespace dnnmg {
+// dnnmg_step with the checks done on the given workspace (used by step_static.cu).
+int step_on_workspace(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
+                      void *workspace, size_t workspace_bytes, double t, cudaStream_t stream) {
+    if (int e = step_checks(mesh, net, h, bf, workspace, workspace_bytes)) return e;
+    if (!xc || !bc) return fail(DNNMG_EINVAL, "NULL array");
+    return step_body(mesh, net, xc, h, bf, bc, carve(mesh->info, workspace), t, stream);
+}
+}  // namespace dnnmg
+
+extern "C" {
+
 int dnnmg_step(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
                void *workspace, size_t workspace_bytes, double t, cudaStream_t stream) {
     clear_error();

@@ -130,5 +130,8 @@ void tc_release(Net &n);
 // Per feature column: (kind << 24) | offset into the residual / node tiles of stencil.cu.
 void feature_table(const MeshGeom &g, int *tab);
 int feature_table_capacity();
+// dnnmg_step on a caller-chosen workspace (argument checks included).
+int step_on_workspace(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
+                      void *workspace, size_t workspace_bytes, double t, cudaStream_t stream);
 
 }  // namespace dnnmg

@@ -78,6 +78,7 @@ def _load():
         "dnnmg_step_launches": [P, P],
         "dnnmg_restrict": [P, P, P, P],
         "dnnmg_rhs": [P, P, P, P],
+        "dnnmg_step_static": [P, P, P, P, P, P, D, P],
         "dnnmg_net_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_net_uses_tensor_cores": [P],
     }
@@ -85,6 +86,8 @@ def _load():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.dnnmg_static_scratch_bytes.argtypes = []
+    lib.dnnmg_static_scratch_bytes.restype = ctypes.c_size_t
     lib.dnnmg_last_error.argtypes = []
     lib.dnnmg_last_error.restype = ctypes.c_char_p
     return lib
@@ -335,6 +338,21 @@ def dnnmg_step(mesh, net, xc, h, bf, bc, workspace, t, stream=None):
         raise TypeError("workspace must be a CUDA uint8 tensor")
     _check(_lib.dnnmg_step(mesh.handle, net.handle, _ptr(xc), _ptr(h), _ptr(bf), _ptr(bc),
                            _ptr(workspace), workspace.numel(), float(t), _stream(stream)))
+
+
+def dnnmg_step_static(mesh, net, xc, h, bf, bc, t, stream=None):
+    """dnnmg_step with the library's static scratch instead of a workspace (allocates nothing)."""
+    I = mesh.info
+    _need(xc, torch.float64, 3 * I.Nc, "xc")
+    _need(h, mesh.real, I.P * net.H, "h")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
+    _need(bc, torch.float64, 3 * I.Nc, "bc")
+    _check(_lib.dnnmg_step_static(mesh.handle, net.handle, _ptr(xc), _ptr(h), _ptr(bf), _ptr(bc), float(t),
+                                  _stream(stream)))
+
+
+def dnnmg_static_scratch_bytes():
+    return _lib.dnnmg_static_scratch_bytes()
 
 
 def dnnmg_step_host(mesh, net, xc_host, h, bf, bc_host, workspace, t, stream=None):

@@ -27,7 +27,7 @@ def declared_symbols():
         if f.endswith(".h"):
             src = open(os.path.join(inc, f)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:int|const char \*)\s*(dnnmg_\w+)\s*\(", src, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:int|size_t|const char \*)\s*(dnnmg_\w+)\s*\(", src, flags=re.M))
     return names
 
 
