@@ -271,6 +271,15 @@ void fem_coefficients(const dnnmg_mesh_desc &d, FemCoef<double> *out) {
     stencil(f.Gy, f.nGy);
     stencil(f.Dx, f.nDx);
     stencil(f.Dy, f.nDy);
+    for (int py = 0; py < 2; ++py)
+        for (int px = 0; px < 2; ++px)
+            for (int ey = 0; ey < 2 - py; ++ey)
+                for (int ex = 0; ex < 2 - px; ++ex) {
+                    const int a = px ? 1 : 2 * ex, b = py ? 1 : 2 * ey;   // the node in this patch
+                    for (int kb = 0; kb < 3; ++kb)
+                        for (int ka = 0; ka < 3; ++ka)
+                            f.L5[py][px][kb - b + 2][ka - a + 2] += f.S9[3 * b + a][3 * kb + ka];
+                }
     f.cg0 = gp[0];
     f.cg1 = gp[1];
     f.inv_hx = 1.0 / hx;

@@ -70,6 +70,10 @@ struct FemCoef {
     // node stencils [dy+1][dx+1] of interior nodes (4 fluid cells), assembled
     // from the element matrices above
     T nA[3][3], nB[3][3], nGx[3][3], nGy[3][3], nDx[3][3], nDy[3][3];
+    // LPS node stencils of interior nodes [y class][x class][dy+2][dx+2]; a
+    // node's class in one direction is 0 on a patch edge line (two patches
+    // hold it) and 1 on a patch mid line (one patch)
+    T L5[2][2][5][5];
     // tensor-product 2x2 Gauss evaluation of the convection term
     T cg0, cg1;       // Gauss points on [0, 1]
     T inv_hx, inv_hy;

@@ -102,42 +102,54 @@ __device__ __forceinline__ void stage_window(const MeshGeom &g, const T *__restr
 // Coarse nodes that a window of fine nodes [Ilo, Ilo+FW) x [Jlo, Jlo+FH)
 // interpolates from, staged once per CTA in the fine arithmetic type (FP64
 // throughput on GB300 is 1/64 of FP32, so converting per fine node is not an
-// option).  Fine node I lies in coarse cell clamp(I >> K, 0, nxc-1).
+// option).  Fine node I lies in coarse cell I >> K (floor) at offset
+// (I mod R) / R; the last node nxf falls at offset 0 of a cell "nxc", which
+// blends the same two coarse nodes as the edge of cell nxc-1.  Coarse nodes
+// outside the mesh are staged as zeros (only window nodes outside the mesh
+// read them, and those are never used).
 template <int R> struct Log2;
 template <> struct Log2<2> { static constexpr int v = 1; };
 template <> struct Log2<4> { static constexpr int v = 2; };
 template <> struct Log2<8> { static constexpr int v = 3; };
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// lo + w (hi - lo) with one explicit rounding of the product-sum, so every
+// kernel that interpolates a node produces the same bits.
+template <typename T> __device__ __forceinline__ T lerp(T lo, T hi, T w) { return fma_t(w, hi - lo, lo); }
 
 template <typename T, int R, int FW, int FH>
 struct CoarseWin {
     static constexpr int K = Log2<R>::v;
     static constexpr int CW = (FW - 1) / R + 3, CH = (FH - 1) / R + 3, N = 3 * CW * CH;
     T *cs;          // [3][CH][CW] in shared memory
-    int ci0, cj0;   // first staged coarse node
+    int ci0, cj0;   // first staged coarse node (may be negative)
 
     __device__ __forceinline__ void stage(const MeshGeom &g, const double *__restrict__ xc, int Ilo, int Jlo) {
-        ci0 = min(max(Ilo >> K, 0), g.nxc - 1);
-        cj0 = min(max(Jlo >> K, 0), g.nyc - 1);
+        ci0 = Ilo >> K;
+        cj0 = Jlo >> K;
         const size_t nc1 = (size_t)g.nxc + 1, Nc = nc1 * (g.nyc + 1);
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
             const int c = e / (CW * CH), rem = e - c * (CW * CH);
             const int b = rem / CW, a = rem - b * CW;
             const int ci = ci0 + a, cj = cj0 + b;
             T v = T(0);
-            if (ci <= g.nxc && cj <= g.nyc) v = (T)__ldg(xc + c * Nc + (size_t)cj * nc1 + ci);
+            if (ci >= 0 && cj >= 0 && ci <= g.nxc && cj <= g.nyc) v = (T)__ldg(xc + c * Nc + (size_t)cj * nc1 + ci);
             cs[e] = v;
         }
     }
-    // Bilinear value of all three fields at fine node (I, J) (raw P, no BC).
-    __device__ __forceinline__ void interp(const MeshGeom &g, int I, int J, T (&out)[3]) const {
+    // Bilinear value of all three fields at fine node (I, J) (raw P, no BC):
+    // blends along y on the cell's left and right edges, then along x.
+    __device__ __forceinline__ void interp(int I, int J, T (&out)[3]) const {
         constexpr T inv_r = T(1) / T(R);   // exact: R is a power of two
-        const int ci = min(max(I >> K, 0), g.nxc - 1), cj = min(max(J >> K, 0), g.nyc - 1);
-        const T a = T(I - (ci << K)) * inv_r, b = T(J - (cj << K)) * inv_r;
+        const int ci = I >> K, cj = J >> K;
+        const T a = T(I & (R - 1)) * inv_r, b = T(J & (R - 1)) * inv_r;
         const int o = (cj - cj0) * CW + (ci - ci0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T *q = cs + c * CW * CH + o;
-            out[c] = (T(1) - a) * (T(1) - b) * q[0] + a * (T(1) - b) * q[1] + (T(1) - a) * b * q[CW] + a * b * q[CW + 1];
+            out[c] = lerp(lerp(q[0], q[CW], b), lerp(q[1], q[CW + 1], b), a);
         }
     }
 };
@@ -194,7 +206,7 @@ k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, doub
     for (int q = 0; q < 4; ++q) {
         const int I = Ib + q;
         T x[3];
-        cw.interp(g, I, J, x);
+        cw.interp(I, J, x);
         if (!fast && I <= g.nxf) dirichlet_value(g, I, J, inflow_scale, x[0], x[1]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) val[c][q] = x[c];
@@ -255,26 +267,193 @@ __device__ __forceinline__ void convection(const FemCoef<T> &fc, const T (&u)[4]
 // node window of x~ spans columns I0-4 .. I0+35 (16-byte aligned; node I0+ii
 // at column ii+4) and rows J0-2 .. J0+18 (node J0+jj at row jj+2).
 struct ResLayout {
-    static constexpr int HX = 40, HY = NYN + 4, XO = 4, YO = 2;
+    static constexpr int HX = 40, HY = NYN + 4, XO = 4, YO = 2, HP = HX * HY;
     static constexpr int BX = 36;                              // b_f window: columns I0 .. I0+35
-    static constexpr int CX = TXC + 2, CY = TYC + 2;           // cells with 1-cell halo
+    static constexpr int CX = TXC + 2, CY = TYC + 2;           // cells -1 .. 32 x -1 .. 16
     static constexpr int NCELL = CX * CY;
     static constexpr int LX = TXC / 2 + 2, LY = TYC / 2 + 2;   // LPS patches touching the tile
     static constexpr int NLPS = LX * LY;
     static constexpr int FX = TXC + 4, FY = TYC + 4;           // cell codes with 2-cell halo
-    static constexpr int XS = 3 * HY * HX;
+    static constexpr int XS = 3 * HP;
     static constexpr int BS = 2 * NYN * BX;
     static constexpr int CC = 8 * NCELL;
     static constexpr int LC = 9 * NLPS;
-    static constexpr int RS = 3 * NYN * NXN;
     static constexpr int MAXCS = 3 * ((HX - 1) / 2 + 3) * ((HY - 1) / 2 + 3);   // coarse window, R = 2
+    // the coarse window is dead once x~ is formed, the LPS buffer is born after
+    static constexpr int UN = LC > MAXCS ? LC : MAXCS;
+    static constexpr int MAXP = (TXC / 2) * (TYC / 2);         // patches of a tile (S = 2)
+    static constexpr int NBX = TXC / 2 + 1, NBY = TYC / 2 + 1, NB = NBX * NBY;   // 2x2 node blocks
     static constexpr int MAX_LDX = 1024;                       // feature columns supported
-    template <typename T> static constexpr size_t bytes(bool from_coarse) {
-        return sizeof(T) * (XS + BS + CC + LC + RS + (from_coarse ? MAXCS : 0)) + FX * FY;
+    template <typename T> static constexpr size_t bytes() {
+        return sizeof(T) * (XS + BS + CC + UN) + sizeof(int) * MAXP + FX * FY;
     }
 };
 
 enum { FEAT_RES = 0, FEAT_VEL = 1, FEAT_PECLET = 2, FEAT_GEO = 3, FEAT_ZERO = 4 };
+
+// x~ = P x_c on the node window of a residual tile (Sec. 3 prolongation).
+// One item is one window row inside one coarse cell column: the two vertical
+// blends are formed once and the R nodes of the item read off them, with the
+// arithmetic of CoarseWin::interp (same bits).
+template <typename T, int R, typename CWin>
+__device__ __forceinline__ void interp_window(const CWin &cw, int I0, int J0, T *xs) {
+    using L = ResLayout;
+    constexpr int K = Log2<R>::v;
+    constexpr T inv_r = T(1) / T(R);
+    // I0 is a multiple of 32, so the window's first column sits OFF nodes into its coarse cell
+    constexpr int OFF = (R - L::XO % R) % R;
+    constexpr int NKX = (L::HX + OFF + R - 1) / R;
+    for (int e = threadIdx.x; e < NKX * L::HY; e += blockDim.x) {
+        const int jj = e / NKX, kx = e - jj * NKX;
+        const int J = J0 - L::YO + jj;
+        const T b = T(J & (R - 1)) * inv_r;
+        const T *q = cw.cs + ((J >> K) - cw.cj0) * CWin::CW + kx;
+        T lo[3], d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T *qc = q + c * CWin::CW * CWin::CH;
+            lo[c] = lerp(qc[0], qc[CWin::CW], b);
+            d[c] = lerp(qc[1], qc[CWin::CW + 1], b) - lo[c];
+        }
+        T *dst = xs + jj * L::HX + kx * R - OFF;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int col = kx * R + i - OFF;
+            if (col < 0 || col >= L::HX) continue;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dst[c * L::HP + i] = fma_t(T(i) * inv_r, d[c], lo[c]);
+        }
+    }
+}
+
+// Residual of tile node (ii, jj) into the feature rows of the patches that
+// hold it: its own patch, and the left/lower neighbour when the node lies on
+// that patch's edge.  Columns: component c, patch node (lj, li) at
+// c nf + lj (S+1) + li (Sec. 5.2 inputs).
+template <typename T, typename TX>
+__device__ __forceinline__ void put_residual(const MeshGeom &g, TX *__restrict__ X, const int *pid, int tpx,
+                                             int tpy, int lS, int ii, int jj, T ru, T rv, T rp) {
+    const int S = 1 << lS;
+    const int px = ii >> lS, li = ii & (S - 1), py = jj >> lS, lj = jj & (S - 1);
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+        if (oy == 0 ? py >= tpy : (lj != 0 || py == 0)) continue;
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+            if (ox == 0 ? px >= tpx : (li != 0 || px == 0)) continue;
+            const int id = pid[(py - oy) * tpx + px - ox];
+            if (id < 0) continue;
+            TX *p = X + (size_t)id * g.ldx + (lj + oy * S) * (S + 1) + li + ox * S;
+            p[0] = store_as<TX, T>(ru);
+            p[g.nf] = store_as<TX, T>(rv);
+            p[2 * g.nf] = store_as<TX, T>(rp);
+        }
+    }
+}
+
+__device__ __forceinline__ void store2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+__device__ __forceinline__ void store2(double *p, double a, double b) {
+    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+}
+
+// Residual of the 2x2 node block (2bx .. 2bx+1, 2by .. 2by+1) of a tile whose
+// whole neighbourhood is fluid.  The tile origin is even, so node (2bx+dx,
+// 2by+dy) has LPS class (dx, dy): the LPS term is a fixed node stencil, like
+// the linear velocity, pressure-gradient and divergence terms; only the
+// convection comes from the per-cell contributions in cc.  The zero centre
+// column of the x-gradient/divergence stencils (zero centre row in y) is
+// skipped.  Nodes 2bx+1 = 33 and 2by+1 = 17 lie past the tile and are
+// discarded.
+template <typename T, typename TX>
+__device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<T> &fc, const T *xs,
+                                               const T *bs, const T *cc, const int *pid, int tpx, int tpy,
+                                               int lS, int I0, int J0, int bx, int by, T *__restrict__ rf,
+                                               TX *__restrict__ X) {
+    using L = ResLayout;
+    T Au[2][2], Av[2][2], Ap[2][2];   // [dy][dx]: velocity rows and pressure row of A(x~) x~
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) Au[dy][dx] = Av[dy][dx] = Ap[dy][dx] = T(0);
+    // window rows 2by-2 .. 2by+2, columns 2bx-2 .. 2bx+2
+    const T *w = xs + (2 * by + L::YO - 2) * L::HX + 2 * bx + L::XO - 2;
+#pragma unroll
+    for (int ry = 0; ry < 5; ++ry) {
+        T u[5], v[5], p[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            p[k] = w[ry * L::HX + 2 * L::HP + k];
+            u[k] = v[k] = T(0);
+            if (ry >= 1 && k >= 1) {
+                u[k] = w[ry * L::HX + k];
+                v[k] = w[ry * L::HX + L::HP + k];
+            }
+        }
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int oy = ry - 2 - dy;   // stencil row of this window row for node (dx, dy)
+                if (oy >= dy - 2 && oy <= 2 - dy) {
+#pragma unroll
+                    for (int ox = dx - 2; ox <= 2 - dx; ++ox)
+                        Ap[dy][dx] += fc.L5[dy][dx][oy + 2][ox + 2] * p[dx + ox + 2];
+                }
+                if (oy >= -1 && oy <= 1) {
+                    const int sy = oy + 1;
+#pragma unroll
+                    for (int sx = 0; sx < 3; ++sx) {
+                        const int k = dx + sx + 1;
+                        Au[dy][dx] += fc.nA[sy][sx] * u[k];
+                        Av[dy][dx] += fc.nA[sy][sx] * v[k];
+                        if (sx != 1) {
+                            Au[dy][dx] -= fc.nGx[sy][sx] * p[k];
+                            Ap[dy][dx] += fc.nDx[sy][sx] * u[k];
+                        }
+                        if (sy != 1) {
+                            Av[dy][dx] -= fc.nGy[sy][sx] * p[k];
+                            Ap[dy][dx] += fc.nDy[sy][sx] * v[k];
+                        }
+                    }
+                }
+            }
+    }
+    const bool xin = bx < L::NBX - 1, yin = by < L::NBY - 1;   // node 2bx+1 / 2by+1 inside the tile
+    const int cb = 2 * by * L::CX + 2 * bx;                    // cell (2bx-1, 2by-1)
+    T ru[2][2], rv[2][2], rp[2][2];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            ru[dy][dx] = rv[dy][dx] = T(0);
+            rp[dy][dx] = -Ap[dy][dx];
+            if ((dx == 0 || xin) && (dy == 0 || yin)) {
+                // convection: corner contributions of the cells SW, SE, NW, NE of the node
+                const int c = cb + dy * L::CX + dx;
+                const T cu = (cc[3 * L::NCELL + c] + cc[2 * L::NCELL + c + 1]) +
+                             (cc[1 * L::NCELL + c + L::CX] + cc[c + L::CX + 1]);
+                const T cv = (cc[7 * L::NCELL + c] + cc[6 * L::NCELL + c + 1]) +
+                             (cc[5 * L::NCELL + c + L::CX] + cc[4 * L::NCELL + c + L::CX + 1]);
+                const int nb = (2 * by + dy) * L::BX + 2 * bx + dx;
+                ru[dy][dx] = bs[nb] - (Au[dy][dx] + cu);
+                rv[dy][dx] = bs[NYN * L::BX + nb] - (Av[dy][dx] + cv);
+            }
+        }
+    if (rf && xin && yin) {   // owned nodes (a fast tile never reaches nxf or nyf)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const size_t node = (size_t)(J0 + 2 * by + dy) * g.pitch + I0 + 2 * bx;
+            store2(rf + node, ru[dy][0], ru[dy][1]);
+            store2(rf + g.plane + node, rv[dy][0], rv[dy][1]);
+            store2(rf + 2 * g.plane + node, rp[dy][0], rp[dy][1]);
+        }
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+            put_residual(g, X, pid, tpx, tpy, lS, 2 * bx + dx, 2 * by + dy, ru[dy][dx], rv[dy][dx], rp[dy][dx]);
+}
 
 // S2 + S3 for one 32 x 16-cell tile.  R = 0: x~ is read from xf (S1 done by
 // the caller); R = 2, 4, 8: x~ is interpolated from the coarse vector xc
@@ -289,24 +468,31 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
     T *xs = reinterpret_cast<T *>(smem_raw);   // [3][HY][HX]   u, v, p
     T *bs = xs + L::XS;                        // [2][NYN][BX]  b_u, b_v
     T *cc = bs + L::BS;                        // [8][NCELL]    cell contributions (velocity rows)
-    T *lc = cc + L::CC;                        // [9][NLPS]     LPS contributions
-    T *rs = lc + L::LC;                        // [3][NYN][NXN] residual
-    T *csm = rs + L::RS;                       // coarse window (R > 0)
-    unsigned char *cf = reinterpret_cast<unsigned char *>(csm + (R > 0 ? L::MAXCS : 0));   // [FY][FX]
+    T *un = cc + L::CC;                        // coarse window (R > 0), then [9][NLPS] LPS contributions
+    int *pid = reinterpret_cast<int *>(un + L::UN);                          // [tpy][tpx] patch numbers
+    unsigned char *cf = reinterpret_cast<unsigned char *>(pid + L::MAXP);   // [FY][FX] cell codes
 
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    const int lS = g.K + g.s - 1;   // S = s 2^K with s = 1, 2
+    const int tpx = TXC >> lS, tpy = TYC >> lS;
     stage_window<T, 2, NYN, L::BX>(g, bf, I0, J0, bs);
     using CWin = CoarseWin<T, (R > 0 ? R : 2), L::HX, L::HY>;
     CWin cw;
-    cw.cs = csm;
+    cw.cs = un;
     if constexpr (R > 0) {
-        static_assert(CWin::N <= L::MAXCS, "coarse window");
+        static_assert(CWin::N <= L::UN, "coarse window");
         cw.stage(g, xc, I0 - L::XO, J0 - L::YO);
     } else {
         stage_window<T, 3, L::HY, L::HX>(g, xf, I0 - L::XO, J0 - L::YO, xs);
     }
+    for (int e = threadIdx.x; e < tpx * tpy; e += blockDim.x) {
+        const int py = e / tpx, px = e - py * tpx;
+        const int pi = (I0 >> lS) + px, pj = (J0 >> lS) + py;
+        pid[e] = (pi < g.npx && pj < g.npy) ? g.patch_id[pj * g.npx + pi] : -1;
+    }
     // fast tiles: every cell within two of the tile is fluid and exists, so
     // no tile node is a boundary node and node stencils apply everywhere
+    // (the barrier inside also publishes the coarse window and pid)
     const bool fast = block_all_fluid(g, I0 - 2, I0 + TXC + 1, J0 - 2, J0 + TYC + 1);
     if (!fast) {
         for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
@@ -315,79 +501,124 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
         }
     }
     if constexpr (R > 0) {
-        // x~ = P x_c on the window (the barrier in block_all_fluid published the
-        // coarse nodes), then the Dirichlet velocity where a node has one;
-        // fast tiles have none within the cells they use.
-        for (int e = threadIdx.x; e < L::HX * L::HY; e += blockDim.x) {
-            const int jj = e / L::HX, ii = e - jj * L::HX;
-            const int I = I0 - L::XO + ii, J = J0 - L::YO + jj;
-            T x[3];
-            cw.interp(g, I, J, x);
-            if (!fast && I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf)
-                dirichlet_value(g, I, J, inflow_scale, x[0], x[1]);
-            xs[e] = x[0];
-            xs[L::HY * L::HX + e] = x[1];
-            xs[2 * L::HY * L::HX + e] = x[2];
+        interp_window<T, R>(cw, I0, J0, xs);
+        if (!fast) {
+            // the Dirichlet velocity where a window node has one (fast tiles
+            // have none within the cells they use)
+            __syncthreads();
+            for (int e = threadIdx.x; e < L::HP; e += blockDim.x) {
+                const int jj = e / L::HX, ii = e - jj * L::HX;
+                const int I = I0 - L::XO + ii, J = J0 - L::YO + jj;
+                if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf)
+                    dirichlet_value(g, I, J, inflow_scale, xs[e], xs[L::HP + e]);
+            }
         }
     }
     cp_async_wait_all();
     __syncthreads();
 
-    // Phase A: velocity-row contributions of every cell (fast tiles: convection only)
+    // Feature columns after the residual ones (Sec. 5.2 inputs): x~ and the
+    // Peclet number on the coarse patch nodes, geometry, zero padding;
+    // feat_tab[c] says where column c comes from relative to the patch
+    // origin.  One warp per patch; lanes write consecutive columns.
+    {
+        const int S = 1 << lS, nres = 3 * g.nf;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int tp = warp; tp < tpx * tpy; tp += nw) {
+            const int id = pid[tp];
+            if (id < 0) continue;
+            const int lpy = tp / tpx, lpx = tp - lpy * tpx;
+            const T *xbase = xs + lpy * S * L::HX + lpx * S;
+            TX *row = X + (size_t)id * g.ldx;
+            for (int c = nres + lane; c < g.ldx; c += 32) {
+                const int e = __ldg(g.feat_tab + c);
+                const int kind = e >> 24, off = e & 0xFFFFFF;
+                T val = T(0);
+                if (kind == FEAT_VEL) {
+                    val = xbase[off];
+                } else if (kind == FEAT_PECLET) {
+                    const T u = xbase[off], v = xbase[off + L::HP];
+                    val = fc.q_over_nu * sqrt(u * u + v * v);
+                } else if (kind == FEAT_GEO) {
+                    val = fc.geo[off];
+                }
+                row[c] = store_as<TX, T>(val);
+            }
+        }
+    }
+
+    if (fast) {
+        // convection contributions of every cell around the tile's nodes
+        for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
+            const int cj = cid / L::CX, ci = cid - cj * L::CX;   // cell (ci-1, cj-1)
+            const int base = (cj - 1 + L::YO) * L::HX + ci - 1 + L::XO;
+            const T u[4] = {xs[base], xs[base + 1], xs[base + L::HX], xs[base + L::HX + 1]};
+            const T v[4] = {xs[L::HP + base], xs[L::HP + base + 1], xs[L::HP + base + L::HX],
+                            xs[L::HP + base + L::HX + 1]};
+            T cu[4], cv[4];
+            convection(fc, u, v, cu, cv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                cc[a * L::NCELL + cid] = cu[a];
+                cc[(4 + a) * L::NCELL + cid] = cv[a];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < L::NB) {
+            const int by = threadIdx.x / L::NBX, bx = threadIdx.x - by * L::NBX;
+            block_residual(g, fc, xs, bs, cc, pid, tpx, tpy, lS, I0, J0, bx, by, rf, X);
+        }
+        return;
+    }
+
+    // ---- tiles near a boundary: element by element, with the cell codes
+    T *lc = un;   // [9][NLPS]
+    // Phase A: velocity-row contributions of every fluid cell
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
         const int ci = cid % L::CX - 1, cj = cid / L::CX - 1;
         T out[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) out[k] = T(0);
-        if (fast || cf[(cj + 2) * L::FX + ci + 2] == 1) {
+        if (cf[(cj + 2) * L::FX + ci + 2] == 1) {
             const int base = (cj + L::YO) * L::HX + ci + L::XO;
             const int off[4] = {0, 1, L::HX, L::HX + 1};
-            T u[4], v[4];
+            T u[4], v[4], p[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 u[b] = xs[base + off[b]];
-                v[b] = xs[L::HY * L::HX + base + off[b]];
+                v[b] = xs[L::HP + base + off[b]];
+                p[b] = xs[2 * L::HP + base + off[b]];
             }
             T cu[4], cv[4];
             convection(fc, u, v, cu, cv);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                out[a] = cu[a];
-                out[4 + a] = cv[a];
-            }
-            if (!fast) {
-                T p[4];
+                T au = T(0), av = T(0);
 #pragma unroll
-                for (int b = 0; b < 4; ++b) p[b] = xs[2 * L::HY * L::HX + base + off[b]];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    T au = T(0), av = T(0);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        au += fc.Av[a][b] * u[b] - fc.Gx[a][b] * p[b];
-                        av += fc.Av[a][b] * v[b] - fc.Gy[a][b] * p[b];
-                    }
-                    out[a] += au;
-                    out[4 + a] += av;
+                for (int b = 0; b < 4; ++b) {
+                    au += fc.Av[a][b] * u[b] - fc.Gx[a][b] * p[b];
+                    av += fc.Av[a][b] * v[b] - fc.Gy[a][b] * p[b];
                 }
+                out[a] = cu[a] + au;
+                out[4 + a] = cv[a] + av;
             }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) cc[k * L::NCELL + cid] = out[k];
     }
-    // Phase A': LPS contributions of every 2x2-cell patch touching the tile.
+    // Phase A': LPS contributions of every fluid 2x2-cell patch touching the tile
     for (int lid = threadIdx.x; lid < L::NLPS; lid += blockDim.x) {
         const int m = lid % L::LX - 1, n = lid / L::LX - 1;
         T out[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i] = T(0);
-        if (fast || cf[(2 * n + 2) * L::FX + 2 * m + 2] == 1) {
+        if (cf[(2 * n + 2) * L::FX + 2 * m + 2] == 1) {
             T p9[9];
 #pragma unroll
             for (int b = 0; b < 3; ++b)
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    p9[3 * b + a] = xs[2 * L::HY * L::HX + (2 * n + b + L::YO) * L::HX + 2 * m + a + L::XO];
+                    p9[3 * b + a] = xs[2 * L::HP + (2 * n + b + L::YO) * L::HX + 2 * m + a + L::XO];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 T acc = T(0);
@@ -405,124 +636,57 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
     for (int nid = threadIdx.x; nid < NXN * NYN; nid += blockDim.x) {
         const int jj = nid / NXN, ii = nid - jj * NXN;
         const int I = I0 + ii, J = J0 + jj;
+        if (I > g.nxf || J > g.nyf) continue;
+        const int cells[4] = {jj * L::CX + ii, jj * L::CX + ii + 1, (jj + 1) * L::CX + ii,
+                              (jj + 1) * L::CX + ii + 1};   // cells SW, SE, NW, NE of the node
+        const int corner[4] = {3, 2, 1, 0};
+        T Au = T(0), Av = T(0), Ap = T(0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            Au += cc[corner[t] * L::NCELL + cells[t]];
+            Av += cc[(4 + corner[t]) * L::NCELL + cells[t]];
+        }
+        const T *pu = xs + (jj + L::YO - 1) * L::HX + ii + L::XO - 1;   // node (ii-1, jj-1)
+        const T *pv = pu + L::HP;
+        // divergence rows from the fluid cells around the node
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int cx = t & 1, cy = t >> 1;   // cell SW, SE, NW, NE of the node
+            if (cf[(jj + 1 + cy) * L::FX + ii + 1 + cx] != 1) continue;
+            const int a = corner[t];
+            const T *cu = pu + cy * L::HX + cx, *cvp = pv + cy * L::HX + cx;
+            const T ub[4] = {cu[0], cu[1], cu[L::HX], cu[L::HX + 1]};
+            const T vb[4] = {cvp[0], cvp[1], cvp[L::HX], cvp[L::HX + 1]};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Ap += fc.Dx[a][b] * ub[b] + fc.Dy[a][b] * vb[b];
+        }
+        const int nmx = (ii & 1) ? 1 : 2, nmy = (jj & 1) ? 1 : 2;
+        for (int ty = 0; ty < nmy; ++ty) {
+            const int n = (jj & 1) ? (jj - 1) / 2 : jj / 2 - 1 + ty;
+            const int b = (jj & 1) ? 1 : (ty == 0 ? 2 : 0);
+            for (int tx = 0; tx < nmx; ++tx) {
+                const int m = (ii & 1) ? (ii - 1) / 2 : ii / 2 - 1 + tx;
+                const int a = (ii & 1) ? 1 : (tx == 0 ? 2 : 0);
+                Ap += lc[(3 * b + a) * L::NLPS + (n + 1) * L::LX + m + 1];
+            }
+        }
+        const NodeClass nc = classify(cf[(jj + 1) * L::FX + ii + 1], cf[(jj + 1) * L::FX + ii + 2],
+                                      cf[(jj + 2) * L::FX + ii + 1], cf[(jj + 2) * L::FX + ii + 2], I, J, g.nyf);
         T ru = T(0), rv = T(0), rp = T(0);
-        if (I <= g.nxf && J <= g.nyf) {
-            const int cells[4] = {jj * L::CX + ii, jj * L::CX + ii + 1, (jj + 1) * L::CX + ii,
-                                  (jj + 1) * L::CX + ii + 1};   // cells SW, SE, NW, NE of the node
-            const int corner[4] = {3, 2, 1, 0};
-            T Au = T(0), Av = T(0), Ap = T(0);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                Au += cc[corner[t] * L::NCELL + cells[t]];
-                Av += cc[(4 + corner[t]) * L::NCELL + cells[t]];
-            }
-            const T *pu = xs + (jj + L::YO - 1) * L::HX + ii + L::XO - 1;   // node (ii-1, jj-1)
-            const T *pv = pu + L::HY * L::HX;
-            const T *pp = pv + L::HY * L::HX;
-            if (fast) {
-                // independent partial sums per stencil row keep the FMA chains short
-                T su[3], sv[3], sp[3];
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy) {
-                    su[dy] = sv[dy] = sp[dy] = T(0);
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
-                        const T u = pu[dy * L::HX + dx], v = pv[dy * L::HX + dx], p = pp[dy * L::HX + dx];
-                        su[dy] += fc.nA[dy][dx] * u - fc.nGx[dy][dx] * p;
-                        sv[dy] += fc.nA[dy][dx] * v - fc.nGy[dy][dx] * p;
-                        sp[dy] += fc.nDx[dy][dx] * u + fc.nDy[dy][dx] * v;
-                    }
-                }
-                Au += (su[0] + su[1]) + su[2];
-                Av += (sv[0] + sv[1]) + sv[2];
-                Ap += (sp[0] + sp[1]) + sp[2];
-            } else {
-                // divergence rows from the fluid cells around the node
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int cx = t & 1, cy = t >> 1;   // cell SW, SE, NW, NE of the node
-                    if (cf[(jj + 1 + cy) * L::FX + ii + 1 + cx] != 1) continue;
-                    const int a = corner[t];
-                    const T *cu = pu + cy * L::HX + cx, *cvp = pv + cy * L::HX + cx;
-                    const T ub[4] = {cu[0], cu[1], cu[L::HX], cu[L::HX + 1]};
-                    const T vb[4] = {cvp[0], cvp[1], cvp[L::HX], cvp[L::HX + 1]};
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) Ap += fc.Dx[a][b] * ub[b] + fc.Dy[a][b] * vb[b];
-                }
-            }
-            const int nmx = (ii & 1) ? 1 : 2, nmy = (jj & 1) ? 1 : 2;
-            for (int ty = 0; ty < nmy; ++ty) {
-                const int n = (jj & 1) ? (jj - 1) / 2 : jj / 2 - 1 + ty;
-                const int b = (jj & 1) ? 1 : (ty == 0 ? 2 : 0);
-                for (int tx = 0; tx < nmx; ++tx) {
-                    const int m = (ii & 1) ? (ii - 1) / 2 : ii / 2 - 1 + tx;
-                    const int a = (ii & 1) ? 1 : (tx == 0 ? 2 : 0);
-                    Ap += lc[(3 * b + a) * L::NLPS + (n + 1) * L::LX + m + 1];
-                }
-            }
-            bool dirichlet = false, p_active = true;
-            if (!fast) {
-                const NodeClass nc = classify(cf[(jj + 1) * L::FX + ii + 1], cf[(jj + 1) * L::FX + ii + 2],
-                                              cf[(jj + 2) * L::FX + ii + 1], cf[(jj + 2) * L::FX + ii + 2],
-                                              I, J, g.nyf);
-                dirichlet = nc.dirichlet;
-                p_active = nc.p_active;
-            }
-            if (!dirichlet) {
-                ru = bs[jj * L::BX + ii] - Au;
-                rv = bs[NYN * L::BX + jj * L::BX + ii] - Av;
-            }
-            if (p_active) rp = -Ap;
-            // a node on the tile's right/top edge belongs to the next tile
-            // (which may take the other path): write owned nodes only
-            if (rf && (ii < TXC || I == g.nxf) && (jj < TYC || J == g.nyf)) {
-                const size_t node = (size_t)J * g.pitch + I;
-                rf[node] = ru;
-                rf[g.plane + node] = rv;
-                rf[2 * g.plane + node] = rp;
-            }
+        if (!nc.dirichlet) {
+            ru = bs[jj * L::BX + ii] - Au;
+            rv = bs[NYN * L::BX + jj * L::BX + ii] - Av;
         }
-        rs[nid] = ru;
-        rs[NYN * NXN + nid] = rv;
-        rs[2 * NYN * NXN + nid] = rp;
-    }
-    __syncthreads();
-
-    // Phase C: one feature row per fluid patch of the tile (Sec. 5.2 inputs);
-    // feat_tab[c] says where column c comes from relative to the patch origin.
-    // One warp per patch row; lanes write consecutive columns.
-    const int S = g.S;
-    const int tpx = TXC / S, tpy = TYC / S;
-    const int pi0 = I0 / S, pj0 = J0 / S;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int tp = warp; tp < tpx * tpy; tp += nw) {
-        const int lpy = tp / tpx, lpx = tp - lpy * tpx;
-        const int pi = pi0 + lpx, pj = pj0 + lpy;
-        if (pi >= g.npx || pj >= g.npy) continue;
-        const int id = g.patch_id[pj * g.npx + pi];
-        if (id < 0) continue;
-        const T *rbase = rs + lpy * S * NXN + lpx * S;
-        const T *xbase = xs + lpy * S * L::HX + lpx * S;
-        TX *row = X + (size_t)id * g.ldx;
-#pragma unroll 4
-        for (int c = lane; c < g.ldx; c += 32) {
-            const int e = __ldg(g.feat_tab + c);
-            const int kind = e >> 24, off = e & 0xFFFFFF;
-            T val;
-            if (kind == FEAT_RES) {
-                val = rbase[off];
-            } else if (kind == FEAT_VEL) {
-                val = xbase[off];
-            } else if (kind == FEAT_PECLET) {
-                const T u = xbase[off], v = xbase[off + L::HY * L::HX];
-                val = fc.q_over_nu * sqrt(u * u + v * v);
-            } else if (kind == FEAT_GEO) {
-                val = fc.geo[off];
-            } else {
-                val = T(0);
-            }
-            row[c] = store_as<TX, T>(val);
+        if (nc.p_active) rp = -Ap;
+        // a node on the tile's right/top edge belongs to the next tile
+        // (which may take the other path): write owned nodes only
+        if (rf && (ii < TXC || I == g.nxf) && (jj < TYC || J == g.nyf)) {
+            const size_t node = (size_t)J * g.pitch + I;
+            rf[node] = ru;
+            rf[g.plane + node] = rv;
+            rf[2 * g.plane + node] = rp;
         }
+        put_residual(g, X, pid, tpx, tpy, lS, ii, jj, ru, rv, rp);
     }
 }
 
@@ -558,7 +722,7 @@ k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, con
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             T x[3];
-            cw.interp(g, Ib + q, J, x);
+            cw.interp(Ib + q, J, x);
             u[q] = x[0];
             v[q] = x[1];
         }
@@ -934,7 +1098,7 @@ template <typename T, typename TX, int R>
 cudaError_t run_residual(const MeshGeom &g, const FemCoef<T> &fc, const void *xf, const double *xc, double w,
                          const void *bf, void *rf, void *X, cudaStream_t st) {
     auto k = k_residual_features<T, TX, R>;
-    const size_t sm = ResLayout::bytes<T>(R > 0);
+    const size_t sm = ResLayout::bytes<T>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k<<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, (const T *)xf, xc, w, (const T *)bf, (T *)rf, (TX *)X);
