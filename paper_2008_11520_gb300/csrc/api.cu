@@ -401,6 +401,22 @@ int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out) {
         return fail(DNNMG_ENOMEM, "device allocation of the feature table failed");
     }
     g.feat_tab = m->d_feat_tab;
+    tile_counts(g, &g.ntx, &g.nty);
+    std::vector<uint8_t> tflags((size_t)g.ntx * g.nty);
+    tile_flags(g, solid.data(), tflags.data());
+    m->d_tile_flags = nullptr;
+    if (cudaMalloc(&m->d_tile_flags, tflags.size()) != cudaSuccess ||
+        cudaMemcpy(m->d_tile_flags, tflags.data(), tflags.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(m->d_solid);
+        cudaFree(m->d_patch_id);
+        cudaFree(m->d_patch_cell);
+        cudaFree(m->d_feat_tab);
+        cudaFree(m->d_tile_flags);
+        delete m;
+        cudaGetLastError();
+        return fail(DNNMG_ENOMEM, "device allocation of the tile flags failed");
+    }
+    g.tile_flags = m->d_tile_flags;
     fem_coefficients(*desc, &m->fem64);
     to_float(m->fem64, &m->fem32);
     *out = m;
@@ -414,6 +430,7 @@ int dnnmg_mesh_destroy(dnnmg_mesh_t mesh) {
     cudaFree(mesh->d_patch_id);
     cudaFree(mesh->d_patch_cell);
     cudaFree(mesh->d_feat_tab);
+    cudaFree(mesh->d_tile_flags);
     delete mesh;
     return DNNMG_OK;
 }

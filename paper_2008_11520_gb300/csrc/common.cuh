@@ -48,6 +48,8 @@ struct MeshGeom {
     const int *patch_id;          // device [npy][npx], fluid patch number or -1
     const int *patch_cell;        // device [P], pj npx + pi
     const int *feat_tab;          // device [ldx], source of each feature column (stencil.cu)
+    const uint8_t *tile_flags;    // device [nty][ntx], all-fluid bits of each 32 x 16-cell tile
+    int ntx, nty;
 };
 
 // Element constants of one fine cell (local nodes SW, SE, NW, NE) and of one
@@ -91,6 +93,7 @@ struct Mesh {
     int *d_patch_id;
     int *d_patch_cell;
     int *d_feat_tab;
+    uint8_t *d_tile_flags;
 };
 
 struct Net {
@@ -134,6 +137,10 @@ void tc_release(Net &n);
 // Per feature column: (kind << 24) | offset into the residual / node tiles of stencil.cu.
 void feature_table(const MeshGeom &g, int *tab);
 int feature_table_capacity();
+// Per 32 x 16-cell stencil tile (ntx x nty of them): bit 0 = every fine cell
+// within two cells of the tile exists and is fluid, bit 1 = the same within one.
+void tile_flags(const MeshGeom &g, const uint8_t *solid, uint8_t *flags);
+void tile_counts(const MeshGeom &g, int *ntx, int *nty);
 // dnnmg_step on a caller-chosen workspace (argument checks included).
 int step_on_workspace(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
                       void *workspace, size_t workspace_bytes, double t, cudaStream_t stream);

@@ -56,19 +56,14 @@ __device__ __forceinline__ NodeClass classify_global(const MeshGeom &g, int I, i
                     cell_code(g, I, J), I, J, g.nyf);
 }
 
-// True (in every thread of the CTA) iff every fine cell in [i0, i1] x [j0, j1]
-// exists and is fluid; the coarse cells covering the range are checked.
-__device__ __forceinline__ bool block_all_fluid(const MeshGeom &g, int i0, int i1, int j0, int j1) {
-    bool ok = i0 >= 0 && j0 >= 0 && i1 < g.nxf && j1 < g.nyf;
-    if (ok) {
-        const int ci0 = i0 >> g.K, ci1 = i1 >> g.K, cj0 = j0 >> g.K, cj1 = j1 >> g.K;
-        const int w = ci1 - ci0 + 1, n = w * (cj1 - cj0 + 1);
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const int cj = cj0 + e / w, ci = ci0 + e % w;
-            ok &= g.solid[(size_t)cj * g.nxc + ci] == 0;
-        }
-    }
-    return __syncthreads_and(ok);
+// Fast-path tests from the per-tile flags (computed with the mesh): tile
+// (tx, ty) of 32 x 16 cells with all cells within `halo` (1 or 2) fluid; a
+// 64 x 16 node tile is the union of two stencil tiles.
+__device__ __forceinline__ bool tile_fluid(const MeshGeom &g, int tx, int ty, int bit) {
+    return tx < g.ntx && ty < g.nty && (__ldg(g.tile_flags + (size_t)ty * g.ntx + tx) & bit);
+}
+__device__ __forceinline__ bool node_tile_fluid(const MeshGeom &g, int bx, int by) {
+    return tile_fluid(g, 2 * bx, by, 2) && tile_fluid(g, 2 * bx + 1, by, 2);
 }
 
 // Asynchronous 16-byte copy global -> shared; src_bytes = 0 writes zeros.
@@ -140,7 +135,7 @@ struct CoarseWin {
         }
     }
     // Bilinear value of all three fields at fine node (I, J) (raw P, no BC):
-    // blends along y on the cell's left and right edges, then along x.
+    // blends along x on the cell's bottom and top edges, then along y.
     __device__ __forceinline__ void interp(int I, int J, T (&out)[3]) const {
         constexpr T inv_r = T(1) / T(R);   // exact: R is a power of two
         const int ci = I >> K, cj = J >> K;
@@ -149,7 +144,7 @@ struct CoarseWin {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T *q = cs + c * CW * CH + o;
-            out[c] = lerp(lerp(q[0], q[CW], b), lerp(q[1], q[CW + 1], b), a);
+            out[c] = lerp(lerp(q[0], q[1], a), lerp(q[CW], q[CW + 1], a), b);
         }
     }
 };
@@ -197,7 +192,8 @@ k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, doub
     cw.stage(g, xc, I0, J0);
     // no Dirichlet node in the tile: all cells around its nodes exist and are
     // fluid (the barrier inside also publishes the staged coarse nodes)
-    const bool fast = block_all_fluid(g, I0 - 1, I0 + PTX, J0 - 1, J0 + PTY);
+    const bool fast = node_tile_fluid(g, blockIdx.x, blockIdx.y);
+    __syncthreads();   // publishes the staged coarse nodes
     const int J = J0 + threadIdx.x / (PTX / 4);
     const int Ib = I0 + 4 * (threadIdx.x % (PTX / 4));
     if (J > g.nyf) return;
@@ -217,49 +213,124 @@ k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, doub
 }
 
 // ------------------------------------------------------------------ S2 + S3
+// Two FP32 values in one 64-bit register pair, operated on by the packed
+// f32x2 instructions of sm_100 and later: one issue slot gives two results,
+// each rounded as its scalar form would be.  Passes that work on two cells or
+// two nodes side by side use them; FP64 tiles use a plain pair of doubles.
+struct F2 {
+    unsigned long long r;
+};
+struct D2 {
+    double a, b;
+};
+__device__ __forceinline__ F2 pack2(float a, float b) {
+    F2 p;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(p.r) : "f"(a), "f"(b));
+    return p;
+}
+__device__ __forceinline__ void unpack2(F2 p, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p.r));
+}
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {   // a b + c
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return d;
+}
+__device__ __forceinline__ D2 pack2(double a, double b) { return D2{a, b}; }
+__device__ __forceinline__ void unpack2(D2 p, double &a, double &b) {
+    a = p.a;
+    b = p.b;
+}
+__device__ __forceinline__ D2 vadd(D2 x, D2 y) { return D2{__dadd_rn(x.a, y.a), __dadd_rn(x.b, y.b)}; }
+__device__ __forceinline__ D2 vsub(D2 x, D2 y) { return D2{__dsub_rn(x.a, y.a), __dsub_rn(x.b, y.b)}; }
+__device__ __forceinline__ D2 vmul(D2 x, D2 y) { return D2{__dmul_rn(x.a, y.a), __dmul_rn(x.b, y.b)}; }
+__device__ __forceinline__ D2 vfma(D2 x, D2 y, D2 z) { return D2{__fma_rn(x.a, y.a, z.a), __fma_rn(x.b, y.b, z.b)}; }
+// scalar forms, so one template serves one cell or two
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename T> struct Packed;
+template <> struct Packed<float> { using type = F2; };
+template <> struct Packed<double> { using type = D2; };
+
+template <typename V> __device__ __forceinline__ V splat(float x) { return pack2(x, x); }
+template <> __device__ __forceinline__ float splat<float>(float x) { return x; }
+template <typename V> __device__ __forceinline__ V splat(double x) { return pack2(x, x); }
+template <> __device__ __forceinline__ double splat<double>(double x) { return x; }
+
+// Constants of the convection term in the value type V (one cell or a pair).
+template <typename V> struct ConvK {
+    V g0, g1, ihx, ihy, w0, w1;
+    template <typename T> __device__ __forceinline__ explicit ConvK(const FemCoef<T> &fc)
+        : g0(splat<V>(fc.cg0)), g1(splat<V>(fc.cg1)), ihx(splat<V>(fc.inv_hx)), ihy(splat<V>(fc.inv_hy)),
+          w0(splat<V>(fc.cwg0)), w1(splat<V>(fc.cwg1)) {}
+};
+
 // 1/2 (v.grad v_c, phi_a) of one cell for its corners a = SW, SE, NW, NE, by
 // 2x2 Gauss in tensor-product form: values and derivatives at the 4 points
 // from edge interpolants, then the test-function sums one direction at a time.
-template <typename T>
-__device__ __forceinline__ void convection(const FemCoef<T> &fc, const T (&u)[4], const T (&v)[4], T (&cu)[4],
-                                           T (&cv)[4]) {
-    const T g0 = fc.cg0, g1 = fc.cg1;
+template <typename V>
+__device__ __forceinline__ void convection(const ConvK<V> &k, const V (&u)[4], const V (&v)[4], V (&cu)[4],
+                                           V (&cv)[4]) {
     // along x on the bottom (0, 1) and top (2, 3) edges
-    const T dub = u[1] - u[0], dut = u[3] - u[2], dvb = v[1] - v[0], dvt = v[3] - v[2];
-    const T ub[2] = {u[0] + g0 * dub, u[0] + g1 * dub}, ut[2] = {u[2] + g0 * dut, u[2] + g1 * dut};
-    const T vb[2] = {v[0] + g0 * dvb, v[0] + g1 * dvb}, vt[2] = {v[2] + g0 * dvt, v[2] + g1 * dvt};
+    const V dub = vsub(u[1], u[0]), dut = vsub(u[3], u[2]), dvb = vsub(v[1], v[0]), dvt = vsub(v[3], v[2]);
+    const V ub[2] = {vfma(k.g0, dub, u[0]), vfma(k.g1, dub, u[0])};
+    const V ut[2] = {vfma(k.g0, dut, u[2]), vfma(k.g1, dut, u[2])};
+    const V vb[2] = {vfma(k.g0, dvb, v[0]), vfma(k.g1, dvb, v[0])};
+    const V vt[2] = {vfma(k.g0, dvt, v[2]), vfma(k.g1, dvt, v[2])};
     // x-derivatives depend on eta only, y-derivatives on xi only
-    const T ux[2] = {dub + g0 * (dut - dub), dub + g1 * (dut - dub)};
-    const T vx[2] = {dvb + g0 * (dvt - dvb), dvb + g1 * (dvt - dvb)};
-    const T uy[2] = {ut[0] - ub[0], ut[1] - ub[1]};
-    const T vy[2] = {vt[0] - vb[0], vt[1] - vb[1]};
-    T c_u[2][2], c_v[2][2];   // [eta index j][xi index i]
+    const V ddu = vsub(dut, dub), ddv = vsub(dvt, dvb);
+    const V ux[2] = {vfma(k.g0, ddu, dub), vfma(k.g1, ddu, dub)};
+    const V vx[2] = {vfma(k.g0, ddv, dvb), vfma(k.g1, ddv, dvb)};
+    const V uy[2] = {vsub(ut[0], ub[0]), vsub(ut[1], ub[1])};
+    const V vy[2] = {vsub(vt[0], vb[0]), vsub(vt[1], vb[1])};
+    V c_u[2][2], c_v[2][2];   // [eta index j][xi index i]
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        const T gj = j ? g1 : g0;
+        const V gj = j ? k.g1 : k.g0;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            const T U = (ub[i] + gj * uy[i]) * fc.inv_hx;
-            const T V = (vb[i] + gj * vy[i]) * fc.inv_hy;
-            c_u[j][i] = U * ux[j] + V * uy[i];
-            c_v[j][i] = U * vx[j] + V * vy[i];
+            const V U = vmul(vfma(gj, uy[i], ub[i]), k.ihx);
+            const V W = vmul(vfma(gj, vy[i], vb[i]), k.ihy);
+            c_u[j][i] = vfma(U, ux[j], vmul(W, uy[i]));
+            c_v[j][i] = vfma(U, vx[j], vmul(W, vy[i]));
         }
     }
     // test with l_0(g) = 1 - g, l_1(g) = g (1 - g0 = g1), weights (qw / 2)
-    T su[2][2], sv[2][2];   // [j][ax]
+    V su[2][2], sv[2][2];   // [j][ax]
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        su[j][0] = g1 * c_u[j][0] + g0 * c_u[j][1];
-        su[j][1] = g0 * c_u[j][0] + g1 * c_u[j][1];
-        sv[j][0] = g1 * c_v[j][0] + g0 * c_v[j][1];
-        sv[j][1] = g0 * c_v[j][0] + g1 * c_v[j][1];
+        su[j][0] = vfma(k.g1, c_u[j][0], vmul(k.g0, c_u[j][1]));
+        su[j][1] = vfma(k.g0, c_u[j][0], vmul(k.g1, c_u[j][1]));
+        sv[j][0] = vfma(k.g1, c_v[j][0], vmul(k.g0, c_v[j][1]));
+        sv[j][1] = vfma(k.g0, c_v[j][0], vmul(k.g1, c_v[j][1]));
     }
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
-        cu[ax] = fc.cwg1 * su[0][ax] + fc.cwg0 * su[1][ax];
-        cu[2 + ax] = fc.cwg0 * su[0][ax] + fc.cwg1 * su[1][ax];
-        cv[ax] = fc.cwg1 * sv[0][ax] + fc.cwg0 * sv[1][ax];
-        cv[2 + ax] = fc.cwg0 * sv[0][ax] + fc.cwg1 * sv[1][ax];
+        cu[ax] = vfma(k.w1, su[0][ax], vmul(k.w0, su[1][ax]));
+        cu[2 + ax] = vfma(k.w0, su[0][ax], vmul(k.w1, su[1][ax]));
+        cv[ax] = vfma(k.w1, sv[0][ax], vmul(k.w0, sv[1][ax]));
+        cv[2 + ax] = vfma(k.w0, sv[0][ax], vmul(k.w1, sv[1][ax]));
     }
 }
 
@@ -271,12 +342,16 @@ struct ResLayout {
     static constexpr int BX = 36;                              // b_f window: columns I0 .. I0+35
     static constexpr int CX = TXC + 2, CY = TYC + 2;           // cells -1 .. 32 x -1 .. 16
     static constexpr int NCELL = CX * CY;
+    // cell contributions: one array per (component, corner), pitch NCP; the
+    // arrays of the west corners (SW, NW) start one element later so that the
+    // two nodes of a block read each array as one aligned pair
+    static constexpr int NCP = NCELL + 4;
     static constexpr int LX = TXC / 2 + 2, LY = TYC / 2 + 2;   // LPS patches touching the tile
     static constexpr int NLPS = LX * LY;
     static constexpr int FX = TXC + 4, FY = TYC + 4;           // cell codes with 2-cell halo
     static constexpr int XS = 3 * HP;
     static constexpr int BS = 2 * NYN * BX;
-    static constexpr int CC = 8 * NCELL;
+    static constexpr int CC = 8 * NCP;
     static constexpr int LC = 9 * NLPS;
     static constexpr int MAXCS = 3 * ((HX - 1) / 2 + 3) * ((HY - 1) / 2 + 3);   // coarse window, R = 2
     // the coarse window is dead once x~ is formed, the LPS buffer is born after
@@ -287,41 +362,44 @@ struct ResLayout {
     template <typename T> static constexpr size_t bytes() {
         return sizeof(T) * (XS + BS + CC + UN) + sizeof(int) * MAXP + FX * FY;
     }
+    // element of corner k (0..3: u rows of SW, SE, NW, NE; 4..7: v rows) of cell cid
+    static __device__ __forceinline__ int ccx(int k, int cid) { return k * NCP + cid + ((k & 1) ^ 1); }
 };
 
 enum { FEAT_RES = 0, FEAT_VEL = 1, FEAT_PECLET = 2, FEAT_GEO = 3, FEAT_ZERO = 4 };
 
 // x~ = P x_c on the node window of a residual tile (Sec. 3 prolongation).
-// One item is one window row inside one coarse cell column: the two vertical
-// blends are formed once and the R nodes of the item read off them, with the
-// arithmetic of CoarseWin::interp (same bits).
+// One item is one window column inside one coarse cell row: the blends
+// along x on the cell's bottom and top edges are formed once and the R
+// nodes of the item read off them, with the arithmetic of CoarseWin::interp
+// (same bits).  Lanes take consecutive columns.
 template <typename T, int R, typename CWin>
 __device__ __forceinline__ void interp_window(const CWin &cw, int I0, int J0, T *xs) {
     using L = ResLayout;
     constexpr int K = Log2<R>::v;
     constexpr T inv_r = T(1) / T(R);
-    // I0 is a multiple of 32, so the window's first column sits OFF nodes into its coarse cell
-    constexpr int OFF = (R - L::XO % R) % R;
-    constexpr int NKX = (L::HX + OFF + R - 1) / R;
-    for (int e = threadIdx.x; e < NKX * L::HY; e += blockDim.x) {
-        const int jj = e / NKX, kx = e - jj * NKX;
-        const int J = J0 - L::YO + jj;
-        const T b = T(J & (R - 1)) * inv_r;
-        const T *q = cw.cs + ((J >> K) - cw.cj0) * CWin::CW + kx;
+    // J0 is a multiple of 16, so the window's first row sits OFFY rows into its coarse cell
+    constexpr int OFFY = (R - L::YO % R) % R;
+    constexpr int NKY = (L::HY + OFFY + R - 1) / R;
+    for (int e = threadIdx.x; e < NKY * L::HX; e += blockDim.x) {
+        const int ky = e / L::HX, col = e - ky * L::HX;
+        const int I = I0 - L::XO + col;
+        const T a = T(I & (R - 1)) * inv_r;
+        const T *q = cw.cs + ky * CWin::CW + ((I >> K) - cw.ci0);
         T lo[3], d[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T *qc = q + c * CWin::CW * CWin::CH;
-            lo[c] = lerp(qc[0], qc[CWin::CW], b);
-            d[c] = lerp(qc[1], qc[CWin::CW + 1], b) - lo[c];
+            lo[c] = lerp(qc[0], qc[1], a);
+            d[c] = lerp(qc[CWin::CW], qc[CWin::CW + 1], a) - lo[c];
         }
-        T *dst = xs + jj * L::HX + kx * R - OFF;
+        T *dst = xs + (ky * R - OFFY) * L::HX + col;
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int col = kx * R + i - OFF;
-            if (col < 0 || col >= L::HX) continue;
+        for (int j = 0; j < R; ++j) {
+            const int row = ky * R + j - OFFY;
+            if (row < 0 || row >= L::HY) continue;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dst[c * L::HP + i] = fma_t(T(i) * inv_r, d[c], lo[c]);
+            for (int c = 0; c < 3; ++c) dst[c * L::HP + j * L::HX] = fma_t(T(j) * inv_r, d[c], lo[c]);
         }
     }
 }
@@ -351,9 +429,56 @@ __device__ __forceinline__ void put_residual(const MeshGeom &g, TX *__restrict__
     }
 }
 
+// The same for the 2x2 node block (2bx .. 2bx+1, 2by .. 2by+1): the block
+// lies in one patch (S is even), and only its even column / row can also
+// be the last column / row of the left / lower patch.  Nodes past the tile
+// (2bx+1 = 33, 2by+1 = 17) fall outside every patch of the tile and are
+// dropped.
+template <typename T, typename TX>
+__device__ __forceinline__ void put_block(const MeshGeom &g, TX *__restrict__ X, const int *pid, int tpx, int tpy,
+                                          int lS, int bx, int by, const T (&ru)[2][2], const T (&rv)[2][2],
+                                          const T (&rp)[2][2]) {
+    const int S = 1 << lS, S1 = S + 1, nf = g.nf;
+    const int px = (2 * bx) >> lS, li = (2 * bx) & (S - 1), py = (2 * by) >> lS, lj = (2 * by) & (S - 1);
+    TX *base[2][2];   // [oy][ox]: row of patch (px - ox, py - oy) at the block's first node, or null
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+            const bool ok = (oy ? (lj == 0 && py > 0) : py < tpy) && (ox ? (li == 0 && px > 0) : px < tpx);
+            const int id = ok ? pid[(py - oy) * tpx + px - ox] : -1;
+            base[oy][ox] = id >= 0 ? X + (size_t)id * g.ldx + (lj + oy * S) * S1 + li + ox * S : nullptr;
+        }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+            for (int oy = 0; oy <= 1 - dy; ++oy)
+#pragma unroll
+                for (int ox = 0; ox <= 1 - dx; ++ox) {
+                    TX *q = base[oy][ox];
+                    if (!q) continue;
+                    q += (oy ? 0 : dy * S1) + (ox ? 0 : dx);
+                    q[0] = store_as<TX, T>(ru[dy][dx]);
+                    q[nf] = store_as<TX, T>(rv[dy][dx]);
+                    q[2 * nf] = store_as<TX, T>(rp[dy][dx]);
+                }
+}
+
 __device__ __forceinline__ void store2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
 __device__ __forceinline__ void store2(double *p, double a, double b) {
     *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void ld2(const float *p, float &a, float &b) {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    a = t.x;
+    b = t.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double &a, double &b) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    a = t.x;
+    b = t.y;
 }
 
 // Residual of the 2x2 node block (2bx .. 2bx+1, 2by .. 2by+1) of a tile whose
@@ -362,8 +487,8 @@ __device__ __forceinline__ void store2(double *p, double a, double b) {
 // the linear velocity, pressure-gradient and divergence terms; only the
 // convection comes from the per-cell contributions in cc.  The zero centre
 // column of the x-gradient/divergence stencils (zero centre row in y) is
-// skipped.  Nodes 2bx+1 = 33 and 2by+1 = 17 lie past the tile and are
-// discarded.
+// skipped.  Window values and cell contributions are read as aligned pairs.
+// Nodes 2bx+1 = 33 and 2by+1 = 17 lie past the tile and are discarded.
 template <typename T, typename TX>
 __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<T> &fc, const T *xs,
                                                const T *bs, const T *cc, const int *pid, int tpx, int tpy,
@@ -375,18 +500,18 @@ __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx) Au[dy][dx] = Av[dy][dx] = Ap[dy][dx] = T(0);
-    // window rows 2by-2 .. 2by+2, columns 2bx-2 .. 2bx+2
+    // window rows 2by-2 .. 2by+2, columns 2bx-2 .. 2bx+3 (even start: aligned pairs)
     const T *w = xs + (2 * by + L::YO - 2) * L::HX + 2 * bx + L::XO - 2;
 #pragma unroll
     for (int ry = 0; ry < 5; ++ry) {
-        T u[5], v[5], p[5];
+        T u[6], v[6], p[6];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            p[k] = w[ry * L::HX + 2 * L::HP + k];
-            u[k] = v[k] = T(0);
-            if (ry >= 1 && k >= 1) {
-                u[k] = w[ry * L::HX + k];
-                v[k] = w[ry * L::HX + L::HP + k];
+        for (int k = 0; k < 6; k += 2) {
+            ld2(w + ry * L::HX + 2 * L::HP + k, p[k], p[k + 1]);
+            u[k] = u[k + 1] = v[k] = v[k + 1] = T(0);
+            if (ry >= 1) {
+                ld2(w + ry * L::HX + k, u[k], u[k + 1]);
+                ld2(w + ry * L::HX + L::HP + k, v[k], v[k + 1]);
             }
         }
 #pragma unroll
@@ -422,23 +547,36 @@ __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<
     const int cb = 2 * by * L::CX + 2 * bx;                    // cell (2bx-1, 2by-1)
     T ru[2][2], rv[2][2], rp[2][2];
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
+    for (int dy = 0; dy < 2; ++dy) {
+        ru[dy][0] = ru[dy][1] = rv[dy][0] = rv[dy][1] = T(0);
+        rp[dy][0] = -Ap[dy][0];
+        rp[dy][1] = -Ap[dy][1];
+        if (dy == 1 && !yin) continue;
+        // convection: corner contributions of the cells SW, SE, NW, NE of
+        // the two nodes of this row (cells c, c+1, c+CX, c+CX+1 of node 0)
+        const int c = cb + dy * L::CX;
+        T cu[2], cv[2];
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-            ru[dy][dx] = rv[dy][dx] = T(0);
-            rp[dy][dx] = -Ap[dy][dx];
-            if ((dx == 0 || xin) && (dy == 0 || yin)) {
-                // convection: corner contributions of the cells SW, SE, NW, NE of the node
-                const int c = cb + dy * L::CX + dx;
-                const T cu = (cc[3 * L::NCELL + c] + cc[2 * L::NCELL + c + 1]) +
-                             (cc[1 * L::NCELL + c + L::CX] + cc[c + L::CX + 1]);
-                const T cv = (cc[7 * L::NCELL + c] + cc[6 * L::NCELL + c + 1]) +
-                             (cc[5 * L::NCELL + c + L::CX] + cc[4 * L::NCELL + c + L::CX + 1]);
-                const int nb = (2 * by + dy) * L::BX + 2 * bx + dx;
-                ru[dy][dx] = bs[nb] - (Au[dy][dx] + cu);
-                rv[dy][dx] = bs[NYN * L::BX + nb] - (Av[dy][dx] + cv);
-            }
+        for (int comp = 0; comp < 2; ++comp) {
+            T a0, a1, b0, b1, d0, d1, e0, e1;
+            ld2(cc + L::ccx(4 * comp + 3, c), a0, a1);
+            ld2(cc + L::ccx(4 * comp + 2, c + 1), b0, b1);
+            ld2(cc + L::ccx(4 * comp + 1, c + L::CX), d0, d1);
+            ld2(cc + L::ccx(4 * comp + 0, c + L::CX + 1), e0, e1);
+            (comp ? cv : cu)[0] = (a0 + b0) + (d0 + e0);
+            (comp ? cv : cu)[1] = (a1 + b1) + (d1 + e1);
         }
+        T bu0, bu1, bv0, bv1;
+        const int nb = (2 * by + dy) * L::BX + 2 * bx;
+        ld2(bs + nb, bu0, bu1);
+        ld2(bs + NYN * L::BX + nb, bv0, bv1);
+        ru[dy][0] = bu0 - (Au[dy][0] + cu[0]);
+        rv[dy][0] = bv0 - (Av[dy][0] + cv[0]);
+        if (xin) {
+            ru[dy][1] = bu1 - (Au[dy][1] + cu[1]);
+            rv[dy][1] = bv1 - (Av[dy][1] + cv[1]);
+        }
+    }
     if (rf && xin && yin) {   // owned nodes (a fast tile never reaches nxf or nyf)
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
@@ -448,11 +586,7 @@ __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<
             store2(rf + 2 * g.plane + node, rp[dy][0], rp[dy][1]);
         }
     }
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx)
-            put_residual(g, X, pid, tpx, tpy, lS, 2 * bx + dx, 2 * by + dy, ru[dy][dx], rv[dy][dx], rp[dy][dx]);
+    put_block(g, X, pid, tpx, tpy, lS, bx, by, ru, rv, rp);
 }
 
 // S2 + S3 for one 32 x 16-cell tile.  R = 0: x~ is read from xf (S1 done by
@@ -465,9 +599,10 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
                     double inflow_scale, const T *__restrict__ bf, T *__restrict__ rf, TX *__restrict__ X) {
     using L = ResLayout;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T geo_s[12];
     T *xs = reinterpret_cast<T *>(smem_raw);   // [3][HY][HX]   u, v, p
     T *bs = xs + L::XS;                        // [2][NYN][BX]  b_u, b_v
-    T *cc = bs + L::BS;                        // [8][NCELL]    cell contributions (velocity rows)
+    T *cc = bs + L::BS;                        // [8][NCP]      cell contributions (velocity rows)
     T *un = cc + L::CC;                        // coarse window (R > 0), then [9][NLPS] LPS contributions
     int *pid = reinterpret_cast<int *>(un + L::UN);                          // [tpy][tpx] patch numbers
     unsigned char *cf = reinterpret_cast<unsigned char *>(pid + L::MAXP);   // [FY][FX] cell codes
@@ -486,14 +621,16 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
         stage_window<T, 3, L::HY, L::HX>(g, xf, I0 - L::XO, J0 - L::YO, xs);
     }
     for (int e = threadIdx.x; e < tpx * tpy; e += blockDim.x) {
-        const int py = e / tpx, px = e - py * tpx;
+        const int py = e >> (5 - lS), px = e & (tpx - 1);
         const int pi = (I0 >> lS) + px, pj = (J0 >> lS) + py;
         pid[e] = (pi < g.npx && pj < g.npy) ? g.patch_id[pj * g.npx + pi] : -1;
     }
+    if (threadIdx.x < 12) geo_s[threadIdx.x] = fc.geo[threadIdx.x];
     // fast tiles: every cell within two of the tile is fluid and exists, so
     // no tile node is a boundary node and node stencils apply everywhere
-    // (the barrier inside also publishes the coarse window and pid)
-    const bool fast = block_all_fluid(g, I0 - 2, I0 + TXC + 1, J0 - 2, J0 + TYC + 1);
+    // (the barrier inside also publishes the coarse window, pid and geo_s)
+    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 1);
+    __syncthreads();   // publishes the coarse window, pid and geo_s
     if (!fast) {
         for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
             const int jj = idx / L::FX, ii = idx - jj * L::FX;
@@ -527,45 +664,57 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
         for (int tp = warp; tp < tpx * tpy; tp += nw) {
             const int id = pid[tp];
             if (id < 0) continue;
-            const int lpy = tp / tpx, lpx = tp - lpy * tpx;
+            const int lpy = tp >> (5 - lS), lpx = tp & (tpx - 1);
             const T *xbase = xs + lpy * S * L::HX + lpx * S;
             TX *row = X + (size_t)id * g.ldx;
             for (int c = nres + lane; c < g.ldx; c += 32) {
                 const int e = __ldg(g.feat_tab + c);
                 const int kind = e >> 24, off = e & 0xFFFFFF;
-                T val = T(0);
-                if (kind == FEAT_VEL) {
-                    val = xbase[off];
-                } else if (kind == FEAT_PECLET) {
-                    const T u = xbase[off], v = xbase[off + L::HP];
-                    val = fc.q_over_nu * sqrt(u * u + v * v);
-                } else if (kind == FEAT_GEO) {
-                    val = fc.geo[off];
-                }
+                const int o = kind <= FEAT_PECLET ? off : 0;
+                const T a = xbase[o], b = xbase[o + L::HP];
+                T val = kind == FEAT_VEL ? a : (kind == FEAT_GEO ? geo_s[off < 12 ? off : 0] : T(0));
+                if (kind == FEAT_PECLET) val = fc.q_over_nu * sqrt(a * a + b * b);
                 row[c] = store_as<TX, T>(val);
             }
         }
     }
 
     if (fast) {
-        // convection contributions of every cell around the tile's nodes
-        for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
-            const int cj = cid / L::CX, ci = cid - cj * L::CX;   // cell (ci-1, cj-1)
-            const int base = (cj - 1 + L::YO) * L::HX + ci - 1 + L::XO;
-            const T u[4] = {xs[base], xs[base + 1], xs[base + L::HX], xs[base + L::HX + 1]};
-            const T v[4] = {xs[L::HP + base], xs[L::HP + base + 1], xs[L::HP + base + L::HX],
-                            xs[L::HP + base + L::HX + 1]};
-            T cu[4], cv[4];
-            convection(fc, u, v, cu, cv);
+        // convection contributions of every cell around the tile's nodes,
+        // two vertically adjacent cells per thread in packed arithmetic
+        using V = typename Packed<T>::type;
+        const ConvK<V> k2(fc);
+        for (int e = threadIdx.x; e < L::CX * (L::CY / 2); e += blockDim.x) {
+            const int cjp = e / L::CX, ci = e - cjp * L::CX;   // cells (ci-1, 2cjp-1) and (ci-1, 2cjp)
+            const int cid = 2 * cjp * L::CX + ci;
+            const T *q = xs + (2 * cjp - 1 + L::YO) * L::HX + ci - 1 + L::XO;   // SW node of the lower cell
+            V u[4], v[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {   // corners SW, SE, NW, NE
+                const int o = (b >> 1) * L::HX + (b & 1);
+                u[b] = pack2(q[o], q[o + L::HX]);
+                v[b] = pack2(q[L::HP + o], q[L::HP + o + L::HX]);
+            }
+            V cu[4], cv[4];
+            convection(k2, u, v, cu, cv);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                cc[a * L::NCELL + cid] = cu[a];
-                cc[(4 + a) * L::NCELL + cid] = cv[a];
+                T lo, hi;
+                unpack2(cu[a], lo, hi);
+                cc[L::ccx(a, cid)] = lo;
+                cc[L::ccx(a, cid + L::CX)] = hi;
+                unpack2(cv[a], lo, hi);
+                cc[L::ccx(4 + a, cid)] = lo;
+                cc[L::ccx(4 + a, cid + L::CX)] = hi;
             }
         }
         __syncthreads();
+        // 16 blocks of one row per half-warp (contiguous pairs: conflict-free
+        // 64-bit loads), then the last block column
         if (threadIdx.x < L::NB) {
-            const int by = threadIdx.x / L::NBX, bx = threadIdx.x - by * L::NBX;
+            const int t = threadIdx.x;
+            const bool main = t < 16 * L::NBY;
+            const int bx = main ? (t & 15) : L::NBX - 1, by = main ? (t >> 4) : t - 16 * L::NBY;
             block_residual(g, fc, xs, bs, cc, pid, tpx, tpy, lS, I0, J0, bx, by, rf, X);
         }
         return;
@@ -573,6 +722,7 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
 
     // ---- tiles near a boundary: element by element, with the cell codes
     T *lc = un;   // [9][NLPS]
+    const ConvK<T> k1(fc);
     // Phase A: velocity-row contributions of every fluid cell
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
         const int ci = cid % L::CX - 1, cj = cid / L::CX - 1;
@@ -590,7 +740,7 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
                 p[b] = xs[2 * L::HP + base + off[b]];
             }
             T cu[4], cv[4];
-            convection(fc, u, v, cu, cv);
+            convection(k1, u, v, cu, cv);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 T au = T(0), av = T(0);
@@ -604,7 +754,7 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) cc[k * L::NCELL + cid] = out[k];
+        for (int k = 0; k < 8; ++k) cc[L::ccx(k, cid)] = out[k];
     }
     // Phase A': LPS contributions of every fluid 2x2-cell patch touching the tile
     for (int lid = threadIdx.x; lid < L::NLPS; lid += blockDim.x) {
@@ -643,8 +793,8 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
         T Au = T(0), Av = T(0), Ap = T(0);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            Au += cc[corner[t] * L::NCELL + cells[t]];
-            Av += cc[(4 + corner[t]) * L::NCELL + cells[t]];
+            Au += cc[L::ccx(corner[t], cells[t])];
+            Av += cc[L::ccx(4 + corner[t], cells[t])];
         }
         const T *pu = xs + (jj + L::YO - 1) * L::HX + ii + L::XO - 1;   // node (ii-1, jj-1)
         const T *pv = pu + L::HP;
@@ -703,7 +853,8 @@ k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, con
     CWin cw;
     cw.cs = cs_mem;
     if constexpr (R > 0) cw.stage(g, xc, I0, J0);
-    const bool fast = block_all_fluid(g, I0 - 1, I0 + PTX, J0 - 1, J0 + PTY);
+    const bool fast = node_tile_fluid(g, blockIdx.x, blockIdx.y);
+    __syncthreads();   // publishes the staged coarse nodes
     const int J = J0 + threadIdx.x / (PTX / 4);
     const int Ib = I0 + 4 * (threadIdx.x % (PTX / 4));
     if (J > g.nyf) return;
@@ -796,7 +947,7 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
 
     stage_window<T, 2, L::HY, L::HX>(g, vcorr, I0 - L::XO, J0 - L::YO, vs);
-    const bool fast = block_all_fluid(g, I0 - 1, I0 + TXC, J0 - 1, J0 + TYC);
+    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 2);
     if (!fast) {
         for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
             const int jj = idx / L::CX, ii = idx - jj * L::CX;
@@ -821,7 +972,7 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
                 v[b] = vs[L::HY * L::HX + base + off[b]];
             }
             T cu[4], cv[4];
-            convection(fc, u, v, cu, cv);
+            convection(ConvK<T>(fc), u, v, cu, cv);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 out[a] = -cu[a];
@@ -1071,6 +1222,28 @@ void feature_table(const MeshGeom &g, int *tab) {
 }
 
 int feature_table_capacity() { return ResLayout::MAX_LDX; }
+
+void tile_counts(const MeshGeom &g, int *ntx, int *nty) {
+    *ntx = (g.nxf + TXC - 1) / TXC;
+    *nty = (g.nyf + TYC - 1) / TYC;
+}
+
+void tile_flags(const MeshGeom &g, const uint8_t *solid, uint8_t *flags) {
+    auto all_fluid = [&](int i0, int i1, int j0, int j1) {
+        if (i0 < 0 || j0 < 0 || i1 >= g.nxf || j1 >= g.nyf) return false;
+        for (int cj = j0 >> g.K; cj <= j1 >> g.K; ++cj)
+            for (int ci = i0 >> g.K; ci <= i1 >> g.K; ++ci)
+                if (solid[(size_t)cj * g.nxc + ci]) return false;
+        return true;
+    };
+    for (int ty = 0; ty < g.nty; ++ty)
+        for (int tx = 0; tx < g.ntx; ++tx) {
+            const int I0 = tx * TXC, J0 = ty * TYC;
+            flags[(size_t)ty * g.ntx + tx] =
+                (uint8_t)((all_fluid(I0 - 2, I0 + TXC + 1, J0 - 2, J0 + TYC + 1) ? 1 : 0) |
+                          (all_fluid(I0 - 1, I0 + TXC, J0 - 1, J0 + TYC) ? 2 : 0));
+        }
+}
 
 double inflow_ramp(const MeshGeom &g, double t) {
     return g.ramp ? (t <= 0.5 ? 0.5 - 0.5 * cos(2.0 * 3.14159265358979323846 * t) : 1.0) : 1.0;
