@@ -56,11 +56,10 @@ struct TcItem {
     int kind;    // ITEM_*
     int kc;      // K chunk (X chunks first, then h chunks)
     int dcol;    // first TMEM column of the accumulator
-    int acc;     // accumulate into D (0 for the first K chunk of an output block)
 };
 
 struct TcParams {
-    int n_in, ldx, H, n_out, nfc, nxc, nhc, nxs, nitems, end1, end2, first_h, tmem_cols;
+    int n_in, ldx, H, n_out, nfc, nxc, nhc, nxs, nitems, end1, end2, tmem_cols;
     const uint8_t *wblob;
     int *status;
     TcItem items[MAX_ITEMS];
@@ -174,7 +173,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 // byte offset of 16-byte unit u (0..7) of row `row` in a 128B-swizzled chunk
 __device__ __forceinline__ uint32_t swz(int row, int u) { return (uint32_t)(row * 128 + ((u ^ (row & 7)) << 4)); }
-__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
+// Activations on the special-function unit: tanh.approx.f32 (PTX; relative
+// error about 2^-11, well inside the BF16 operand rounding of this kernel)
+// and the logistic function as 1/2 + tanh(x/2)/2.
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sigm(float x) { return fmaf(0.5f, tanh_fast(0.5f * x), 0.5f); }
+
+// Ring position i -> weight item: every CTA walks the items of each phase
+// starting at its own offset, so the CTAs of a wave request different chunks
+// of the (shared, L2-resident) weight blob at any moment instead of all
+// hitting the same lines.
+__device__ __forceinline__ int item_at(const TcParams &p, int i, int rot) {
+    if (i < p.end1) return (i + rot) % p.end1;
+    if (i < p.end2) return p.end1 + (i - p.end1 + rot) % (p.end2 - p.end1);
+    return p.end2 + (i - p.end2 + rot) % (p.nitems - p.end2);
+}
 
 // Store 16 consecutive state columns c0..c0+15 of `row` as bf16 into the h chunks.
 __device__ __forceinline__ void store_h16(uint8_t *sAh, int row, int c0, const float *v) {
@@ -258,7 +275,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
                 // the last HB stages hold the state until the epilogue has read it
                 if (i == NSTAGE - HB && !mbar_wait(ah_bar, 0, abort_flag)) break;
                 if (i >= NSTAGE && !mbar_wait(empty0 + 8 * s, ((i / NSTAGE) - 1) & 1, abort_flag)) break;
-                const TcItem &it = p.items[i];
+                const TcItem &it = p.items[item_at(p, i, blockIdx.x)];
                 expect_tx(full0 + 8 * s, (uint32_t)(it.rows * 128));
                 bulk_load(sW_u + s * CHUNK, p.wblob + it.off, (uint32_t)(it.rows * 128), full0 + 8 * s);
                 issued = i + 1;
@@ -277,21 +294,35 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         if (lane == 0) {
             bool ok = mbar_wait(x_full, 0, abort_flag);
             tc_after_sync();
+            uint32_t inited = 0;   // output blocks (32-column units) written in this phase
+            bool h_ready = false;
             for (int i = 0; ok && i < p.nitems; ++i) {
-                if (i == p.first_h) ok = mbar_wait(ah_bar, 0, abort_flag);
                 if (ok && i == p.end1) ok = mbar_wait(rh_bar, 0, abort_flag);
-                if (ok && i == p.end2) ok = mbar_wait(hn_bar, 0, abort_flag);
+                if (ok && i == p.end2) {
+                    ok = mbar_wait(hn_bar, 0, abort_flag);
+                    inited = 0;   // the output layer starts over in the D1 columns
+                }
+                const TcItem &it = p.items[item_at(p, i, blockIdx.x)];
+                if (ok && i < p.end1 && it.kc >= p.nxc && !h_ready) {
+                    ok = mbar_wait(ah_bar, 0, abort_flag);   // the first h chunk of phase 1
+                    h_ready = true;
+                }
                 const int s = i % NSTAGE;
                 if (ok) ok = mbar_wait(full0 + 8 * s, (i / NSTAGE) & 1, abort_flag);
                 if (!ok) break;
                 tc_after_sync();
-                const TcItem &it = p.items[i];
+                uint32_t accf = 1;   // phase 2 adds onto the candidate accumulator of phase 1
+                if (it.kind != ITEM_D2H) {
+                    const uint32_t bit = 1u << (it.dcol >> 5);
+                    accf = (inited & bit) ? 1u : 0u;
+                    inited |= bit;
+                }
                 const uint32_t a0 = it.kc < p.nxc ? sX_u + it.kc * CHUNK : sAh_u + (it.kc - p.nxc) * CHUNK;
                 const uint32_t b0 = sW_u + s * CHUNK;
                 const uint32_t idesc = idesc_bf16(TM, it.rows);
 #pragma unroll
                 for (int k = 0; k < KC / 16; ++k)
-                    umma(tmem + it.dcol, sdesc(a0 + k * 32), sdesc(b0 + k * 32), idesc, (it.acc || k > 0) ? 1u : 0u);
+                    umma(tmem + it.dcol, sdesc(a0 + k * 32), sdesc(b0 + k * 32), idesc, (accf || k > 0) ? 1u : 0u);
                 tc_commit(empty0 + 8 * s);
                 if (i == p.end1 - 1) tc_commit(d1_bar);
                 if (i == p.end2 - 1) tc_commit(d2_bar);
@@ -359,7 +390,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const float z = sigm(zv[i]);
-                    hv[16 * b + i] = z * hv[16 * b + i] + (1.0f - z) * tanhf(cv[i]);
+                    hv[16 * b + i] = z * hv[16 * b + i] + (1.0f - z) * tanh_fast(cv[i]);
                 }
                 store_h16(sAh, row, c0 + 16 * b, hv + 16 * b);
             }
@@ -471,14 +502,13 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
     std::vector<TcItem> items;
     std::vector<uint8_t> blob;
     // one chunk: rows [r0, r0 + rows) of a B matrix, K columns kc*64 .. kc*64+63
-    auto add = [&](int kind, int kc, int r0, int rows, int dcol, int acc, auto value) {
+    auto add = [&](int kind, int kc, int r0, int rows, int dcol, auto value) {
         TcItem it;
         it.off = (int)blob.size();
         it.rows = rows;
         it.kind = kind;
         it.kc = kc;
         it.dcol = dcol;
-        it.acc = acc;
         blob.resize(blob.size() + (size_t)rows * 128, 0);
         uint8_t *dst = blob.data() + it.off;
         for (int r = 0; r < rows; ++r)
@@ -492,11 +522,9 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
         for (int r0 = 0; r0 < total; r0 += 128) fn(r0, total - r0 < 128 ? total - r0 : 128);
     };
     // phase 1: X chunks (z, r and W_h rows), then h chunks (z and r rows only)
-    p.first_h = -1;
     for (int kc = 0; kc < nxc + nhc; ++kc) {
-        if (kc == nxc) p.first_h = (int)items.size();
         blocks(2 * H, [&](int r0, int rows) {
-            add(ITEM_D1, kc, r0, rows, r0, kc > 0, [&](int r, int k) -> double {
+            add(ITEM_D1, kc, r0, rows, r0, [&](int r, int k) -> double {
                 if (kc < nxc) {
                     const int col = kc * KC + k;
                     return col < n_in ? Wx[(size_t)r * n_in + col] : 0.0;
@@ -507,7 +535,7 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
         });
         if (kc < nxc)
             blocks(H, [&](int r0, int rows) {
-                add(ITEM_D2X, kc, r0, rows, 2 * H + r0, kc > 0, [&](int r, int k) -> double {
+                add(ITEM_D2X, kc, r0, rows, 2 * H + r0, [&](int r, int k) -> double {
                     const int col = kc * KC + k;
                     return col < n_in ? Wx[(size_t)(2 * H + r) * n_in + col] : 0.0;
                 });
@@ -516,7 +544,7 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
     p.end1 = (int)items.size();
     for (int kc = 0; kc < nhc; ++kc)
         blocks(H, [&](int r0, int rows) {
-            add(ITEM_D2H, nxc + kc, r0, rows, 2 * H + r0, 1, [&](int r, int k) -> double {
+            add(ITEM_D2H, nxc + kc, r0, rows, 2 * H + r0, [&](int r, int k) -> double {
                 const int col = kc * KC + k;
                 return col < H ? Uh[(size_t)(2 * H + r) * H + col] : 0.0;
             });
@@ -524,7 +552,7 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
     p.end2 = (int)items.size();
     for (int kc = 0; kc < nhc; ++kc)
         blocks(nfc, [&](int r0, int rows) {
-            add(ITEM_D3, nxc + kc, r0, rows, r0, kc > 0, [&](int r, int k) -> double {
+            add(ITEM_D3, nxc + kc, r0, rows, r0, [&](int r, int k) -> double {
                 const int col = kc * KC + k;
                 return (r < n_out && col < H) ? Wfc[(size_t)r * H + col] : 0.0;
             });
