@@ -843,31 +843,36 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
 // ------------------------------------------------------------------ S5
 // Same tiling as S1: 4 consecutive nodes per thread.  R = 0: v~ is read from
 // xf; R = 2, 4, 8: v~ is interpolated from xc inside the tile (S1 fused).
+// The numbers of the patches holding the tile's nodes are staged once.
 template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS)
 k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, const double *__restrict__ xc,
               double inflow_scale, T *__restrict__ vc) {
     using CWin = CoarseWin<T, (R > 0 ? R : 2), PTX, PTY>;
+    constexpr int PW = PTX / 2 + 2, PH = PTY / 2 + 2;   // patches touching a tile (S = 2 is the most)
     __shared__ T cs_mem[R > 0 ? CWin::N : 1];
+    __shared__ int pid_s[PW * PH];
     const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
+    const int lS = g.K + g.s - 1, S = 1 << lS;   // S = s 2^K with s = 1, 2
+    // patch columns px0 .. px0+npw-1 and rows py0 .. py0+nph-1 hold the tile's nodes
+    const int px0 = (I0 >> lS) - 1, py0 = (J0 >> lS) - 1;
+    const int npw = ((I0 + PTX - 1) >> lS) - px0 + 1, nph = ((J0 + PTY - 1) >> lS) - py0 + 1;
+    for (int e = threadIdx.x; e < npw * nph; e += blockDim.x) {
+        const int b = e / npw, a = e - b * npw;
+        const int pi = px0 + a, pj = py0 + b;
+        pid_s[e] = (pi >= 0 && pj >= 0 && pi < g.npx && pj < g.npy) ? __ldg(g.patch_id + pj * g.npx + pi) : -1;
+    }
     CWin cw;
     cw.cs = cs_mem;
     if constexpr (R > 0) cw.stage(g, xc, I0, J0);
     const bool fast = node_tile_fluid(g, blockIdx.x, blockIdx.y);
-    __syncthreads();   // publishes the staged coarse nodes
+    __syncthreads();   // publishes pid_s and the staged coarse nodes
     const int J = J0 + threadIdx.x / (PTX / 4);
     const int Ib = I0 + 4 * (threadIdx.x % (PTX / 4));
     if (J > g.nyf) return;
     const size_t node = (size_t)J * g.pitch + Ib;
-    const int S = g.S;
-    // patch rows containing J: one, or two on a patch edge (lower one first)
-    int pjs[2], npj = 0;
-    if (J % S == 0) {
-        if (J / S - 1 >= 0) pjs[npj++] = J / S - 1;
-        if (J / S < g.npy) pjs[npj++] = J / S;
-    } else {
-        pjs[npj++] = J / S;
-    }
+    // patch rows holding J: its own, and the one below when J is on a patch edge
+    const int rowA = (J >> lS) - py0, ljA = J & (S - 1);
     T u[4], v[4];
     if constexpr (R > 0) {
 #pragma unroll
@@ -895,27 +900,29 @@ k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, con
                 continue;
             }
         }
-        int pis[2], npi = 0;
-        if (I % S == 0) {
-            if (I / S - 1 >= 0) pis[npi++] = I / S - 1;
-            if (I / S < g.npx) pis[npi++] = I / S;
-        } else {
-            pis[npi++] = I / S;
-        }
+        const int colA = (I >> lS) - px0, liA = I & (S - 1);
         T su = T(0), sv = T(0);
         int cnt = 0;
-        for (int tj = 0; tj < npj; ++tj)
-            for (int ti = 0; ti < npi; ++ti) {
-                const int id = g.patch_id[pjs[tj] * g.npx + pis[ti]];
+        // lower / left patch first
+#pragma unroll
+        for (int oy = 1; oy >= 0; --oy) {
+            if (oy && ljA != 0) continue;
+#pragma unroll
+            for (int ox = 1; ox >= 0; --ox) {
+                if (ox && liA != 0) continue;
+                const int id = pid_s[(rowA - oy) * npw + colA - ox];
                 if (id < 0) continue;
-                const int k = (J - pjs[tj] * S) * (S + 1) + (I - pis[ti] * S);
+                const int k = (ljA + oy * S) * (S + 1) + liA + ox * S;
                 su += d[(size_t)id * g.n_out + k];
                 sv += d[(size_t)id * g.n_out + g.nf + k];
                 ++cnt;
             }
+        }
         if (cnt) {
-            u[q] += su / T(cnt);
-            v[q] += sv / T(cnt);
+            // the mean over the patches; 1, 1/2 and 1/4 are exact
+            const T inv = cnt == 1 ? T(1) : cnt == 2 ? T(0.5) : cnt == 4 ? T(0.25) : T(1) / T(cnt);
+            u[q] += su * inv;
+            v[q] += sv * inv;
         }
     }
     store4(vc + node, u);
