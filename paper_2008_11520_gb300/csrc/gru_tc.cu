@@ -50,19 +50,20 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 
 enum { ITEM_D1 = 0, ITEM_D2X = 1, ITEM_D2H = 2, ITEM_D3 = 3 };
 
-struct TcItem {
-    int off;     // byte offset of the chunk in the weight blob
-    int rows;    // rows of B in this chunk (= MMA N)
-    int kind;    // ITEM_*
-    int kc;      // K chunk (X chunks first, then h chunks)
-    int dcol;    // first TMEM column of the accumulator
-};
+// One weight chunk of the schedule, as the MMA and producer threads read it
+// (one 16-byte shared-memory load per chunk):
+//   x: byte offset of the chunk in the weight blob
+//   y: byte offset of the A operand chunk from the shared-memory base
+//   z: instruction descriptor (M = 128, N = rows)
+//   w: first TMEM column (bits 0-8) | accumulate (bit 9) | first h chunk of
+//      phase 1 (bit 10) | rows of B = MMA N (bits 16-31)
+constexpr uint32_t SCHED_ACC = 1u << 9, SCHED_FIRST_H = 1u << 10;
 
 struct TcParams {
     int n_in, ldx, H, n_out, nfc, nxc, nhc, nxs, nitems, end1, end2, tmem_cols;
     const uint8_t *wblob;
     int *status;
-    TcItem items[MAX_ITEMS];
+    uint4 items[MAX_ITEMS];
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -77,6 +78,15 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -183,16 +193,6 @@ __device__ __forceinline__ float tanh_fast(float x) {
 }
 __device__ __forceinline__ float sigm(float x) { return fmaf(0.5f, tanh_fast(0.5f * x), 0.5f); }
 
-// Ring position i -> weight item: every CTA walks the items of each phase
-// starting at its own offset, so the CTAs of a wave request different chunks
-// of the (shared, L2-resident) weight blob at any moment instead of all
-// hitting the same lines.
-__device__ __forceinline__ int item_at(const TcParams &p, int i, int rot) {
-    if (i < p.end1) return (i + rot) % p.end1;
-    if (i < p.end2) return p.end1 + (i - p.end1 + rot) % (p.end2 - p.end1);
-    return p.end2 + (i - p.end2 + rot) % (p.nitems - p.end2);
-}
-
 // Store 16 consecutive state columns c0..c0+15 of `row` as bf16 into the h chunks.
 __device__ __forceinline__ void store_h16(uint8_t *sAh, int row, int c0, const float *v) {
     uint8_t *chunk = sAh + (c0 / KC) * CHUNK;
@@ -219,6 +219,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
     // barriers: full[NSTAGE], empty[NSTAGE], x_full, ah, d1, rh, d2, hn, d3, drain, h_full
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 9);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint4 *sched = reinterpret_cast<uint4 *>(bars + 2 * NSTAGE + 12);   // [nitems], 16-byte aligned
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p0 = blockIdx.x * TM;
@@ -249,6 +250,8 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
+    if (warp == 2)
+        for (int i = lane; i < p.nitems; i += 32) sched[i] = p.items[i];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(p.tmem_cols)
@@ -270,15 +273,21 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
             expect_tx(h_full, (uint32_t)(HB * CHUNK));
             for (int q = 0; q < HB; ++q) tma_load_2d(smem_u32(sH) + q * CHUNK, &tmH, 32 * q, p0, h_full);
             int issued = 0;
+            uint32_t s = 0, ph = 1;   // ring stage and the parity of its previous release
             for (int i = 0; i < p.nitems; ++i) {
-                const int s = i % NSTAGE;
                 // the last HB stages hold the state until the epilogue has read it
                 if (i == NSTAGE - HB && !mbar_wait(ah_bar, 0, abort_flag)) break;
-                if (i >= NSTAGE && !mbar_wait(empty0 + 8 * s, ((i / NSTAGE) - 1) & 1, abort_flag)) break;
-                const TcItem &it = p.items[item_at(p, i, blockIdx.x)];
-                expect_tx(full0 + 8 * s, (uint32_t)(it.rows * 128));
-                bulk_load(sW_u + s * CHUNK, p.wblob + it.off, (uint32_t)(it.rows * 128), full0 + 8 * s);
+                const uint32_t eb = empty0 + 8 * s;
+                if (i >= NSTAGE && !mbar_test(eb, ph) && !mbar_wait(eb, ph, abort_flag)) break;
+                const uint4 it = sched[i];
+                const uint32_t bytes = (it.w >> 16) * 128;
+                expect_tx(full0 + 8 * s, bytes);
+                bulk_load(sW_u + s * CHUNK, p.wblob + it.x, bytes, full0 + 8 * s);
                 issued = i + 1;
+                if (++s == NSTAGE) {
+                    s = 0;
+                    ph ^= 1;
+                }
             }
             if (*abort_flag) {
                 // let every started copy land before the CTA may exit
@@ -294,36 +303,28 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         if (lane == 0) {
             bool ok = mbar_wait(x_full, 0, abort_flag);
             tc_after_sync();
-            uint32_t inited = 0;   // output blocks (32-column units) written in this phase
-            bool h_ready = false;
+            uint32_t s = 0, ph = 0;   // ring stage and the parity of its current fill
+            const uint32_t base_u = smem_u32(base);
             for (int i = 0; ok && i < p.nitems; ++i) {
-                if (ok && i == p.end1) ok = mbar_wait(rh_bar, 0, abort_flag);
-                if (ok && i == p.end2) {
-                    ok = mbar_wait(hn_bar, 0, abort_flag);
-                    inited = 0;   // the output layer starts over in the D1 columns
-                }
-                const TcItem &it = p.items[item_at(p, i, blockIdx.x)];
-                if (ok && i < p.end1 && it.kc >= p.nxc && !h_ready) {
-                    ok = mbar_wait(ah_bar, 0, abort_flag);   // the first h chunk of phase 1
-                    h_ready = true;
-                }
-                const int s = i % NSTAGE;
-                if (ok) ok = mbar_wait(full0 + 8 * s, (i / NSTAGE) & 1, abort_flag);
+                const uint4 it = sched[i];
+                if (i == p.end1) ok = mbar_wait(rh_bar, 0, abort_flag);
+                if (ok && i == p.end2) ok = mbar_wait(hn_bar, 0, abort_flag);
+                if (ok && (it.w & SCHED_FIRST_H)) ok = mbar_wait(ah_bar, 0, abort_flag);
+                const uint32_t fb = full0 + 8 * s;
+                if (ok && !mbar_test(fb, ph)) ok = mbar_wait(fb, ph, abort_flag);
                 if (!ok) break;
                 tc_after_sync();
-                uint32_t accf = 1;   // phase 2 adds onto the candidate accumulator of phase 1
-                if (it.kind != ITEM_D2H) {
-                    const uint32_t bit = 1u << (it.dcol >> 5);
-                    accf = (inited & bit) ? 1u : 0u;
-                    inited |= bit;
-                }
-                const uint32_t a0 = it.kc < p.nxc ? sX_u + it.kc * CHUNK : sAh_u + (it.kc - p.nxc) * CHUNK;
-                const uint32_t b0 = sW_u + s * CHUNK;
-                const uint32_t idesc = idesc_bf16(TM, it.rows);
+                // K steps of 16 elements advance both start addresses by 32 bytes (2 descriptor units)
+                const uint64_t ad = sdesc(base_u + it.y), bd = sdesc(sW_u + s * CHUNK);
+                const uint32_t dt = tmem + (it.w & 0x1FFu);
+                umma(dt, ad, bd, it.z, (it.w & SCHED_ACC) ? 1u : 0u);
 #pragma unroll
-                for (int k = 0; k < KC / 16; ++k)
-                    umma(tmem + it.dcol, sdesc(a0 + k * 32), sdesc(b0 + k * 32), idesc, (accf || k > 0) ? 1u : 0u);
+                for (int k = 1; k < KC / 16; ++k) umma(dt, ad + 2 * k, bd + 2 * k, it.z, 1u);
                 tc_commit(empty0 + 8 * s);
+                if (++s == NSTAGE) {
+                    s = 0;
+                    ph ^= 1;
+                }
                 if (i == p.end1 - 1) tc_commit(d1_bar);
                 if (i == p.end2 - 1) tc_commit(d2_bar);
                 if (i == p.nitems - 1) tc_commit(d3_bar);
@@ -464,7 +465,8 @@ inline size_t swz_host(int row, int k) {
 }
 
 size_t smem_bytes(const TcParams &p) {
-    return (size_t)(p.nxs + p.nhc + NSTAGE) * CHUNK + 1024 + 256;
+    // operand chunks, ring, alignment slack, barriers and flags (256 B), schedule
+    return (size_t)(p.nxs + p.nhc + NSTAGE) * CHUNK + 1024 + 256 + MAX_ITEMS * sizeof(uint4);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -499,11 +501,14 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
     memset(&p, 0, sizeof p);
     p.n_in = n_in; p.ldx = ldx; p.H = H; p.n_out = n_out; p.nfc = nfc; p.nxc = nxc; p.nhc = nhc;
     p.nxs = nxc > H / 32 ? nxc : H / 32;
-    std::vector<TcItem> items;
+    struct HostItem {
+        int off, rows, kind, kc, dcol;
+    };
+    std::vector<HostItem> items;
     std::vector<uint8_t> blob;
     // one chunk: rows [r0, r0 + rows) of a B matrix, K columns kc*64 .. kc*64+63
     auto add = [&](int kind, int kc, int r0, int rows, int dcol, auto value) {
-        TcItem it;
+        HostItem it;
         it.off = (int)blob.size();
         it.rows = rows;
         it.kind = kind;
@@ -562,7 +567,23 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
     int cols = 32;
     while (cols < 3 * H) cols *= 2;
     p.tmem_cols = cols;
-    for (int i = 0; i < p.nitems; ++i) p.items[i] = items[i];
+    // schedule words; a chunk accumulates unless it is the first K chunk of
+    // its output block within its phase (phase 2 always adds onto phase 1)
+    bool seen_h = false;
+    for (int i = 0; i < p.nitems; ++i) {
+        const HostItem &it = items[i];
+        bool acc = it.kind == ITEM_D2H;
+        for (int j = i - 1; !acc && j >= 0; --j) {
+            const bool same_phase = (j < p.end1) == (i < p.end1) && (j >= p.end2) == (i >= p.end2);
+            acc = same_phase && items[j].dcol == it.dcol && items[j].kind == it.kind;
+        }
+        const bool first_h = i < p.end1 && it.kc >= nxc && !seen_h;
+        seen_h = seen_h || first_h;
+        const int achunk = it.kc < nxc ? it.kc : p.nxs + it.kc - nxc;
+        p.items[i] = make_uint4((uint32_t)it.off, (uint32_t)(achunk * CHUNK), idesc_bf16(TM, it.rows),
+                                (uint32_t)it.dcol | (acc ? SCHED_ACC : 0u) | (first_h ? SCHED_FIRST_H : 0u) |
+                                    ((uint32_t)it.rows << 16));
+    }
     if (smem_bytes(p) > 227 * 1024) return false;
     void *dblob = nullptr;
     if (cudaMalloc(&dblob, blob.size()) != cudaSuccess) return false;
