@@ -209,6 +209,17 @@ int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *b
 int dnnmg_rhs(dnnmg_mesh_t mesh, const void *vcorr, void *bf, cudaStream_t stream);
 
 /*
+ * S5 + S6 fused, Algorithm 2 lines 7-8: bf = Rhs(v~ + averaged d) with
+ * v~ = P xc at time t formed inside each tile (as dnnmg_scatter_avg with xc
+ * followed by dnnmg_rhs, same arithmetic); v_corr never reaches memory,
+ * at the price of averaging every tile's one-node halo again.
+ *   d [P][n_out] real (in; ignored if P = 0), xc [3][Nc] double (in),
+ *   bf [2][plane] real (out).
+ */
+int dnnmg_scatter_rhs(dnnmg_mesh_t mesh, const void *d, const double *xc, double t, void *bf,
+                      cudaStream_t stream);
+
+/*
  * S7 alone, Algorithm 2 line 9: bc = R bf with R = P^T (the transpose of the
  * bilinear prolongation across the K levels), coarse Dirichlet velocity rows
  * and all pressure rows zero.  Float input is accumulated with error-free

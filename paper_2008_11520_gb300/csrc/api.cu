@@ -610,6 +610,16 @@ int dnnmg_rhs(dnnmg_mesh_t mesh, const void *vcorr, void *bf, cudaStream_t strea
     return DNNMG_OK;
 }
 
+int dnnmg_scatter_rhs(dnnmg_mesh_t mesh, const void *d, const double *xc, double t, void *bf,
+                      cudaStream_t stream) {
+    clear_error();
+    if (int e = check_mesh(mesh)) return e;
+    if ((!d && mesh->info.P) || !xc || !bf) return fail(DNNMG_EINVAL, "NULL array");
+    if (!aligned16(bf)) return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
+    DNNMG_CUDA_TRY(launch_avg_rhs(mesh->g, mesh->info.precision, mesh->fem64, mesh->fem32, d, xc, t, bf, stream));
+    return DNNMG_OK;
+}
+
 int dnnmg_restrict(dnnmg_mesh_t mesh, const void *bf, double *bc, cudaStream_t stream) {
     clear_error();
     if (int e = check_mesh(mesh)) return e;
@@ -654,8 +664,10 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
                      double *bc, const Workspace &w, double t, cudaStream_t s) {
     const int prec = mesh->info.precision;
     const MeshGeom &g = mesh->g;
-    // S1 is fused into S2+S3 and S5: both interpolate x~ from xc inside their
-    // tiles, so x~ never goes to memory
+    // S1 is fused into S2+S3 and into S5: both interpolate x~ from xc inside
+    // their tiles, so x~ never goes to memory.  (S5+S6 as one kernel keeps
+    // v_corr on chip but recomputes the averaging on every tile's halo, which
+    // costs more than the v_corr round trip; see dnnmg_scatter_rhs.)
     DNNMG_CUDA_TRY(launch_residual_features(g, prec, mesh->fem64, mesh->fem32, nullptr, xc, t, bf, nullptr, w.X, s));
     if (mesh->info.P) DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
     DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, nullptr, xc, t, w.vc, s));

@@ -124,6 +124,9 @@ cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const
                                double t, void *vcorr, cudaStream_t st);
 cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
                        const FemCoef<float> &f32, const void *vcorr, void *bf, cudaStream_t st);
+// S5 + S6 fused: b_f = Rhs(P x_c + mean of d) without writing v_corr.
+cudaError_t launch_avg_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
+                           const void *d, const double *xc, double t, void *bf, cudaStream_t st);
 cudaError_t launch_restrict(const MeshGeom &g, int prec, const void *bf, double *bc,
                             cudaStream_t st);
 cudaError_t launch_mesh_maps(const MeshGeom &g, unsigned char *flags, unsigned char *mult,

@@ -114,11 +114,12 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 // kernel that interpolates a node produces the same bits.
 template <typename T> __device__ __forceinline__ T lerp(T lo, T hi, T w) { return fma_t(w, hi - lo, lo); }
 
-template <typename T, int R, int FW, int FH>
+// NC = 3 stages u, v, p; NC = 2 the velocity only.
+template <typename T, int R, int FW, int FH, int NC = 3>
 struct CoarseWin {
     static constexpr int K = Log2<R>::v;
-    static constexpr int CW = (FW - 1) / R + 3, CH = (FH - 1) / R + 3, N = 3 * CW * CH;
-    T *cs;          // [3][CH][CW] in shared memory
+    static constexpr int CW = (FW - 1) / R + 3, CH = (FH - 1) / R + 3, N = NC * CW * CH;
+    T *cs;          // [NC][CH][CW] in shared memory
     int ci0, cj0;   // first staged coarse node (may be negative)
 
     __device__ __forceinline__ void stage(const MeshGeom &g, const double *__restrict__ xc, int Ilo, int Jlo) {
@@ -134,28 +135,36 @@ struct CoarseWin {
             cs[e] = v;
         }
     }
-    // Bilinear value of all three fields at fine node (I, J) (raw P, no BC):
+    // Bilinear value of the staged fields at fine node (I, J) (raw P, no BC):
     // blends along x on the cell's bottom and top edges, then along y.
-    __device__ __forceinline__ void interp(int I, int J, T (&out)[3]) const {
+    __device__ __forceinline__ void interp(int I, int J, T (&out)[NC]) const {
         constexpr T inv_r = T(1) / T(R);   // exact: R is a power of two
         const int ci = I >> K, cj = J >> K;
         const T a = T(I & (R - 1)) * inv_r, b = T(J & (R - 1)) * inv_r;
         const int o = (cj - cj0) * CW + (ci - ci0);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < NC; ++c) {
             const T *q = cs + c * CW * CH + o;
             out[c] = lerp(lerp(q[0], q[1], a), lerp(q[CW], q[CW + 1], a), b);
         }
     }
 };
 
-// Dirichlet velocity of fine node (I, J) if it has one (Sec. 6.1).
+// Parabolic inflow u = up 4 y (ly - y) / ly^2 at fine row J, up the (ramped)
+// peak velocity: evaluated in FP64 and rounded once.  Kept out of line so
+// that only inflow nodes execute it (FP64 runs at 1/64 of FP32 on GB300).
+template <typename T> __device__ __noinline__ T inflow_value(const MeshGeom &g, int J, double up) {
+    const double y = J * g.hyf;
+    return (T)(up * 4.0 * y * (g.ly - y) / (g.ly * g.ly));
+}
+
+// Dirichlet velocity of fine node (I, J) if it has one (Sec. 6.1): the
+// inflow profile on the left boundary, no-slip elsewhere.
 template <typename T>
-__device__ __forceinline__ bool dirichlet_value(const MeshGeom &g, int I, int J, double inflow_scale, T &u, T &v) {
+__device__ __forceinline__ bool dirichlet_value(const MeshGeom &g, int I, int J, double up, T &u, T &v) {
     const NodeClass nc = classify_global(g, I, J);
     if (!nc.dirichlet) return false;
-    const double y = J * g.hyf;
-    u = nc.inflow ? (T)(g.u_max * 4.0 * y * (g.ly - y) / (g.ly * g.ly) * inflow_scale) : T(0);
+    u = nc.inflow ? inflow_value<T>(g, J, up) : T(0);
     v = T(0);
     return true;
 }
@@ -183,7 +192,7 @@ constexpr int PTX = 64, PTY = 16;
 
 template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS)
-k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, double inflow_scale) {
+k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, double up) {
     using CW = CoarseWin<T, R, PTX, PTY>;
     __shared__ T cs_mem[CW::N];
     const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
@@ -203,7 +212,7 @@ k_prolongate(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xf, doub
         const int I = Ib + q;
         T x[3];
         cw.interp(I, J, x);
-        if (!fast && I <= g.nxf) dirichlet_value(g, I, J, inflow_scale, x[0], x[1]);
+        if (!fast && I <= g.nxf) dirichlet_value(g, I, J, up, x[0], x[1]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) val[c][q] = x[c];
     }
@@ -596,7 +605,7 @@ __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<
 template <typename T, typename TX, int R>
 __global__ void __launch_bounds__(NTHREADS)
 k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const double *__restrict__ xc,
-                    double inflow_scale, const T *__restrict__ bf, T *__restrict__ rf, TX *__restrict__ X) {
+                    double inflow_peak, const T *__restrict__ bf, T *__restrict__ rf, TX *__restrict__ X) {
     using L = ResLayout;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T geo_s[12];
@@ -647,7 +656,7 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
                 const int jj = e / L::HX, ii = e - jj * L::HX;
                 const int I = I0 - L::XO + ii, J = J0 - L::YO + jj;
                 if (I >= 0 && I <= g.nxf && J >= 0 && J <= g.nyf)
-                    dirichlet_value(g, I, J, inflow_scale, xs[e], xs[L::HP + e]);
+                    dirichlet_value(g, I, J, inflow_peak, xs[e], xs[L::HP + e]);
             }
         }
     }
@@ -841,134 +850,218 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
 }
 
 // ------------------------------------------------------------------ S5
-// Same tiling as S1: 4 consecutive nodes per thread.  R = 0: v~ is read from
-// xf; R = 2, 4, 8: v~ is interpolated from xc inside the tile (S1 fused).
-// The numbers of the patches holding the tile's nodes are staged once.
-template <typename T, int R>
-__global__ void __launch_bounds__(NTHREADS)
-k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, const double *__restrict__ xc,
-              double inflow_scale, T *__restrict__ vc) {
-    using CWin = CoarseWin<T, (R > 0 ? R : 2), PTX, PTY>;
-    constexpr int PW = PTX / 2 + 2, PH = PTY / 2 + 2;   // patches touching a tile (S = 2 is the most)
-    __shared__ T cs_mem[R > 0 ? CWin::N : 1];
-    __shared__ int pid_s[PW * PH];
-    const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
-    const int lS = g.K + g.s - 1, S = 1 << lS;   // S = s 2^K with s = 1, 2
-    // patch columns px0 .. px0+npw-1 and rows py0 .. py0+nph-1 hold the tile's nodes
-    const int px0 = (I0 >> lS) - 1, py0 = (J0 >> lS) - 1;
-    const int npw = ((I0 + PTX - 1) >> lS) - px0 + 1, nph = ((J0 + PTY - 1) >> lS) - py0 + 1;
-    for (int e = threadIdx.x; e < npw * nph; e += blockDim.x) {
-        const int b = e / npw, a = e - b * npw;
-        const int pi = px0 + a, pj = py0 + b;
-        pid_s[e] = (pi >= 0 && pj >= 0 && pi < g.npx && pj < g.npy) ? __ldg(g.patch_id + pj * g.npx + pi) : -1;
-    }
-    CWin cw;
-    cw.cs = cs_mem;
-    if constexpr (R > 0) cw.stage(g, xc, I0, J0);
-    const bool fast = node_tile_fluid(g, blockIdx.x, blockIdx.y);
-    __syncthreads();   // publishes pid_s and the staged coarse nodes
-    const int J = J0 + threadIdx.x / (PTX / 4);
-    const int Ib = I0 + 4 * (threadIdx.x % (PTX / 4));
-    if (J > g.nyf) return;
-    const size_t node = (size_t)J * g.pitch + Ib;
-    // patch rows holding J: its own, and the one below when J is on a patch edge
-    const int rowA = (J >> lS) - py0, ljA = J & (S - 1);
-    T u[4], v[4];
-    if constexpr (R > 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            T x[3];
-            cw.interp(Ib + q, J, x);
-            u[q] = x[0];
-            v[q] = x[1];
+// Patch numbers of every patch holding a node of the window [Ilo, Ihi] x
+// [Jlo, Jhi]: columns px0 .. px0+npw-1, rows py0 .. py0+nph-1 (-1: none).
+struct PatchWin {
+    int *pid;
+    int px0, py0, npw, lS;
+    __device__ __forceinline__ void stage(const MeshGeom &g, int Ilo, int Ihi, int Jlo, int Jhi) {
+        lS = g.K + g.s - 1;   // S = s 2^K with s = 1, 2
+        px0 = (Ilo >> lS) - 1;
+        py0 = (Jlo >> lS) - 1;
+        npw = (Ihi >> lS) - px0 + 1;
+        const int nph = (Jhi >> lS) - py0 + 1;
+        for (int e = threadIdx.x; e < npw * nph; e += blockDim.x) {
+            const int b = e / npw, a = e - b * npw;
+            const int pi = px0 + a, pj = py0 + b;
+            pid[e] = (pi >= 0 && pj >= 0 && pi < g.npx && pj < g.npy) ? __ldg(g.patch_id + pj * g.npx + pi) : -1;
         }
-    } else {
-        load4(xf + node, u);
-        load4(xf + g.plane + node, v);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int I = Ib + q;
-        if (I > g.nxf) continue;
-        if (!fast) {
-            T uD, vD;
-            if (dirichlet_value(g, I, J, inflow_scale, uD, vD)) {   // keeps v~ = the boundary value
-                if constexpr (R > 0) {
-                    u[q] = uD;
-                    v[q] = vD;
-                }
-                continue;
-            }
-        }
-        const int colA = (I >> lS) - px0, liA = I & (S - 1);
+    // v~ + the mean of d over the fluid patches holding node (I, J) (Eq. for
+    // the averaged correction: every patch holding a node contributes its
+    // network output for that node, lower / left patches first)
+    template <typename T>
+    __device__ __forceinline__ void add_mean(const MeshGeom &g, const T *__restrict__ d, int I, int J, T &u,
+                                             T &v) const {
+        const int S = 1 << lS;
+        const int row = (J >> lS) - py0, lj = J & (S - 1), col = (I >> lS) - px0, li = I & (S - 1);
         T su = T(0), sv = T(0);
         int cnt = 0;
-        // lower / left patch first
 #pragma unroll
         for (int oy = 1; oy >= 0; --oy) {
-            if (oy && ljA != 0) continue;
+            if (oy && lj != 0) continue;
 #pragma unroll
             for (int ox = 1; ox >= 0; --ox) {
-                if (ox && liA != 0) continue;
-                const int id = pid_s[(rowA - oy) * npw + colA - ox];
+                if (ox && li != 0) continue;
+                const int id = pid[(row - oy) * npw + col - ox];
                 if (id < 0) continue;
-                const int k = (ljA + oy * S) * (S + 1) + liA + ox * S;
-                su += d[(size_t)id * g.n_out + k];
-                sv += d[(size_t)id * g.n_out + g.nf + k];
+                const int k = (lj + oy * S) * (S + 1) + li + ox * S;
+                su += __ldg(d + (size_t)id * g.n_out + k);
+                sv += __ldg(d + (size_t)id * g.n_out + g.nf + k);
                 ++cnt;
             }
         }
         if (cnt) {
-            // the mean over the patches; 1, 1/2 and 1/4 are exact
+            // 1, 1/2 and 1/4 are exact
             const T inv = cnt == 1 ? T(1) : cnt == 2 ? T(0.5) : cnt == 4 ? T(0.25) : T(1) / T(cnt);
-            u[q] += su * inv;
-            v[q] += sv * inv;
+            u += su * inv;
+            v += sv * inv;
         }
     }
-    store4(vc + node, u);
-    store4(vc + g.plane + node, v);
+};
+
+// A CTA owns 64 x 16 nodes; lanes take consecutive nodes of a row (so the
+// reads of d are contiguous runs of each patch row), each thread 4 rows.
+// R = 0: v~ is read from xf; R = 2, 4, 8: v~ is interpolated from xc inside
+// the tile (S1 fused).
+template <typename T, int R>
+__global__ void __launch_bounds__(NTHREADS)
+k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, const double *__restrict__ xc,
+              double inflow_peak, T *__restrict__ vc) {
+    using CWin = CoarseWin<T, (R > 0 ? R : 2), PTX, PTY, 2>;
+    __shared__ T cs_mem[R > 0 ? CWin::N : 1];
+    __shared__ int pid_s[(PTX / 2 + 2) * (PTY / 2 + 2)];   // S = 2 holds the most patches
+    const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
+    PatchWin pw;
+    pw.pid = pid_s;
+    pw.stage(g, I0, I0 + PTX - 1, J0, J0 + PTY - 1);
+    CWin cw;
+    cw.cs = cs_mem;
+    if constexpr (R > 0) cw.stage(g, xc, I0, J0);
+    const bool fast = node_tile_fluid(g, blockIdx.x, blockIdx.y);
+    const double up = inflow_peak;
+    __syncthreads();   // publishes pid_s and the staged coarse nodes
+    const int I = I0 + (threadIdx.x & (PTX - 1));
+    if (I > g.nxf) return;
+    // a fixed trip count lets the loads of all rows be in flight together
+#pragma unroll
+    for (int k = 0; k < PTY / (NTHREADS / PTX); ++k) {
+        const int J = J0 + threadIdx.x / PTX + k * (NTHREADS / PTX);
+        if (J > g.nyf) break;
+        const size_t node = (size_t)J * g.pitch + I;
+        T u, v;
+        if constexpr (R > 0) {
+            T x[2];
+            cw.interp(I, J, x);
+            u = x[0];
+            v = x[1];
+        } else {
+            u = xf[node];
+            v = xf[g.plane + node];
+        }
+        T uD, vD;
+        if (!fast && dirichlet_value(g, I, J, up, uD, vD)) {   // keeps v~ = the boundary value
+            if constexpr (R > 0) {
+                u = uD;
+                v = vD;
+            }
+        } else {
+            pw.add_mean(g, d, I, J, u, v);
+        }
+        vc[node] = u;
+        vc[g.plane + node] = v;
+    }
 }
 
 // ------------------------------------------------------------------ S6
 // Node window of v_corr: columns I0-4 .. I0+35 (node I0+ii at column ii+4),
 // rows J0-1 .. J0+17 (node J0+jj at row jj+1).
 struct RhsLayout {
-    static constexpr int HX = 40, HY = NYN + 2, XO = 4, YO = 1;
-    static constexpr int CX = TXC + 2, CY = TYC + 2;   // cells -1..TXC
+    static constexpr int HX = 40, HY = NYN + 2, XO = 4, YO = 1, HP = HX * HY;
+    static constexpr int CX = TXC + 2, CY = TYC + 2;   // cells -1 .. 32 x -1 .. 16
     static constexpr int NCELL = CX * CY;
-    static constexpr int VS = 2 * HY * HX;
-    static constexpr int CC = 8 * NCELL;
-    template <typename T> static constexpr size_t bytes() {
-        return sizeof(T) * (VS + CC) + NCELL;
-    }
+    static constexpr int NCP = NCELL + 4;              // corner arrays, as in ResLayout
+    static constexpr int VS = 2 * HP;
+    static constexpr int CC = 8 * NCP;
+    template <typename T> static constexpr size_t bytes() { return sizeof(T) * (VS + CC) + NCELL; }
+    static __device__ __forceinline__ int ccx(int k, int cid) { return k * NCP + cid + ((k & 1) ^ 1); }
 };
 
+// Right-hand side (Eq. 4cranknicholson3: (1/k M - nu/2 K) v - 1/2 (v.grad v, phi))
+// of the owned nodes of one 32 x 16-cell tile from the v_corr window vs.
+// Tiles whose neighbourhood is fluid: convection per cell (two vertically
+// adjacent cells per thread in packed arithmetic), then per 2x2 node block
+// the node stencil of the linear term plus the four cells' convection
+// corners, read as aligned pairs; 16 blocks of a row per half-warp.  Other
+// tiles: element by element with the cell codes cf.
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS)
-k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf) {
+__device__ __forceinline__ void rhs_tile(const MeshGeom &g, const FemCoef<T> &fc, const T *vs, T *cc,
+                                         const unsigned char *cf, bool fast, int I0, int J0, T *__restrict__ bf) {
     using L = RhsLayout;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *vs = reinterpret_cast<T *>(smem_raw);   // [2][HY][HX]
-    T *cc = vs + L::VS;                        // [8][NCELL]
-    unsigned char *cf = reinterpret_cast<unsigned char *>(cc + L::CC);  // [CY][CX]
-    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
-
-    stage_window<T, 2, L::HY, L::HX>(g, vcorr, I0 - L::XO, J0 - L::YO, vs);
-    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 2);
-    if (!fast) {
-        for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
-            const int jj = idx / L::CX, ii = idx - jj * L::CX;
-            cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
+    if (fast) {
+        using V = typename Packed<T>::type;
+        const ConvK<V> k2(fc);
+        for (int e = threadIdx.x; e < L::CX * (L::CY / 2); e += blockDim.x) {
+            const int cjp = e / L::CX, ci = e - cjp * L::CX;   // cells (ci-1, 2cjp-1) and (ci-1, 2cjp)
+            const int cid = 2 * cjp * L::CX + ci;
+            const T *q = vs + (2 * cjp - 1 + L::YO) * L::HX + ci - 1 + L::XO;   // SW node of the lower cell
+            V u[4], v[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {   // corners SW, SE, NW, NE
+                const int o = (b >> 1) * L::HX + (b & 1);
+                u[b] = pack2(q[o], q[o + L::HX]);
+                v[b] = pack2(q[L::HP + o], q[L::HP + o + L::HX]);
+            }
+            V cu[4], cv[4];
+            convection(k2, u, v, cu, cv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                T lo, hi;
+                unpack2(cu[a], lo, hi);
+                cc[L::ccx(a, cid)] = -lo;
+                cc[L::ccx(a, cid + L::CX)] = -hi;
+                unpack2(cv[a], lo, hi);
+                cc[L::ccx(4 + a, cid)] = -lo;
+                cc[L::ccx(4 + a, cid + L::CX)] = -hi;
+            }
         }
+        __syncthreads();
+        if (threadIdx.x < (TXC / 2) * (TYC / 2)) {
+            const int bx = threadIdx.x & 15, by = threadIdx.x >> 4;   // nodes 2bx .. 2bx+1, 2by .. 2by+1
+            // window rows 2by-1 .. 2by+2, columns 2bx-2 .. 2bx+3 (even start: aligned pairs)
+            const T *w = vs + (2 * by + L::YO - 1) * L::HX + 2 * bx + L::XO - 2;
+            T Bu[2][2], Bv[2][2];
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) Bu[dy][0] = Bu[dy][1] = Bv[dy][0] = Bv[dy][1] = T(0);
+#pragma unroll
+            for (int ry = 0; ry < 4; ++ry) {
+                T u[6], v[6];
+#pragma unroll
+                for (int k = 0; k < 6; k += 2) {
+                    ld2(w + ry * L::HX + k, u[k], u[k + 1]);
+                    ld2(w + ry * L::HX + L::HP + k, v[k], v[k + 1]);
+                }
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const int sy = ry - dy;
+                    if (sy < 0 || sy > 2) continue;
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+                        for (int sx = 0; sx < 3; ++sx) {
+                            Bu[dy][dx] += fc.nB[sy][sx] * u[dx + sx + 1];
+                            Bv[dy][dx] += fc.nB[sy][sx] * v[dx + sx + 1];
+                        }
+                }
+            }
+            const int cb = 2 * by * L::CX + 2 * bx;   // cell (2bx-1, 2by-1)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                const int c = cb + dy * L::CX;
+                T cu[2], cv[2];
+#pragma unroll
+                for (int comp = 0; comp < 2; ++comp) {
+                    T a0, a1, b0, b1, d0, d1, e0, e1;
+                    ld2(cc + L::ccx(4 * comp + 3, c), a0, a1);
+                    ld2(cc + L::ccx(4 * comp + 2, c + 1), b0, b1);
+                    ld2(cc + L::ccx(4 * comp + 1, c + L::CX), d0, d1);
+                    ld2(cc + L::ccx(4 * comp + 0, c + L::CX + 1), e0, e1);
+                    (comp ? cv : cu)[0] = (a0 + b0) + (d0 + e0);
+                    (comp ? cv : cu)[1] = (a1 + b1) + (d1 + e1);
+                }
+                const size_t node = (size_t)(J0 + 2 * by + dy) * g.pitch + I0 + 2 * bx;
+                store2(bf + node, Bu[dy][0] + cu[0], Bu[dy][1] + cu[1]);
+                store2(bf + g.plane + node, Bv[dy][0] + cv[0], Bv[dy][1] + cv[1]);
+            }
+        }
+        return;
     }
-    cp_async_wait_all();
-    __syncthreads();
-
+    const ConvK<T> k1(fc);
     for (int cid = threadIdx.x; cid < L::NCELL; cid += blockDim.x) {
         T out[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) out[k] = T(0);
-        if (fast || cf[cid] == 1) {
+        if (cf[cid] == 1) {
             const int ci = cid % L::CX, cj = cid / L::CX;   // cell (ci-1, cj-1) of the tile
             const int base = cj * L::HX + ci + L::XO - 1;    // its SW node
             const int off[4] = {0, 1, L::HX, L::HX + 1};
@@ -976,34 +1069,26 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 u[b] = vs[base + off[b]];
-                v[b] = vs[L::HY * L::HX + base + off[b]];
+                v[b] = vs[L::HP + base + off[b]];
             }
             T cu[4], cv[4];
-            convection(ConvK<T>(fc), u, v, cu, cv);
+            convection(k1, u, v, cu, cv);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                out[a] = -cu[a];
-                out[4 + a] = -cv[a];
-            }
-            if (!fast) {
+                T bu = T(0), bv = T(0);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    T bu = T(0), bv = T(0);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        bu += fc.Bv[a][b] * u[b];
-                        bv += fc.Bv[a][b] * v[b];
-                    }
-                    out[a] += bu;
-                    out[4 + a] += bv;
+                for (int b = 0; b < 4; ++b) {
+                    bu += fc.Bv[a][b] * u[b];
+                    bv += fc.Bv[a][b] * v[b];
                 }
+                out[a] = bu - cu[a];
+                out[4 + a] = bv - cv[a];
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) cc[k * L::NCELL + cid] = out[k];
+        for (int k = 0; k < 8; ++k) cc[L::ccx(k, cid)] = out[k];
     }
     __syncthreads();
-
     for (int nid = threadIdx.x; nid < NXN * NYN; nid += blockDim.x) {
         const int jj = nid / NXN, ii = nid - jj * NXN;
         const int I = I0 + ii, J = J0 + jj;
@@ -1016,32 +1101,99 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
         T bu = T(0), bv = T(0);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            bu += cc[corner[t] * L::NCELL + cells[t]];
-            bv += cc[(4 + corner[t]) * L::NCELL + cells[t]];
+            bu += cc[L::ccx(corner[t], cells[t])];
+            bv += cc[L::ccx(4 + corner[t], cells[t])];
         }
-        if (fast) {
-            const T *pu = vs + jj * L::HX + ii + L::XO - 1;   // node (ii-1, jj-1)
-            const T *pv = pu + L::HY * L::HX;
-            T su[3], sv[3];
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy) {
-                su[dy] = sv[dy] = T(0);
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    su[dy] += fc.nB[dy][dx] * pu[dy * L::HX + dx];
-                    sv[dy] += fc.nB[dy][dx] * pv[dy * L::HX + dx];
-                }
-            }
-            bu += (su[0] + su[1]) + su[2];
-            bv += (sv[0] + sv[1]) + sv[2];
-        } else {
-            const NodeClass nc = classify(cf[cells[0]], cf[cells[1]], cf[cells[2]], cf[cells[3]], I, J, g.nyf);
-            if (nc.dirichlet) bu = bv = T(0);
-        }
+        const NodeClass nc = classify(cf[cells[0]], cf[cells[1]], cf[cells[2]], cf[cells[3]], I, J, g.nyf);
+        if (nc.dirichlet) bu = bv = T(0);
         const size_t node = (size_t)J * g.pitch + I;
         bf[node] = bu;
         bf[g.plane + node] = bv;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf) {
+    using L = RhsLayout;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *vs = reinterpret_cast<T *>(smem_raw);   // [2][HY][HX]
+    T *cc = vs + L::VS;                        // [8][NCP]
+    unsigned char *cf = reinterpret_cast<unsigned char *>(cc + L::CC);   // [CY][CX]
+    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    stage_window<T, 2, L::HY, L::HX>(g, vcorr, I0 - L::XO, J0 - L::YO, vs);
+    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 2);
+    if (!fast) {
+        for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
+            const int jj = idx / L::CX, ii = idx - jj * L::CX;
+            cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    rhs_tile(g, fc, vs, cc, cf, fast, I0, J0, bf);
+}
+
+// S5 + S6 fused for the correction step: the v_corr window of a right-hand
+// side tile (x~ = P x_c plus the patch mean of d, Dirichlet values at the
+// boundary) is formed in shared memory and never reaches HBM.  The coarse
+// window and the patch numbers live in the cell-contribution buffer until
+// the window is complete.  Same arithmetic as S5 followed by S6.
+template <typename T, int R>
+__global__ void __launch_bounds__(NTHREADS)
+k_avg_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ d, const double *__restrict__ xc, double inflow_peak,
+          T *__restrict__ bf) {
+    using L = RhsLayout;
+    using CWin = CoarseWin<T, R, L::HX, L::HY, 2>;
+    constexpr int MAXPID = ((L::HX + 3) / 2 + 2) * ((L::HY + 1) / 2 + 2);
+    static_assert(CWin::N * sizeof(T) + MAXPID * sizeof(int) <= L::CC * sizeof(T), "staging fits in cc");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *vs = reinterpret_cast<T *>(smem_raw);   // [2][HY][HX]
+    T *cc = vs + L::VS;                        // [8][NCP]; first the coarse window and the patch numbers
+    unsigned char *cf = reinterpret_cast<unsigned char *>(cc + L::CC);   // [CY][CX]
+    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    const int Ilo = I0 - L::XO, Jlo = J0 - L::YO;
+    CWin cw;
+    cw.cs = cc;
+    cw.stage(g, xc, Ilo, Jlo);
+    PatchWin pw;
+    pw.pid = reinterpret_cast<int *>(cc + CWin::N);
+    pw.stage(g, Ilo, Ilo + L::HX - 1, Jlo, Jlo + L::HY - 1);
+    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 2);
+    if (!fast) {
+        for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
+            const int jj = idx / L::CX, ii = idx - jj * L::CX;
+            cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
+        }
+    }
+    const double up = inflow_peak;
+    __syncthreads();
+    // a fixed trip count lets the loads of all rounds be in flight together
+#pragma unroll
+    for (int rnd = 0; rnd < (L::HP + NTHREADS - 1) / NTHREADS; ++rnd) {
+        const int e = threadIdx.x + rnd * NTHREADS;
+        if (e >= L::HP) break;
+        const int row = e / L::HX, col = e - row * L::HX;
+        const int I = Ilo + col, J = Jlo + row;
+        T u = T(0), v = T(0);
+        if (I >= 0 && J >= 0 && I <= g.nxf && J <= g.nyf) {
+            T x[2];
+            cw.interp(I, J, x);
+            u = x[0];
+            v = x[1];
+            T uD, vD;
+            if (!fast && dirichlet_value(g, I, J, up, uD, vD)) {
+                u = uD;
+                v = vD;
+            } else {
+                pw.add_mean(g, d, I, J, u, v);
+            }
+        }
+        vs[e] = u;
+        vs[L::HP + e] = v;
+    }
+    __syncthreads();
+    rhs_tile(g, fc, vs, cc, cf, fast, I0, J0, bf);
 }
 
 // ------------------------------------------------------------------ S7
@@ -1252,8 +1404,9 @@ void tile_flags(const MeshGeom &g, const uint8_t *solid, uint8_t *flags) {
         }
 }
 
-double inflow_ramp(const MeshGeom &g, double t) {
-    return g.ramp ? (t <= 0.5 ? 0.5 - 0.5 * cos(2.0 * 3.14159265358979323846 * t) : 1.0) : 1.0;
+// Peak inflow velocity at time t (u_max, ramped in over t <= 1/2 if requested).
+double inflow_peak(const MeshGeom &g, double t) {
+    return g.u_max * (g.ramp ? (t <= 0.5 ? 0.5 - 0.5 * cos(2.0 * 3.14159265358979323846 * t) : 1.0) : 1.0);
 }
 
 template <typename T>
@@ -1269,7 +1422,7 @@ cudaError_t run_prolongate(const MeshGeom &g, const double *xc, T *xf, double w,
 
 cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, void *xf, double t,
                               cudaStream_t st) {
-    const double w = inflow_ramp(g, t);
+    const double w = inflow_peak(g, t);
     if (prec == DNNMG_F64) return run_prolongate(g, xc, (double *)xf, w, st);
     return run_prolongate(g, xc, (float *)xf, w, st);
 }
@@ -1300,7 +1453,7 @@ cudaError_t run_residual_r(const MeshGeom &g, const FemCoef<T> &fc, const void *
 cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<double> &f64,
                                      const FemCoef<float> &f32, const void *xf, const double *xc, double t,
                                      const void *bf, void *rf, void *X, cudaStream_t st) {
-    const double w = inflow_ramp(g, t);
+    const double w = inflow_peak(g, t);
     if (prec == DNNMG_F64) return run_residual_r<double, double>(g, f64, xf, xc, w, bf, rf, X, st);
     if (prec == DNNMG_F32) return run_residual_r<float, float>(g, f32, xf, xc, w, bf, rf, X, st);
     return run_residual_r<float, __nv_bfloat16>(g, f32, xf, xc, w, bf, rf, X, st);
@@ -1324,7 +1477,7 @@ cudaError_t run_scatter(const MeshGeom &g, const T *d, const T *xf, const double
 
 cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf, const double *xc,
                                double t, void *vcorr, cudaStream_t st) {
-    const double w = inflow_ramp(g, t);
+    const double w = inflow_peak(g, t);
     if (prec == DNNMG_F64) return run_scatter(g, (const double *)d, (const double *)xf, xc, w, (double *)vcorr, st);
     return run_scatter(g, (const float *)d, (const float *)xf, xc, w, (float *)vcorr, st);
 }
@@ -1342,6 +1495,34 @@ cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
         k_rhs<float><<<tile_grid(g), NTHREADS, sm, st>>>(g, f32, (const float *)vcorr, (float *)bf);
     }
     return cudaGetLastError();
+}
+
+template <typename T, int R>
+cudaError_t run_avg_rhs(const MeshGeom &g, const FemCoef<T> &fc, const T *d, const double *xc, double up, T *bf,
+                        cudaStream_t st) {
+    const size_t sm = RhsLayout::bytes<T>();
+    cudaError_t e = set_smem(k_avg_rhs<T, R>, sm);
+    if (e != cudaSuccess) return e;
+    k_avg_rhs<T, R><<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, d, xc, up, bf);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_avg_rhs_r(const MeshGeom &g, const FemCoef<T> &fc, const T *d, const double *xc, double up, T *bf,
+                          cudaStream_t st) {
+    switch (g.r) {
+        case 2: return run_avg_rhs<T, 2>(g, fc, d, xc, up, bf, st);
+        case 4: return run_avg_rhs<T, 4>(g, fc, d, xc, up, bf, st);
+        case 8: return run_avg_rhs<T, 8>(g, fc, d, xc, up, bf, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_avg_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
+                           const void *d, const double *xc, double t, void *bf, cudaStream_t st) {
+    const double up = inflow_peak(g, t);
+    if (prec == DNNMG_F64) return run_avg_rhs_r(g, f64, (const double *)d, xc, up, (double *)bf, st);
+    return run_avg_rhs_r(g, f32, (const float *)d, xc, up, (float *)bf, st);
 }
 
 cudaError_t launch_restrict(const MeshGeom &g, int prec, const void *bf, double *bc,

@@ -78,6 +78,7 @@ def _load():
         "dnnmg_step_launches": [P, P],
         "dnnmg_restrict": [P, P, P, P],
         "dnnmg_rhs": [P, P, P, P],
+        "dnnmg_scatter_rhs": [P, P, P, D, P, P],
         "dnnmg_step_static": [P, P, P, P, P, P, D, P],
         "dnnmg_net_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_net_uses_tensor_cores": [P],
@@ -308,6 +309,15 @@ def dnnmg_rhs(mesh, vcorr, bf, stream=None):
     _need(vcorr, mesh.real, 2 * I.plane, "vcorr")
     _need(bf, mesh.real, 2 * I.plane, "bf")
     _check(_lib.dnnmg_rhs(mesh.handle, _ptr(vcorr), _ptr(bf), _stream(stream)))
+
+
+def dnnmg_scatter_rhs(mesh, d, xc, bf, t=0.0, stream=None):
+    """S5 + S6 fused: bf = Rhs(P xc + averaged d) without writing v_corr."""
+    I = mesh.info
+    _need(d, mesh.real, I.P * I.n_out, "d")
+    _need(xc, torch.float64, 3 * I.Nc, "xc")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
+    _check(_lib.dnnmg_scatter_rhs(mesh.handle, _ptr(d), _ptr(xc), float(t), _ptr(bf), _stream(stream)))
 
 
 def dnnmg_restrict(mesh, bf, bc, stream=None):

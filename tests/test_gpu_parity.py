@@ -376,6 +376,30 @@ def test_fused_prolongation_forms(dn, name):
     assert rel_l2(m.unpack(vc), average.scatter_average(om, d, xf_ref)) <= tol
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_scatter_rhs_fused_equals_two_passes(dn, name):
+    # S5+S6 in one kernel (v_corr kept on chip) gives the bits of S5 (with xc)
+    # followed by S6, and the oracle's Rhs of the averaged correction
+    case = CASES[name]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    t = 0.15
+    xc = coarse_input(case, t=t)
+    rng = np.random.default_rng(31)
+    d = cuda(as_real(case, rng.normal(0.0, 0.3, (om.P, om.n_out))), m.real)
+    xct = cuda(xc, torch.float64)
+    vc, b1, b2 = m.fine(2), m.fine(2), m.fine(2)
+    dn.dnnmg_scatter_avg(m, d, None, vc, xc=xct, t=t)
+    dn.dnnmg_rhs(m, vc, b1)
+    dn.dnnmg_scatter_rhs(m, d, xct, b2, t=t)
+    torch.cuda.synchronize()
+    assert np.array_equal(m.unpack(b1), m.unpack(b2))
+    vref = average.scatter_average(om, d.cpu().numpy().astype(np.float64), transfer.prolongate(om, PRM, xc, t))
+    ref = fem.rhs(om, PRM, vref)
+    tol = TOL["f64"] if case["prec"] == "f64" else TOL["f32"]
+    assert rel_l2(m.unpack(b2), ref) <= tol
+
+
 def test_rhs_alone_equals_rhs_of_rhs_restrict(dn):
     case = CASES["k2_f32"]
     m = gpu_mesh(dn, case)
