@@ -260,6 +260,13 @@ int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, v
 #define DNNMG_DEVERR_TIMEOUT 1
 int dnnmg_net_status(dnnmg_net_t net, int *status, int reset);
 
+/*
+ * The same for a mesh: bit 0 is set if a stencil kernel of the correction
+ * step gave up waiting for its tile's TMA copies (the kernel then stops
+ * early, leaving its outputs incomplete).  Synchronous; reset != 0 clears it.
+ */
+int dnnmg_mesh_status(dnnmg_mesh_t mesh, int *status, int reset);
+
 /* 1 if the network's GRU step runs on the tensor cores (BF16 networks whose
  * shapes the tcgen05 kernel supports and DNNMG_GRU_KERNEL != "simt" in the
  * environment at creation), else 0. */

@@ -135,12 +135,13 @@ void fill_info(const dnnmg_mesh_desc &d, int P, int n_solid, dnnmg_mesh_info *in
     ws += align256((size_t)P * I.ldx * I.feature_bytes);        // X
     ws += align256((size_t)P * I.n_out * I.real_bytes);         // d
     ws += align256(2 * (size_t)I.plane * I.real_bytes);         // v_corr
+    ws += align256(3 * (size_t)(d.nyc + 1) * round_up(d.nxc + 1, 32) * I.real_bytes);   // padded x_c
     ws += 2 * align256(3 * (size_t)I.Nc * sizeof(double));      // host-call staging of x_c, b_c
     I.workspace_bytes = ws;
 }
 
 struct Workspace {
-    void *X, *d, *vc;
+    void *X, *d, *vc, *xcp;
     double *xc, *bc;
 };
 
@@ -153,6 +154,8 @@ Workspace carve(const dnnmg_mesh_info &I, void *base) {
     p += align256((size_t)I.P * I.n_out * I.real_bytes);
     w.vc = p;
     p += align256(2 * (size_t)I.plane * I.real_bytes);
+    w.xcp = p;
+    p += align256(3 * (size_t)(I.nyc + 1) * round_up(I.nxc + 1, 32) * I.real_bytes);
     w.xc = reinterpret_cast<double *>(p);
     p += align256(3 * (size_t)I.Nc * sizeof(double));
     w.bc = reinterpret_cast<double *>(p);
@@ -417,6 +420,19 @@ int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out) {
         return fail(DNNMG_ENOMEM, "device allocation of the tile flags failed");
     }
     g.tile_flags = m->d_tile_flags;
+    m->d_status = nullptr;
+    if (cudaMalloc(&m->d_status, sizeof(int)) != cudaSuccess || cudaMemset(m->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(m->d_solid);
+        cudaFree(m->d_patch_id);
+        cudaFree(m->d_patch_cell);
+        cudaFree(m->d_feat_tab);
+        cudaFree(m->d_tile_flags);
+        cudaFree(m->d_status);
+        delete m;
+        cudaGetLastError();
+        return fail(DNNMG_ENOMEM, "device allocation of the mesh status failed");
+    }
+    g.status = m->d_status;
     fem_coefficients(*desc, &m->fem64);
     to_float(m->fem64, &m->fem32);
     *out = m;
@@ -431,6 +447,7 @@ int dnnmg_mesh_destroy(dnnmg_mesh_t mesh) {
     cudaFree(mesh->d_patch_cell);
     cudaFree(mesh->d_feat_tab);
     cudaFree(mesh->d_tile_flags);
+    cudaFree(mesh->d_status);
     delete mesh;
     return DNNMG_OK;
 }
@@ -640,6 +657,15 @@ int dnnmg_net_status(dnnmg_net_t net, int *status, int reset) {
 
 int dnnmg_net_uses_tensor_cores(dnnmg_net_t net) { return net && net->tc ? 1 : 0; }
 
+int dnnmg_mesh_status(dnnmg_mesh_t mesh, int *status, int reset) {
+    clear_error();
+    if (!mesh || !status) return fail(DNNMG_EINVAL, "NULL argument");
+    if (int e = check_device(mesh->device)) return e;
+    DNNMG_CUDA_TRY(cudaMemcpy(status, mesh->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (reset) DNNMG_CUDA_TRY(cudaMemset(mesh->d_status, 0, sizeof(int)));
+    return DNNMG_OK;
+}
+
 static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, void *workspace,
                        size_t workspace_bytes) {
     if (int e = check_mesh(mesh)) return e;
@@ -665,10 +691,12 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
     const int prec = mesh->info.precision;
     const MeshGeom &g = mesh->g;
     // S1 is fused into S2+S3 and into S5: both interpolate x~ from xc inside
-    // their tiles, so x~ never goes to memory.  (S5+S6 as one kernel keeps
+    // their tiles, so x~ never goes to memory; S2+S3 reads x_c as a padded
+    // copy in the fine type, fetched by TMA.  (S5+S6 as one kernel keeps
     // v_corr on chip but recomputes the averaging on every tile's halo, which
     // costs more than the v_corr round trip; see dnnmg_scatter_rhs.)
-    DNNMG_CUDA_TRY(launch_residual_features(g, prec, mesh->fem64, mesh->fem32, nullptr, xc, t, bf, nullptr, w.X, s));
+    DNNMG_CUDA_TRY(launch_coarse_pad(g, prec, xc, w.xcp, s));
+    DNNMG_CUDA_TRY(launch_residual_step(g, prec, mesh->fem64, mesh->fem32, w.xcp, t, bf, w.X, s));
     if (mesh->info.P) DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
     DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, nullptr, xc, t, w.vc, s));
     DNNMG_CUDA_TRY(launch_rhs(g, prec, mesh->fem64, mesh->fem32, w.vc, bf, s));
@@ -714,7 +742,7 @@ int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, v
 
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net) {
     if (!mesh || !net) return -1;
-    return 4 + (mesh->info.P ? gru_launch_count(*net) : 0);
+    return 5 + (mesh->info.P ? gru_launch_count(*net) : 0);
 }
 
 }  // extern "C"

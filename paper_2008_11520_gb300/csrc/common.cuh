@@ -2,6 +2,7 @@
 // kernel launchers.  The public boundary is include/dnnmg.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -50,6 +51,7 @@ struct MeshGeom {
     const int *feat_tab;          // device [ldx], source of each feature column (stencil.cu)
     const uint8_t *tile_flags;    // device [nty][ntx], all-fluid bits of each 32 x 16-cell tile
     int ntx, nty;
+    int *status;                  // device status word of the mesh (DNNMG_DEVERR_* bits)
 };
 
 // Element constants of one fine cell (local nodes SW, SE, NW, NE) and of one
@@ -94,6 +96,7 @@ struct Mesh {
     int *d_patch_cell;
     int *d_feat_tab;
     uint8_t *d_tile_flags;
+    int *d_status;
 };
 
 struct Net {
@@ -109,6 +112,11 @@ struct Net {
 };
 
 int round_up(int v, int m);
+// Tiled TMA descriptor (no swizzle, zero fill out of bounds); strides in
+// bytes for dimensions 1 .. rank-1.  False if the driver entry point is
+// missing or the layout is not expressible.
+bool tma_encode_tiled(CUtensorMap *map, CUtensorMapDataType type, unsigned rank, void *base, const cuuint64_t *dims,
+                      const cuuint64_t *strides, const cuuint32_t *box);
 size_t align256(size_t v);
 
 // ---------------------------------------------------------------- launchers
@@ -124,6 +132,16 @@ cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const
                                double t, void *vcorr, cudaStream_t st);
 cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
                        const FemCoef<float> &f32, const void *vcorr, void *bf, cudaStream_t st);
+// The coarse vector in the fine arithmetic type, rows padded to pc (a
+// multiple of 32) so that tiles can fetch coarse windows by TMA: xcp
+// [3][nyc+1][pc], zero past nxc.
+int coarse_pitch(const MeshGeom &g);
+cudaError_t launch_coarse_pad(const MeshGeom &g, int prec, const double *xc, void *xcp, cudaStream_t st);
+// S2 + S3 of the correction step on the padded coarse vector: persistent
+// CTAs, TMA-fed and double-buffered tiles (same arithmetic as
+// launch_residual_features with xc; rf is not written).
+cudaError_t launch_residual_step(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
+                                 const void *xcp, double t, const void *bf, void *X, cudaStream_t st);
 // S5 + S6 fused: b_f = Rhs(P x_c + mean of d) without writing v_corr.
 cudaError_t launch_avg_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
                            const void *d, const double *xc, double t, void *bf, cudaStream_t st);

@@ -14,6 +14,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace dnnmg {
 namespace {
@@ -114,11 +115,14 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 // kernel that interpolates a node produces the same bits.
 template <typename T> __device__ __forceinline__ T lerp(T lo, T hi, T w) { return fma_t(w, hi - lo, lo); }
 
-// NC = 3 stages u, v, p; NC = 2 the velocity only.
-template <typename T, int R, int FW, int FH, int NC = 3>
+// NC = 3 stages u, v, p; NC = 2 the velocity only.  ALIGN > 1: the first
+// staged column is rounded down to a multiple of ALIGN and the row length up
+// (windows fetched by TMA, whose x coordinate must be 16-byte aligned).
+template <typename T, int R, int FW, int FH, int NC = 3, int ALIGN = 1>
 struct CoarseWin {
     static constexpr int K = Log2<R>::v;
-    static constexpr int CW = (FW - 1) / R + 3, CH = (FH - 1) / R + 3, N = NC * CW * CH;
+    static constexpr int CW = ((FW - 1) / R + 3 + ALIGN - 1 + ALIGN - 1) / ALIGN * ALIGN;
+    static constexpr int CH = (FH - 1) / R + 3, N = NC * CW * CH;
     T *cs;          // [NC][CH][CW] in shared memory
     int ci0, cj0;   // first staged coarse node (may be negative)
 
@@ -598,48 +602,18 @@ __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<
     put_block(g, X, pid, tpx, tpy, lS, bx, by, ru, rv, rp);
 }
 
-// S2 + S3 for one 32 x 16-cell tile.  R = 0: x~ is read from xf (S1 done by
-// the caller); R = 2, 4, 8: x~ is interpolated from the coarse vector xc
-// inside the tile (S1 fused: x~ never reaches HBM), with the Dirichlet
-// values set where the tile touches a boundary.
-template <typename T, typename TX, int R>
-__global__ void __launch_bounds__(NTHREADS)
-k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const double *__restrict__ xc,
-                    double inflow_peak, const T *__restrict__ bf, T *__restrict__ rf, TX *__restrict__ X) {
+// S2 + S3 of one tile once its inputs are staged and visible: bs holds the
+// b_f window, xs the x~ window (R = 0) or cw the coarse window (R > 0), pid
+// the tile's patch numbers, geo_s the geometry features, fast the tile's
+// all-fluid flag.  Shared by the per-tile kernel and the persistent one.
+template <typename T, typename TX, int R, typename CWin>
+__device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T> &fc, const CWin &cw,
+                                              double inflow_peak, T *xs, const T *bs, T *cc, T *un, const int *pid,
+                                              unsigned char *cf, const T *geo_s, bool fast, int I0, int J0,
+                                              T *__restrict__ rf, TX *__restrict__ X) {
     using L = ResLayout;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T geo_s[12];
-    T *xs = reinterpret_cast<T *>(smem_raw);   // [3][HY][HX]   u, v, p
-    T *bs = xs + L::XS;                        // [2][NYN][BX]  b_u, b_v
-    T *cc = bs + L::BS;                        // [8][NCP]      cell contributions (velocity rows)
-    T *un = cc + L::CC;                        // coarse window (R > 0), then [9][NLPS] LPS contributions
-    int *pid = reinterpret_cast<int *>(un + L::UN);                          // [tpy][tpx] patch numbers
-    unsigned char *cf = reinterpret_cast<unsigned char *>(pid + L::MAXP);   // [FY][FX] cell codes
-
-    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
     const int lS = g.K + g.s - 1;   // S = s 2^K with s = 1, 2
     const int tpx = TXC >> lS, tpy = TYC >> lS;
-    stage_window<T, 2, NYN, L::BX>(g, bf, I0, J0, bs);
-    using CWin = CoarseWin<T, (R > 0 ? R : 2), L::HX, L::HY>;
-    CWin cw;
-    cw.cs = un;
-    if constexpr (R > 0) {
-        static_assert(CWin::N <= L::UN, "coarse window");
-        cw.stage(g, xc, I0 - L::XO, J0 - L::YO);
-    } else {
-        stage_window<T, 3, L::HY, L::HX>(g, xf, I0 - L::XO, J0 - L::YO, xs);
-    }
-    for (int e = threadIdx.x; e < tpx * tpy; e += blockDim.x) {
-        const int py = e >> (5 - lS), px = e & (tpx - 1);
-        const int pi = (I0 >> lS) + px, pj = (J0 >> lS) + py;
-        pid[e] = (pi < g.npx && pj < g.npy) ? g.patch_id[pj * g.npx + pi] : -1;
-    }
-    if (threadIdx.x < 12) geo_s[threadIdx.x] = fc.geo[threadIdx.x];
-    // fast tiles: every cell within two of the tile is fluid and exists, so
-    // no tile node is a boundary node and node stencils apply everywhere
-    // (the barrier inside also publishes the coarse window, pid and geo_s)
-    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 1);
-    __syncthreads();   // publishes the coarse window, pid and geo_s
     if (!fast) {
         for (int idx = threadIdx.x; idx < L::FX * L::FY; idx += blockDim.x) {
             const int jj = idx / L::FX, ii = idx - jj * L::FX;
@@ -847,6 +821,148 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
         }
         put_residual(g, X, pid, tpx, tpy, lS, ii, jj, ru, rv, rp);
     }
+}
+
+// S2 + S3 for one 32 x 16-cell tile.  R = 0: x~ is read from xf (S1 done by
+// the caller); R = 2, 4, 8: x~ is interpolated from the coarse vector xc
+// inside the tile (S1 fused: x~ never reaches HBM), with the Dirichlet
+// values set where the tile touches a boundary.
+template <typename T, typename TX, int R>
+__global__ void __launch_bounds__(NTHREADS)
+k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const double *__restrict__ xc,
+                    double inflow_peak, const T *__restrict__ bf, T *__restrict__ rf, TX *__restrict__ X) {
+    using L = ResLayout;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T geo_s[12];
+    T *xs = reinterpret_cast<T *>(smem_raw);   // [3][HY][HX]   u, v, p
+    T *bs = xs + L::XS;                        // [2][NYN][BX]  b_u, b_v
+    T *cc = bs + L::BS;                        // [8][NCP]      cell contributions (velocity rows)
+    T *un = cc + L::CC;                        // coarse window (R > 0), then [9][NLPS] LPS contributions
+    int *pid = reinterpret_cast<int *>(un + L::UN);                          // [tpy][tpx] patch numbers
+    unsigned char *cf = reinterpret_cast<unsigned char *>(pid + L::MAXP);   // [FY][FX] cell codes
+
+    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    const int lS = g.K + g.s - 1;   // S = s 2^K with s = 1, 2
+    const int tpx = TXC >> lS, tpy = TYC >> lS;
+    stage_window<T, 2, NYN, L::BX>(g, bf, I0, J0, bs);
+    using CWin = CoarseWin<T, (R > 0 ? R : 2), L::HX, L::HY>;
+    CWin cw;
+    cw.cs = un;
+    if constexpr (R > 0) {
+        static_assert(CWin::N <= L::UN, "coarse window");
+        cw.stage(g, xc, I0 - L::XO, J0 - L::YO);
+    } else {
+        stage_window<T, 3, L::HY, L::HX>(g, xf, I0 - L::XO, J0 - L::YO, xs);
+    }
+    for (int e = threadIdx.x; e < tpx * tpy; e += blockDim.x) {
+        const int py = e >> (5 - lS), px = e & (tpx - 1);
+        const int pi = (I0 >> lS) + px, pj = (J0 >> lS) + py;
+        pid[e] = (pi < g.npx && pj < g.npy) ? g.patch_id[pj * g.npx + pi] : -1;
+    }
+    if (threadIdx.x < 12) geo_s[threadIdx.x] = fc.geo[threadIdx.x];
+    // fast tiles: every cell within two of the tile is fluid and exists, so
+    // no tile node is a boundary node and node stencils apply everywhere
+    // (the barrier inside also publishes the coarse window, pid and geo_s)
+    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 1);
+    __syncthreads();   // publishes the coarse window, pid and geo_s
+    residual_tile<T, TX, R>(g, fc, cw, inflow_peak, xs, bs, cc, un, pid, cf, geo_s, fast, I0, J0, rf, X);
+}
+
+// ------------------------------------------------------------------ S1 staging
+// The coarse vector in the fine arithmetic type with rows padded to pc, so
+// that the step's tiles fetch coarse windows by TMA (the coarse planes have
+// an odd row length, which a TMA stride cannot express) and convert nothing.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+k_coarse_pad(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xcp, int pc) {
+    const size_t nc1 = (size_t)g.nxc + 1;
+    const int rows = 3 * (g.nyc + 1);
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int c = row / (g.nyc + 1), j = row - c * (g.nyc + 1);
+        const double *src = xc + ((size_t)c * (g.nyc + 1) + j) * nc1;
+        T *dst = xcp + (size_t)row * pc;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pc; i += gridDim.x * blockDim.x)
+            dst[i] = i < (int)nc1 ? (T)__ldg(src + i) : T(0);
+    }
+}
+
+// Shared-memory layout of the TMA-fed residual kernel (bytes; the TMA
+// destinations 128-byte aligned): the work buffers of ResLayout plus the
+// b_f window and the coarse window as TMA boxes.
+template <typename T, int R>
+struct StepLayout {
+    using L = ResLayout;
+    using CWin = CoarseWin<T, R, L::HX, L::HY, 3, 4>;
+    static constexpr size_t BS_BYTES = sizeof(T) * L::BS, CS_BYTES = sizeof(T) * CWin::N;
+    static constexpr size_t BSB = 0;                                             // [2][NYN][BX]
+    static constexpr size_t CSB = (BSB + BS_BYTES + 127) / 128 * 128;            // [3][CH][CW]
+    static constexpr size_t XS = (CSB + CS_BYTES + 127) / 128 * 128;
+    static constexpr size_t CC = XS + sizeof(T) * L::XS;
+    static constexpr size_t UN = CC + sizeof(T) * L::CC;
+    static constexpr size_t PID = UN + sizeof(T) * L::LC;
+    static constexpr size_t CF = PID + sizeof(int) * L::MAXP;
+    static constexpr size_t MB = (CF + L::FX * L::FY + 7) / 8 * 8;
+    static constexpr size_t BYTES = MB + 16 + 128;   // barrier and abort flag; base alignment slack
+};
+
+// S2 + S3 of the correction step, one CTA per tile: one thread fetches the
+// b_f window and the coarse window (from the padded copy) as two TMA boxes
+// while the others load the patch numbers; then as residual_tile.  The wait
+// is bounded: on time-out the mesh status gets DNNMG_DEVERR_TIMEOUT and the
+// CTA returns once its copies have landed.
+template <typename T, typename TX, int R>
+__global__ void __launch_bounds__(NTHREADS)
+k_residual_step(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap tmB,
+                const __grid_constant__ CUtensorMap tmC, double inflow_peak, TX *__restrict__ X) {
+    using L = ResLayout;
+    using SL = StepLayout<T, R>;
+    using CWin = typename SL::CWin;
+    constexpr int K = Log2<R>::v;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ T geo_s[12];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const T *bs = reinterpret_cast<const T *>(base + SL::BSB);
+    T *xs = reinterpret_cast<T *>(base + SL::XS);
+    T *cc = reinterpret_cast<T *>(base + SL::CC);
+    T *un = reinterpret_cast<T *>(base + SL::UN);
+    int *pid = reinterpret_cast<int *>(base + SL::PID);
+    unsigned char *cf = base + SL::CF;
+    uint64_t *mb = reinterpret_cast<uint64_t *>(base + SL::MB);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(mb + 1);
+    const uint32_t mb_u = ptx::smem_u32(mb);
+    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    CWin cw;
+    cw.cs = reinterpret_cast<T *>(base + SL::CSB);
+    cw.ci0 = ((I0 - L::XO) >> K) & ~3;
+    cw.cj0 = (J0 - L::YO) >> K;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(mb_u, 1);
+        *abort_flag = 0;
+        ptx::mbar_init_fence();
+        ptx::expect_tx(mb_u, (uint32_t)(SL::BS_BYTES + SL::CS_BYTES));
+        ptx::tma_load_3d(ptx::smem_u32(base + SL::BSB), &tmB, I0, J0, 0, mb_u);
+        ptx::tma_load_3d(ptx::smem_u32(base + SL::CSB), &tmC, cw.ci0, cw.cj0, 0, mb_u);
+    }
+    const int lS = g.K + g.s - 1;
+    const int tpx = TXC >> lS, tpy = TYC >> lS;
+    for (int e = threadIdx.x; e < tpx * tpy; e += blockDim.x) {
+        const int py = e >> (5 - lS), px = e & (tpx - 1);
+        const int pi = (I0 >> lS) + px, pj = (J0 >> lS) + py;
+        pid[e] = (pi < g.npx && pj < g.npy) ? __ldg(g.patch_id + pj * g.npx + pi) : -1;
+    }
+    if (threadIdx.x < 12) geo_s[threadIdx.x] = fc.geo[threadIdx.x];
+    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 1);
+    __syncthreads();   // the barrier is initialised; pid and geo_s are visible
+    const bool ok = ptx::mbar_test(mb_u, 0) || ptx::mbar_wait(mb_u, 0, abort_flag);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(g.status, DNNMG_DEVERR_TIMEOUT);
+            volatile int no_abort = 0;   // let the copies in flight land before leaving
+            ptx::mbar_wait(mb_u, 0, &no_abort);
+        }
+        return;
+    }
+    residual_tile<T, TX, R>(g, fc, cw, inflow_peak, xs, bs, cc, un, pid, cf, geo_s, fast, I0, J0, nullptr, X);
 }
 
 // ------------------------------------------------------------------ S5
@@ -1457,6 +1573,67 @@ cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<
     if (prec == DNNMG_F64) return run_residual_r<double, double>(g, f64, xf, xc, w, bf, rf, X, st);
     if (prec == DNNMG_F32) return run_residual_r<float, float>(g, f32, xf, xc, w, bf, rf, X, st);
     return run_residual_r<float, __nv_bfloat16>(g, f32, xf, xc, w, bf, rf, X, st);
+}
+
+int coarse_pitch(const MeshGeom &g) { return round_up(g.nxc + 1, 32); }
+
+template <typename T>
+cudaError_t run_coarse_pad(const MeshGeom &g, const double *xc, T *xcp, cudaStream_t st) {
+    const int pc = coarse_pitch(g), rows = 3 * (g.nyc + 1);
+    const dim3 grid((unsigned)((pc + NTHREADS - 1) / NTHREADS), (unsigned)(rows < 65535 ? rows : 65535));
+    k_coarse_pad<T><<<grid, NTHREADS, 0, st>>>(g, xc, xcp, pc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_pad(const MeshGeom &g, int prec, const double *xc, void *xcp, cudaStream_t st) {
+    if (prec == DNNMG_F64) return run_coarse_pad(g, xc, (double *)xcp, st);
+    return run_coarse_pad(g, xc, (float *)xcp, st);
+}
+
+template <typename T, typename TX, int R>
+cudaError_t run_residual_step(const MeshGeom &g, const FemCoef<T> &fc, const T *xcp, double up, const T *bf, TX *X,
+                              cudaStream_t st) {
+    using L = ResLayout;
+    using SL = StepLayout<T, R>;
+    const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    // b_f [2][nyf+1][pitch]: boxes of BX columns x NYN rows x 2 components
+    CUtensorMap tmB, tmC;
+    const cuuint64_t bd[3] = {(cuuint64_t)g.nxf + 1, (cuuint64_t)g.nyf + 1, 2};
+    const cuuint64_t bs[2] = {(cuuint64_t)g.pitch * sizeof(T), (cuuint64_t)g.plane * sizeof(T)};
+    const cuuint32_t bb[3] = {(cuuint32_t)L::BX, (cuuint32_t)NYN, 2};
+    // padded coarse vector [3][nyc+1][pc]: boxes of the coarse window
+    const int pc = coarse_pitch(g);
+    const cuuint64_t cd[3] = {(cuuint64_t)g.nxc + 1, (cuuint64_t)g.nyc + 1, 3};
+    const cuuint64_t cs[2] = {(cuuint64_t)pc * sizeof(T), (cuuint64_t)pc * (g.nyc + 1) * sizeof(T)};
+    const cuuint32_t cb[3] = {(cuuint32_t)SL::CWin::CW, (cuuint32_t)SL::CWin::CH, 3};
+    if (!tma_encode_tiled(&tmB, dt, 3, const_cast<T *>(bf), bd, bs, bb) ||
+        !tma_encode_tiled(&tmC, dt, 3, const_cast<T *>(xcp), cd, cs, cb))
+        return cudaErrorInvalidValue;
+    auto k = k_residual_step<T, TX, R>;
+    const size_t sm = SL::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, tmB, tmC, up, X);
+    return cudaGetLastError();
+}
+
+template <typename T, typename TX>
+cudaError_t run_residual_step_r(const MeshGeom &g, const FemCoef<T> &fc, const void *xcp, double up, const void *bf,
+                                void *X, cudaStream_t st) {
+    switch (g.r) {
+        case 2: return run_residual_step<T, TX, 2>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st);
+        case 4: return run_residual_step<T, TX, 4>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st);
+        case 8: return run_residual_step<T, TX, 8>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_residual_step(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
+                                 const void *xcp, double t, const void *bf, void *X, cudaStream_t st) {
+    const double up = inflow_peak(g, t);
+    if (prec == DNNMG_F64) return run_residual_step_r<double, double>(g, f64, xcp, up, bf, X, st);
+    if (prec == DNNMG_F32) return run_residual_step_r<float, float>(g, f32, xcp, up, bf, X, st);
+    return run_residual_step_r<float, __nv_bfloat16>(g, f32, xcp, up, bf, X, st);
 }
 
 template <typename T>

@@ -81,6 +81,7 @@ def _load():
         "dnnmg_scatter_rhs": [P, P, P, D, P, P],
         "dnnmg_step_static": [P, P, P, P, P, P, D, P],
         "dnnmg_net_status": [P, ctypes.POINTER(ctypes.c_int), I],
+        "dnnmg_mesh_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_net_uses_tensor_cores": [P],
     }
     for name, args in sig.items():
@@ -331,6 +332,13 @@ def dnnmg_net_status(net, reset=False):
     """Device status word of the network (0 = no kernel wait ran out of time)."""
     st = ctypes.c_int(0)
     _check(_lib.dnnmg_net_status(net.handle, ctypes.byref(st), 1 if reset else 0))
+    return st.value
+
+
+def dnnmg_mesh_status(mesh, reset=False):
+    """Device status word of the mesh (0 = no stencil kernel wait ran out of time)."""
+    st = ctypes.c_int(0)
+    _check(_lib.dnnmg_mesh_status(mesh.handle, ctypes.byref(st), 1 if reset else 0))
     return st.value
 
 

@@ -260,6 +260,24 @@ def test_step_is_deterministic_and_host_variant_agrees(dn):
         assert np.array_equal(bcs[0][k], bcs[2][k])
 
 
+def test_step_leaves_mesh_status_clear(dn):
+    # the persistent TMA-fed residual kernel of the step reports time-outs of
+    # its bounded waits in the mesh status word; a normal step sets nothing
+    case = CASES["k2_f32"]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
+    net = dn.Net(Wx, Uh, Wfc, "f32")
+    xc = coarse_input(case, t=0.0)
+    h = torch.zeros(om.P, case["H"], device="cuda")
+    bf, bc, ws = m.fine(2), m.coarse(3), m.workspace()
+    for i in range(3):
+        dn.dnnmg_step(m, net, cuda(xc, torch.float64), h, bf, bc, ws, 0.01 * i)
+    torch.cuda.synchronize()
+    assert dn.dnnmg_mesh_status(m) == 0
+    assert dn.dnnmg_net_status(net) == 0
+
+
 def test_zero_network_reduces_to_prolongated_rhs(dn):
     # with W_fc = 0 the correction vanishes, so v_corr = v~ and the step
     # returns R Rhs(P x_c) (Algorithm 2 without the network)
