@@ -121,7 +121,9 @@ def algorithmic_work(info, H):
     rb, fb = info.real_bytes, info.feature_bytes
     # S1 is fused: S2+S3 and S5 read the coarse vector instead of x~
     return {
-        "residual_features": {"bytes": 3 * Nc * 8 + 2 * Nf * rb + P * ldx * fb},
+        # S1 staging: x_c (FP64) once into the padded fine-type copy the residual tiles fetch
+        "coarse_pad": {"bytes": 3 * Nc * 8 + 3 * Nc * rb},
+        "residual_features": {"bytes": 3 * Nc * rb + 2 * Nf * rb + P * ldx * fb},
         "gru": {"bytes": P * ldx * fb + 2 * P * H * rb + P * n_out * rb,
                 "flops": 2 * P * (3 * H * (n_in + H) + H * n_out)},
         "scatter_avg": {"bytes": P * n_out * rb + 3 * Nc * 8 + 2 * Nf * rb},
@@ -179,30 +181,15 @@ def run_ours(args, rank, world, local_rank):
     total_ms = ev[0].elapsed_time(ev[-1])
     clocks = clk.summary()
 
-    # ---- stage timing: the same kernels called stage by stage with events between them
+    # ---- stage timing: the step's own kernels, with events recorded between
+    # them by dnnmg_step_timed on the launching stream
     wsv = torch.empty(0)
-    xf = mesh.fine(3, dev)
-    X = torch.empty(I.P, I.ldx, dtype=torch.bfloat16, device=dev)
-    d = torch.empty(I.P, I.n_out, dtype=torch.float32, device=dev)
-    bf2 = mesh.fine(2, dev)
-    vc = mesh.fine(2, dev)
-    # the kernels dnnmg_step runs, in its order (S1 fused into S2+S3 and S5)
-    names = ["residual_features", "gru", "scatter_avg", "rhs", "restrict"]
+    names = ["coarse_pad", "residual_features"] + (["gru"] if I.P else []) + ["scatter_avg", "rhs", "restrict"]
+    assert len(names) == dnnmg.dnnmg_step_launches(mesh, net)
     sev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
     torch.cuda.synchronize()
     for i in range(args.steps):
-        e = sev[i]
-        e[0].record(stream)
-        dnnmg.dnnmg_patch_features(mesh, None, bf, X, xc=xc, t=0.0)
-        e[1].record(stream)
-        dnnmg.dnnmg_gru_step(net, X, h, d, I.P)
-        e[2].record(stream)
-        dnnmg.dnnmg_scatter_avg(mesh, d, None, vc, xc=xc, t=0.0)
-        e[3].record(stream)
-        dnnmg.dnnmg_rhs(mesh, vc, bf2)
-        e[4].record(stream)
-        dnnmg.dnnmg_restrict(mesh, bf2, bc)
-        e[5].record(stream)
+        dnnmg.dnnmg_step_timed(mesh, net, xc, h, bf, bc, ws, (args.warmup + args.steps + i) * k, sev[i])
     torch.cuda.synchronize()
     stage_ms = {n: statistics.mean(sev[i][j].elapsed_time(sev[i][j + 1]) for i in range(args.steps))
                 for j, n in enumerate(names)}

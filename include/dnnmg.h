@@ -300,6 +300,19 @@ size_t dnnmg_static_scratch_bytes(void);
 /* Number of kernel launches one dnnmg_step enqueues for this mesh/net. */
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net);
 
+/*
+ * dnnmg_step that also records events[0] before its first kernel and
+ * events[i+1] after kernel i, so the caller can time every kernel of the
+ * step (cudaEventElapsedTime).  No counterpart in the paper: an
+ * instrumentation form of dnnmg_step.
+ *   events: n_events = dnnmg_step_launches() + 1 caller-created events.
+ * The kernels, in order: coarse padding (S1 staging), S2+S3, S4 (when the
+ * mesh has fluid patches), S5, S6, S7.
+ */
+int dnnmg_step_timed(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
+                     void *workspace, size_t workspace_bytes, double t, cudaEvent_t *events, int n_events,
+                     cudaStream_t stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char *dnnmg_last_error(void);
 

@@ -686,21 +686,34 @@ static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, vo
     return DNNMG_OK;
 }
 
+// ev (may be null): dnnmg_step_launches() + 1 events, recorded before the
+// first kernel and after each kernel.
 static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf,
-                     double *bc, const Workspace &w, double t, cudaStream_t s) {
+                     double *bc, const Workspace &w, double t, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     const int prec = mesh->info.precision;
     const MeshGeom &g = mesh->g;
+    int nev = 0;
+    auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[nev++], s) : cudaSuccess; };
+    DNNMG_CUDA_TRY(mark());
     // S1 is fused into S2+S3 and into S5: both interpolate x~ from xc inside
     // their tiles, so x~ never goes to memory; S2+S3 reads x_c as a padded
     // copy in the fine type, fetched by TMA.  (S5+S6 as one kernel keeps
     // v_corr on chip but recomputes the averaging on every tile's halo, which
     // costs more than the v_corr round trip; see dnnmg_scatter_rhs.)
     DNNMG_CUDA_TRY(launch_coarse_pad(g, prec, xc, w.xcp, s));
+    DNNMG_CUDA_TRY(mark());
     DNNMG_CUDA_TRY(launch_residual_step(g, prec, mesh->fem64, mesh->fem32, w.xcp, t, bf, w.X, s));
-    if (mesh->info.P) DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
+    DNNMG_CUDA_TRY(mark());
+    if (mesh->info.P) {
+        DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
+        DNNMG_CUDA_TRY(mark());
+    }
     DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, nullptr, xc, t, w.vc, s));
+    DNNMG_CUDA_TRY(mark());
     DNNMG_CUDA_TRY(launch_rhs(g, prec, mesh->fem64, mesh->fem32, w.vc, bf, s));
+    DNNMG_CUDA_TRY(mark());
     DNNMG_CUDA_TRY(launch_restrict(g, prec, bf, bc, s));
+    DNNMG_CUDA_TRY(mark());
     return DNNMG_OK;
 }
 
@@ -738,6 +751,17 @@ int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, v
     if (int e = step_body(mesh, net, w.xc, h, bf, w.bc, w, t, stream)) return e;
     DNNMG_CUDA_TRY(cudaMemcpyAsync(bc_host, w.bc, nbytes, cudaMemcpyDeviceToHost, stream));
     return DNNMG_OK;
+}
+
+int dnnmg_step_timed(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
+                     void *workspace, size_t workspace_bytes, double t, cudaEvent_t *events, int n_events,
+                     cudaStream_t stream) {
+    clear_error();
+    if (int e = step_checks(mesh, net, h, bf, workspace, workspace_bytes)) return e;
+    if (!xc || !bc || !events) return fail(DNNMG_EINVAL, "NULL array");
+    if (n_events != dnnmg_step_launches(mesh, net) + 1)
+        return fail(DNNMG_EINVAL, "%d events given, the step needs %d", n_events, dnnmg_step_launches(mesh, net) + 1);
+    return step_body(mesh, net, xc, h, bf, bc, carve(mesh->info, workspace), t, stream, events);
 }
 
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net) {

@@ -44,26 +44,29 @@ namespace {
 constexpr int TM = 128;                 // patch rows per tile (UMMA M)
 constexpr int NTH = 320;                // producer warp, MMA warp, 8 epilogue warps
 constexpr int KC = 64;                  // K elements per chunk = one 128-byte swizzle row
-constexpr int CHUNK = TM * KC * 2;      // 16 KB: one A chunk, and the largest weight chunk
-constexpr int NSTAGE = 6;
+constexpr int CHUNK = TM * KC * 2;      // 16 KB: one A chunk (128 rows x 64 K)
+constexpr int SSZ = 2 * CHUNK;          // 32 KB weight-ring stage: up to 256 B rows x 64 K, or two K chunks
+constexpr int NSTAGE = 3;
 constexpr int MAX_ITEMS = 48;
 
 enum { ITEM_D1 = 0, ITEM_D2X = 1, ITEM_D2H = 2, ITEM_D3 = 3 };
 
-// One weight chunk of the schedule, as the MMA and producer threads read it
-// (one 16-byte shared-memory load per chunk):
-//   x: byte offset of the chunk in the weight blob
-//   y: byte offset of the A operand chunk from the shared-memory base
-//   z: instruction descriptor (M = 128, N = rows)
-//   w: first TMEM column (bits 0-8) | accumulate (bit 9) | first h chunk of
-//      phase 1 (bit 10) | rows of B = MMA N (bits 16-31)
-constexpr uint32_t SCHED_ACC = 1u << 9, SCHED_FIRST_H = 1u << 10;
+// One ring-stage fill of the schedule, as the MMA and producer threads read
+// it (two 16-byte shared-memory loads): one or two K chunks of 64 of the
+// same B rows (one accumulator block), stored one after the other.
+//   first word  x: byte offset in the weight blob, y: bytes, z: instruction
+//               descriptor (M = 128, N = rows), w: first TMEM column (bits
+//               0-8) | accumulate (bit 9) | first h chunk of phase 1 (bit 10)
+//               | two K chunks (bit 11) | rows = MMA N (bits 16-31)
+//   second word x, y: byte offsets of the A chunks from the shared-memory
+//               base, z: offset of the second B chunk in the stage
+constexpr uint32_t SCHED_ACC = 1u << 9, SCHED_FIRST_H = 1u << 10, SCHED_PAIR = 1u << 11;
 
 struct TcParams {
     int n_in, ldx, H, n_out, nfc, nxc, nhc, nxs, nitems, end1, end2, tmem_cols;
     const uint8_t *wblob;
     int *status;
-    uint4 items[MAX_ITEMS];
+    uint4 items[2 * MAX_ITEMS];
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -146,11 +149,11 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
     uint8_t *sX = base;                                   // max(nxc, H/32) chunks
     uint8_t *sAh = sX + p.nxs * CHUNK;                    // nhc chunks
     uint8_t *sW = sAh + p.nhc * CHUNK;                    // NSTAGE stages
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sW + NSTAGE * CHUNK);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sW + NSTAGE * SSZ);
     // barriers: full[NSTAGE], empty[NSTAGE], x_full, ah, d1, rh, d2, hn, d3, drain, h_full
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 9);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    uint4 *sched = reinterpret_cast<uint4 *>(bars + 2 * NSTAGE + 12);   // [nitems], 16-byte aligned
+    uint4 *sched = reinterpret_cast<uint4 *>(bars + 2 * NSTAGE + 12);   // [2 nitems], 16-byte aligned
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p0 = blockIdx.x * TM;
@@ -159,8 +162,9 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
     const uint32_t x_full = smem_u32(bars + 2 * NSTAGE), ah_bar = x_full + 8, d1_bar = x_full + 16,
                    rh_bar = x_full + 24, d2_bar = x_full + 32, hn_bar = x_full + 40, d3_bar = x_full + 48,
                    drain_bar = x_full + 56, h_full = x_full + 64;
-    constexpr int HB = H / 32;                 // 32-column boxes of the FP32 state
-    uint8_t *sH = sW + (NSTAGE - HB) * CHUNK;  // the state arrives in the last HB ring stages
+    constexpr int HB = H / 32;                 // 32-column boxes (16 KB) of the FP32 state
+    uint8_t *sH = sW + NSTAGE * SSZ - HB * CHUNK;   // the state arrives at the end of the ring
+    constexpr int HSTAGE = (NSTAGE * SSZ - HB * CHUNK) / SSZ;   // first ring stage it overlaps
     constexpr int NEPI = NTH - 64;   // epilogue threads
 
     if (tid == 0) {
@@ -182,7 +186,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         fence_async_smem();
     }
     if (warp == 2)
-        for (int i = lane; i < p.nitems; i += 32) sched[i] = p.items[i];
+        for (int i = lane; i < 2 * p.nitems; i += 32) sched[i] = p.items[i];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(p.tmem_cols)
@@ -206,14 +210,13 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
             int issued = 0;
             uint32_t s = 0, ph = 1;   // ring stage and the parity of its previous release
             for (int i = 0; i < p.nitems; ++i) {
-                // the last HB stages hold the state until the epilogue has read it
-                if (i == NSTAGE - HB && !mbar_wait(ah_bar, 0, abort_flag)) break;
+                // the stages under the state wait until the epilogue has read it
+                if (i == HSTAGE && !mbar_wait(ah_bar, 0, abort_flag)) break;
                 const uint32_t eb = empty0 + 8 * s;
                 if (i >= NSTAGE && !mbar_test(eb, ph) && !mbar_wait(eb, ph, abort_flag)) break;
-                const uint4 it = sched[i];
-                const uint32_t bytes = (it.w >> 16) * 128;
-                expect_tx(full0 + 8 * s, bytes);
-                bulk_load(sW_u + s * CHUNK, p.wblob + it.x, bytes, full0 + 8 * s);
+                const uint4 it = sched[2 * i];
+                expect_tx(full0 + 8 * s, it.y);
+                bulk_load(sW_u + s * SSZ, p.wblob + it.x, it.y, full0 + 8 * s);
                 issued = i + 1;
                 if (++s == NSTAGE) {
                     s = 0;
@@ -237,7 +240,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
             uint32_t s = 0, ph = 0;   // ring stage and the parity of its current fill
             const uint32_t base_u = smem_u32(base);
             for (int i = 0; ok && i < p.nitems; ++i) {
-                const uint4 it = sched[i];
+                const uint4 it = sched[2 * i], it2 = sched[2 * i + 1];
                 if (i == p.end1) ok = mbar_wait(rh_bar, 0, abort_flag);
                 if (ok && i == p.end2) ok = mbar_wait(hn_bar, 0, abort_flag);
                 if (ok && (it.w & SCHED_FIRST_H)) ok = mbar_wait(ah_bar, 0, abort_flag);
@@ -246,11 +249,18 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
                 if (!ok) break;
                 tc_after_sync();
                 // K steps of 16 elements advance both start addresses by 32 bytes (2 descriptor units)
-                const uint64_t ad = sdesc(base_u + it.y), bd = sdesc(sW_u + s * CHUNK);
                 const uint32_t dt = tmem + (it.w & 0x1FFu);
-                umma(dt, ad, bd, it.z, (it.w & SCHED_ACC) ? 1u : 0u);
+                {
+                    const uint64_t ad = sdesc(base_u + it2.x), bd = sdesc(sW_u + s * SSZ);
+                    umma(dt, ad, bd, it.z, (it.w & SCHED_ACC) ? 1u : 0u);
 #pragma unroll
-                for (int k = 1; k < KC / 16; ++k) umma(dt, ad + 2 * k, bd + 2 * k, it.z, 1u);
+                    for (int k = 1; k < KC / 16; ++k) umma(dt, ad + 2 * k, bd + 2 * k, it.z, 1u);
+                }
+                if (it.w & SCHED_PAIR) {   // the second K chunk adds onto the first
+                    const uint64_t ad = sdesc(base_u + it2.y), bd = sdesc(sW_u + s * SSZ + it2.z);
+#pragma unroll
+                    for (int k = 0; k < KC / 16; ++k) umma(dt, ad + 2 * k, bd + 2 * k, it.z, 1u);
+                }
                 tc_commit(empty0 + 8 * s);
                 if (++s == NSTAGE) {
                     s = 0;
@@ -397,7 +407,7 @@ inline size_t swz_host(int row, int k) {
 
 size_t smem_bytes(const TcParams &p) {
     // operand chunks, ring, alignment slack, barriers and flags (256 B), schedule
-    return (size_t)(p.nxs + p.nhc + NSTAGE) * CHUNK + 1024 + 256 + MAX_ITEMS * sizeof(uint4);
+    return (size_t)(p.nxs + p.nhc) * CHUNK + (size_t)NSTAGE * SSZ + 1024 + 256 + 2 * MAX_ITEMS * sizeof(uint4);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -435,79 +445,76 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
     const int nfc = round_up(n_out, 16);
     const int nxc = (ldx + KC - 1) / KC, nhc = (H + KC - 1) / KC;
     if (!(H == 32 || H == 64 || H == 96 || H == 128) || nfc > 2 * H) return false;
-    if ((size_t)TM * n_out * 4 > (size_t)NSTAGE * CHUNK || n_out % 2) return false;   // d staging in the ring
+    if ((size_t)TM * n_out * 4 > (size_t)NSTAGE * SSZ || n_out % 2) return false;   // d staging in the ring
     if (!encode_fn()) return false;
     TcParams p;
     memset(&p, 0, sizeof p);
     p.n_in = n_in; p.ldx = ldx; p.H = H; p.n_out = n_out; p.nfc = nfc; p.nxc = nxc; p.nhc = nhc;
     p.nxs = nxc > H / 32 ? nxc : H / 32;
+    // a ring-stage fill: K chunks kc0 (and kc0 + 1 if pair) of rows [r0, r0 + rows)
+    // of one B matrix, accumulating into TMEM columns dcol ..
     struct HostItem {
-        int off, rows, kind, kc, dcol;
+        int off, bytes, rows, kind, kc0, pair, dcol;
     };
     std::vector<HostItem> items;
     std::vector<uint8_t> blob;
-    // one chunk: rows [r0, r0 + rows) of a B matrix, K columns kc*64 .. kc*64+63
-    auto add = [&](int kind, int kc, int r0, int rows, int dcol, auto value) {
-        HostItem it;
-        it.off = (int)blob.size();
-        it.rows = rows;
-        it.kind = kind;
-        it.kc = kc;
-        it.dcol = dcol;
-        blob.resize(blob.size() + (size_t)rows * 128, 0);
-        uint8_t *dst = blob.data() + it.off;
-        for (int r = 0; r < rows; ++r)
-            for (int k = 0; k < KC; ++k) {
-                const __nv_bfloat16 b = __float2bfloat16_rn((float)value(r0 + r, k));
-                memcpy(dst + swz_host(r, k), &b, 2);
-            }
+    auto add = [&](int kind, int kc0, bool pair, int r0, int rows, int dcol, auto value) {
+        HostItem it{(int)blob.size(), 0, rows, kind, kc0, pair ? 1 : 0, dcol};
+        for (int q = 0; q <= it.pair; ++q) {
+            const size_t off = blob.size();
+            blob.resize(off + (size_t)rows * 128, 0);
+            for (int r = 0; r < rows; ++r)
+                for (int k = 0; k < KC; ++k) {
+                    const __nv_bfloat16 b = __float2bfloat16_rn((float)value(kc0 + q, r0 + r, k));
+                    memcpy(blob.data() + off + swz_host(r, k), &b, 2);
+                }
+        }
+        it.bytes = (int)blob.size() - it.off;
         items.push_back(it);
     };
-    auto blocks = [](int total, auto fn) {   // row blocks of at most 128 rows
-        for (int r0 = 0; r0 < total; r0 += 128) fn(r0, total - r0 < 128 ? total - r0 : 128);
+    const bool pair_h = 2 * H * 128 <= SSZ, pair_fc = 2 * nfc * 128 <= SSZ, pair_zr = 2 * (2 * H) * 128 <= SSZ;
+    auto wx = [&](int kc, int r, int k) -> double {   // W_x row r (z, r, candidate blocks), K chunk kc
+        const int col = kc * KC + k;
+        return col < n_in ? Wx[(size_t)r * n_in + col] : 0.0;
     };
-    // phase 1: X chunks (z, r and W_h rows), then h chunks (z and r rows only)
-    for (int kc = 0; kc < nxc + nhc; ++kc) {
-        blocks(2 * H, [&](int r0, int rows) {
-            add(ITEM_D1, kc, r0, rows, r0, [&](int r, int k) -> double {
-                if (kc < nxc) {
-                    const int col = kc * KC + k;
-                    return col < n_in ? Wx[(size_t)r * n_in + col] : 0.0;
-                }
-                const int col = (kc - nxc) * KC + k;
-                return col < H ? Uh[(size_t)r * H + col] : 0.0;
-            });
-        });
-        if (kc < nxc)
-            blocks(H, [&](int r0, int rows) {
-                add(ITEM_D2X, kc, r0, rows, 2 * H + r0, [&](int r, int k) -> double {
-                    const int col = kc * KC + k;
-                    return col < n_in ? Wx[(size_t)(2 * H + r) * n_in + col] : 0.0;
-                });
-            });
+    auto uh = [&](int kc, int r, int k) -> double {   // U_h row r, h chunk kc (counted after the X chunks)
+        const int col = (kc - nxc) * KC + k;
+        return col < H ? Uh[(size_t)r * H + col] : 0.0;
+    };
+    // phase 1: z and r pre-activations (one N = 2H block) over the X chunks,
+    // the candidate's X part (N = H) interleaved, then the h chunks of z, r
+    for (int kc = 0; kc < nxc; kc += (pair_zr && kc + 1 < nxc) ? 2 : 1) {
+        const bool pr = pair_zr && kc + 1 < nxc;
+        add(ITEM_D1, kc, pr, 0, 2 * H, 0, wx);
+        const int last = kc + (pr ? 1 : 0);
+        // candidate pairs end on odd chunks (or at the last X chunk)
+        for (int c = kc; c <= last; ++c)
+            if (c % 2 == 1 || c == nxc - 1) {
+                const bool cp = c % 2 == 1;   // pair (c - 1, c)
+                add(ITEM_D2X, cp ? c - 1 : c, cp, 0, H, 2 * H,
+                    [&](int q, int r, int k) { return wx(q, 2 * H + r, k); });
+            }
     }
+    for (int kc = nxc; kc < nxc + nhc; kc += (pair_zr && kc + 1 < nxc + nhc) ? 2 : 1)
+        add(ITEM_D1, kc, pair_zr && kc + 1 < nxc + nhc, 0, 2 * H, 0, uh);
     p.end1 = (int)items.size();
-    for (int kc = 0; kc < nhc; ++kc)
-        blocks(H, [&](int r0, int rows) {
-            add(ITEM_D2H, nxc + kc, r0, rows, 2 * H + r0, [&](int r, int k) -> double {
-                const int col = kc * KC + k;
-                return col < H ? Uh[(size_t)(2 * H + r) * H + col] : 0.0;
-            });
-        });
+    // phase 2: the candidate's recurrent part on (r * h)
+    for (int kc = nxc; kc < nxc + nhc; kc += (pair_h && kc + 1 < nxc + nhc) ? 2 : 1)
+        add(ITEM_D2H, kc, pair_h && kc + 1 < nxc + nhc, 0, H, 2 * H,
+            [&](int q, int r, int k) { return uh(q, 2 * H + r, k); });
     p.end2 = (int)items.size();
-    for (int kc = 0; kc < nhc; ++kc)
-        blocks(nfc, [&](int r0, int rows) {
-            add(ITEM_D3, nxc + kc, r0, rows, r0, [&](int r, int k) -> double {
-                const int col = kc * KC + k;
-                return (r < n_out && col < H) ? Wfc[(size_t)r * H + col] : 0.0;
-            });
+    // phase 3: the output layer on h'
+    for (int kc = nxc; kc < nxc + nhc; kc += (pair_fc && kc + 1 < nxc + nhc) ? 2 : 1)
+        add(ITEM_D3, kc, pair_fc && kc + 1 < nxc + nhc, 0, nfc, 0, [&](int q, int r, int k) -> double {
+            const int col = (q - nxc) * KC + k;
+            return (r < n_out && col < H) ? Wfc[(size_t)r * H + col] : 0.0;
         });
     p.nitems = (int)items.size();
     if (p.nitems > MAX_ITEMS) return false;
     int cols = 32;
     while (cols < 3 * H) cols *= 2;
     p.tmem_cols = cols;
-    // schedule words; a chunk accumulates unless it is the first K chunk of
+    // schedule words; a fill accumulates unless it holds the first K chunk of
     // its output block within its phase (phase 2 always adds onto phase 1)
     bool seen_h = false;
     for (int i = 0; i < p.nitems; ++i) {
@@ -517,12 +524,13 @@ bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc) {
             const bool same_phase = (j < p.end1) == (i < p.end1) && (j >= p.end2) == (i >= p.end2);
             acc = same_phase && items[j].dcol == it.dcol && items[j].kind == it.kind;
         }
-        const bool first_h = i < p.end1 && it.kc >= nxc && !seen_h;
+        const bool first_h = i < p.end1 && it.kc0 + it.pair >= nxc && !seen_h;
         seen_h = seen_h || first_h;
-        const int achunk = it.kc < nxc ? it.kc : p.nxs + it.kc - nxc;
-        p.items[i] = make_uint4((uint32_t)it.off, (uint32_t)(achunk * CHUNK), idesc_bf16(TM, it.rows),
-                                (uint32_t)it.dcol | (acc ? SCHED_ACC : 0u) | (first_h ? SCHED_FIRST_H : 0u) |
-                                    ((uint32_t)it.rows << 16));
+        auto aoff = [&](int kc) { return (uint32_t)((kc < nxc ? kc : p.nxs + kc - nxc) * CHUNK); };
+        p.items[2 * i] = make_uint4((uint32_t)it.off, (uint32_t)it.bytes, idesc_bf16(TM, it.rows),
+                                    (uint32_t)it.dcol | (acc ? SCHED_ACC : 0u) | (first_h ? SCHED_FIRST_H : 0u) |
+                                        (it.pair ? SCHED_PAIR : 0u) | ((uint32_t)it.rows << 16));
+        p.items[2 * i + 1] = make_uint4(aoff(it.kc0), it.pair ? aoff(it.kc0 + 1) : 0u, (uint32_t)(it.rows * 128), 0u);
     }
     if (smem_bytes(p) > 227 * 1024) return false;
     void *dblob = nullptr;

@@ -76,6 +76,7 @@ def _load():
         "dnnmg_step": [P, P, P, P, P, P, P, S, D, P],
         "dnnmg_step_host": [P, P, P, P, P, P, P, S, D, P],
         "dnnmg_step_launches": [P, P],
+        "dnnmg_step_timed": [P, P, P, P, P, P, P, S, D, P, I, P],
         "dnnmg_restrict": [P, P, P, P],
         "dnnmg_rhs": [P, P, P, P],
         "dnnmg_scatter_rhs": [P, P, P, D, P, P],
@@ -356,6 +357,26 @@ def dnnmg_step(mesh, net, xc, h, bf, bc, workspace, t, stream=None):
         raise TypeError("workspace must be a CUDA uint8 tensor")
     _check(_lib.dnnmg_step(mesh.handle, net.handle, _ptr(xc), _ptr(h), _ptr(bf), _ptr(bc),
                            _ptr(workspace), workspace.numel(), float(t), _stream(stream)))
+
+
+def dnnmg_step_timed(mesh, net, xc, h, bf, bc, workspace, t, events, stream=None):
+    """dnnmg_step recording events[0] before and events[i+1] after kernel i.
+
+    events: dnnmg_step_launches() + 1 torch.cuda.Event objects with timing
+    enabled (each is recorded once here first, which creates it)."""
+    I = mesh.info
+    _need(xc, torch.float64, 3 * I.Nc, "xc")
+    _need(h, mesh.real, I.P * net.H, "h")
+    _need(bf, mesh.real, 2 * I.plane, "bf")
+    _need(bc, torch.float64, 3 * I.Nc, "bc")
+    if workspace.dtype != torch.uint8 or not workspace.is_cuda:
+        raise TypeError("workspace must be a CUDA uint8 tensor")
+    for e in events:
+        if not e.cuda_event:
+            e.record()
+    arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+    _check(_lib.dnnmg_step_timed(mesh.handle, net.handle, _ptr(xc), _ptr(h), _ptr(bf), _ptr(bc),
+                                 _ptr(workspace), workspace.numel(), float(t), arr, len(events), _stream(stream)))
 
 
 def dnnmg_step_static(mesh, net, xc, h, bf, bc, t, stream=None):

@@ -278,6 +278,35 @@ def test_step_leaves_mesh_status_clear(dn):
     assert dn.dnnmg_net_status(net) == 0
 
 
+def test_step_timed_matches_step(dn):
+    # the instrumented step records one event per kernel and computes the same bits
+    case = CASES["k2s2_bf16"]
+    m = gpu_mesh(dn, case)
+    om = oracle_mesh(case)
+    Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
+    net = dn.Net(Wx, Uh, Wfc, "bf16")
+    xc = cuda(coarse_input(case, t=0.0), torch.float64)
+    outs = []
+    for timed in (False, True):
+        h = torch.zeros(om.P, case["H"], device="cuda")
+        bf, bc, ws = m.fine(2), m.coarse(3), m.workspace()
+        if timed:
+            n = dn.dnnmg_step_launches(m, net)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+            dn.dnnmg_step_timed(m, net, xc, h, bf, bc, ws, 0.0, ev)
+            with pytest.raises(dn.DnnmgError):
+                dn.dnnmg_step_timed(m, net, xc, h, bf, bc, ws, 0.0, ev[:-1])
+        else:
+            dn.dnnmg_step(m, net, xc, h, bf, bc, ws, 0.0)
+        torch.cuda.synchronize()
+        outs.append((h.cpu(), bf.cpu(), bc.cpu()))
+        if timed:
+            times = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+            assert all(t >= 0.0 for t in times)
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
 def test_zero_network_reduces_to_prolongated_rhs(dn):
     # with W_fc = 0 the correction vanishes, so v_corr = v~ and the step
     # returns R Rhs(P x_c) (Algorithm 2 without the network)
