@@ -24,6 +24,7 @@ constexpr int TYC = 16;            // fine cells per tile in y
 constexpr int NXN = TXC + 1;       // tile nodes in x
 constexpr int NYN = TYC + 1;
 constexpr int NTHREADS = 256;
+constexpr int RES_THREADS = 256;   // residual/feature kernels (10 warps measured slower)
 
 template <typename TX, typename T> __device__ __forceinline__ TX store_as(T v) { return (TX)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, float>(float v) {
@@ -828,7 +829,7 @@ __device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T
 // inside the tile (S1 fused: x~ never reaches HBM), with the Dirichlet
 // values set where the tile touches a boundary.
 template <typename T, typename TX, int R>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(RES_THREADS)
 k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const double *__restrict__ xc,
                     double inflow_peak, const T *__restrict__ bf, T *__restrict__ rf, TX *__restrict__ X) {
     using L = ResLayout;
@@ -911,7 +912,7 @@ struct StepLayout {
 // is bounded: on time-out the mesh status gets DNNMG_DEVERR_TIMEOUT and the
 // CTA returns once its copies have landed.
 template <typename T, typename TX, int R>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(RES_THREADS)
 k_residual_step(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, double inflow_peak, TX *__restrict__ X) {
     using L = ResLayout;
@@ -983,36 +984,59 @@ struct PatchWin {
             pid[e] = (pi >= 0 && pj >= 0 && pi < g.npx && pj < g.npy) ? __ldg(g.patch_id + pj * g.npx + pi) : -1;
         }
     }
-    // v~ + the mean of d over the fluid patches holding node (I, J) (Eq. for
-    // the averaged correction: every patch holding a node contributes its
-    // network output for that node, lower / left patches first)
+    // The mean of d over the fluid patches holding node (I, J) (the averaged
+    // correction: every patch holding a node contributes its network output
+    // for that node).  In two parts so that callers can issue the loads of
+    // several nodes before using any: the node's own patch (first), then on
+    // patch edges the left, lower and lower-left neighbours.
     template <typename T>
-    __device__ __forceinline__ void add_mean(const MeshGeom &g, const T *__restrict__ d, int I, int J, T &u,
-                                             T &v) const {
+    __device__ __forceinline__ void own_patch(const MeshGeom &g, const T *__restrict__ d, int I, int J, T &su, T &sv,
+                                              int &cnt) const {
+        const int S = 1 << lS;
+        const int id = pid[((J >> lS) - py0) * npw + (I >> lS) - px0];
+        su = sv = T(0);
+        cnt = 0;
+        if (id >= 0) {
+            const T *q = d + (size_t)id * g.n_out + (J & (S - 1)) * (S + 1) + (I & (S - 1));
+            su = __ldg(q);
+            sv = __ldg(q + g.nf);
+            cnt = 1;
+        }
+    }
+    template <typename T>
+    __device__ __forceinline__ void edge_patches(const MeshGeom &g, const T *__restrict__ d, int I, int J, T &su, T &sv,
+                                                 int &cnt) const {
         const int S = 1 << lS;
         const int row = (J >> lS) - py0, lj = J & (S - 1), col = (I >> lS) - px0, li = I & (S - 1);
-        T su = T(0), sv = T(0);
-        int cnt = 0;
+        if (lj != 0 && li != 0) return;
 #pragma unroll
-        for (int oy = 1; oy >= 0; --oy) {
-            if (oy && lj != 0) continue;
-#pragma unroll
-            for (int ox = 1; ox >= 0; --ox) {
-                if (ox && li != 0) continue;
-                const int id = pid[(row - oy) * npw + col - ox];
-                if (id < 0) continue;
-                const int k = (lj + oy * S) * (S + 1) + li + ox * S;
-                su += __ldg(d + (size_t)id * g.n_out + k);
-                sv += __ldg(d + (size_t)id * g.n_out + g.nf + k);
-                ++cnt;
-            }
+        for (int o = 1; o < 4; ++o) {   // (ox, oy) = (1, 0), (0, 1), (1, 1)
+            const int ox = o & 1, oy = o >> 1;
+            if ((ox && li != 0) || (oy && lj != 0)) continue;
+            const int id = pid[(row - oy) * npw + col - ox];
+            if (id < 0) continue;
+            const T *q = d + (size_t)id * g.n_out + (lj + oy * S) * (S + 1) + li + ox * S;
+            su += __ldg(q);
+            sv += __ldg(q + g.nf);
+            ++cnt;
         }
+    }
+    template <typename T> static __device__ __forceinline__ void add_sum(T su, T sv, int cnt, T &u, T &v) {
         if (cnt) {
             // 1, 1/2 and 1/4 are exact
             const T inv = cnt == 1 ? T(1) : cnt == 2 ? T(0.5) : cnt == 4 ? T(0.25) : T(1) / T(cnt);
             u += su * inv;
             v += sv * inv;
         }
+    }
+    template <typename T>
+    __device__ __forceinline__ void add_mean(const MeshGeom &g, const T *__restrict__ d, int I, int J, T &u,
+                                             T &v) const {
+        T su, sv;
+        int cnt;
+        own_patch(g, d, I, J, su, sv, cnt);
+        edge_patches(g, d, I, J, su, sv, cnt);
+        add_sum(su, sv, cnt, u, v);
     }
 };
 
@@ -1039,33 +1063,52 @@ k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, con
     __syncthreads();   // publishes pid_s and the staged coarse nodes
     const int I = I0 + (threadIdx.x & (PTX - 1));
     if (I > g.nxf) return;
-    // a fixed trip count lets the loads of all rows be in flight together
+    // this thread's rows; the own-patch loads of all of them are issued first
+    constexpr int NR = PTY / (NTHREADS / PTX);
+    T u[NR], v[NR], su[NR], sv[NR];
+    int cnt[NR];
+    bool keep[NR];   // row exists and the node is not a Dirichlet node
 #pragma unroll
-    for (int k = 0; k < PTY / (NTHREADS / PTX); ++k) {
+    for (int k = 0; k < NR; ++k) {
         const int J = J0 + threadIdx.x / PTX + k * (NTHREADS / PTX);
-        if (J > g.nyf) break;
-        const size_t node = (size_t)J * g.pitch + I;
-        T u, v;
+        const bool live = J <= g.nyf;
+        const int Jc = live ? J : g.nyf;   // a valid row for the (unused) reads of a dead one
         if constexpr (R > 0) {
             T x[2];
-            cw.interp(I, J, x);
-            u = x[0];
-            v = x[1];
+            cw.interp(I, Jc, x);
+            u[k] = x[0];
+            v[k] = x[1];
         } else {
-            u = xf[node];
-            v = xf[g.plane + node];
+            const size_t node = (size_t)Jc * g.pitch + I;
+            u[k] = xf[node];
+            v[k] = xf[g.plane + node];
         }
-        T uD, vD;
-        if (!fast && dirichlet_value(g, I, J, up, uD, vD)) {   // keeps v~ = the boundary value
-            if constexpr (R > 0) {
-                u = uD;
-                v = vD;
+        keep[k] = live;
+        if (live && !fast) {
+            T uD, vD;
+            if (dirichlet_value(g, I, J, up, uD, vD)) {   // keeps v~ = the boundary value
+                if constexpr (R > 0) {
+                    u[k] = uD;
+                    v[k] = vD;
+                }
+                keep[k] = false;
             }
-        } else {
-            pw.add_mean(g, d, I, J, u, v);
         }
-        vc[node] = u;
-        vc[g.plane + node] = v;
+        su[k] = sv[k] = T(0);
+        cnt[k] = 0;
+        if (keep[k]) pw.own_patch(g, d, I, J, su[k], sv[k], cnt[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int J = J0 + threadIdx.x / PTX + k * (NTHREADS / PTX);
+        if (J > g.nyf) break;
+        if (keep[k]) {
+            pw.edge_patches(g, d, I, J, su[k], sv[k], cnt[k]);
+            PatchWin::add_sum(su[k], sv[k], cnt[k], u[k], v[k]);
+        }
+        const size_t node = (size_t)J * g.pitch + I;
+        vc[node] = u[k];
+        vc[g.plane + node] = v[k];
     }
 }
 
@@ -1550,7 +1593,7 @@ cudaError_t run_residual(const MeshGeom &g, const FemCoef<T> &fc, const void *xf
     const size_t sm = ResLayout::bytes<T>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k<<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, (const T *)xf, xc, w, (const T *)bf, (T *)rf, (TX *)X);
+    k<<<tile_grid(g), RES_THREADS, sm, st>>>(g, fc, (const T *)xf, xc, w, (const T *)bf, (T *)rf, (TX *)X);
     return cudaGetLastError();
 }
 
@@ -1613,7 +1656,7 @@ cudaError_t run_residual_step(const MeshGeom &g, const FemCoef<T> &fc, const T *
     const size_t sm = SL::BYTES;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k<<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, tmB, tmC, up, X);
+    k<<<tile_grid(g), RES_THREADS, sm, st>>>(g, fc, tmB, tmC, up, X);
     return cudaGetLastError();
 }
 
