@@ -641,10 +641,12 @@ __device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T
     // Feature columns after the residual ones (Sec. 5.2 inputs): x~ and the
     // Peclet number on the coarse patch nodes, geometry, zero padding;
     // feat_tab[c] says where column c comes from relative to the patch
-    // origin.  One warp per patch; lanes write consecutive columns.
-    {
+    // origin.  One warp per patch (warps w0 .. w0+nw-1); lanes write
+    // consecutive columns.  Fast tiles run it on the warps the 2x2-block
+    // pass leaves idle.
+    auto patch_inputs = [&](int w0, int nw) {
         const int S = 1 << lS, nres = 3 * g.nf;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const int warp = (int)(threadIdx.x >> 5) - w0, lane = threadIdx.x & 31;
         for (int tp = warp; tp < tpx * tpy; tp += nw) {
             const int id = pid[tp];
             if (id < 0) continue;
@@ -661,7 +663,7 @@ __device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T
                 row[c] = store_as<TX, T>(val);
             }
         }
-    }
+    };
 
     if (fast) {
         // convection contributions of every cell around the tile's nodes,
@@ -695,14 +697,18 @@ __device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T
         __syncthreads();
         // 16 blocks of one row per half-warp (contiguous pairs: conflict-free
         // 64-bit loads), then the last block column
+        constexpr int BW = (L::NB + 31) / 32;   // warps of the block pass
         if (threadIdx.x < L::NB) {
             const int t = threadIdx.x;
             const bool main = t < 16 * L::NBY;
             const int bx = main ? (t & 15) : L::NBX - 1, by = main ? (t >> 4) : t - 16 * L::NBY;
             block_residual(g, fc, xs, bs, cc, pid, tpx, tpy, lS, I0, J0, bx, by, rf, X);
+        } else if (threadIdx.x >= 32 * BW) {
+            patch_inputs(BW, (int)(blockDim.x >> 5) - BW);
         }
         return;
     }
+    patch_inputs(0, blockDim.x >> 5);
 
     // ---- tiles near a boundary: element by element, with the cell codes
     T *lc = un;   // [9][NLPS]
