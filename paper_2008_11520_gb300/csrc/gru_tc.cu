@@ -145,7 +145,9 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
          const __grid_constant__ CUtensorMap tmH, float *__restrict__ h, float *__restrict__ d, int P) {
     constexpr int NH = H / 2;           // state columns per epilogue thread
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // aligned by an offset from the shared-memory symbol itself, so that every
+    // access through base stays a shared-memory access (no generic pointers)
+    uint8_t *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *sX = base;                                   // max(nxc, H/32) chunks
     uint8_t *sAh = sX + p.nxs * CHUNK;                    // nhc chunks
     uint8_t *sW = sAh + p.nhc * CHUNK;                    // NSTAGE stages

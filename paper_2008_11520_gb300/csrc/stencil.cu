@@ -927,7 +927,9 @@ k_residual_step(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap t
     constexpr int K = Log2<R>::v;
     extern __shared__ unsigned char smem_raw[];
     __shared__ T geo_s[12];
-    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // aligned by an offset from the shared-memory symbol itself, so that every
+    // access through base stays a shared-memory access (no generic pointers)
+    unsigned char *base = smem_raw + ((128u - (ptx::smem_u32(smem_raw) & 127u)) & 127u);
     const T *bs = reinterpret_cast<const T *>(base + SL::BSB);
     T *xs = reinterpret_cast<T *>(base + SL::XS);
     T *cc = reinterpret_cast<T *>(base + SL::CC);
