@@ -1130,7 +1130,11 @@ struct RhsLayout {
     static constexpr int NCP = NCELL + 4;              // corner arrays, as in ResLayout
     static constexpr int VS = 2 * HP;
     static constexpr int CC = 8 * NCP;
-    template <typename T> static constexpr size_t bytes() { return sizeof(T) * (VS + CC) + NCELL; }
+    // v_corr window (a TMA box, 128-byte aligned), cell contributions, cell
+    // codes, the barrier and the abort flag, alignment slack
+    template <typename T> static constexpr size_t bytes() {
+        return (sizeof(T) * (VS + CC) + NCELL + 7) / 8 * 8 + 16 + 128;
+    }
     static __device__ __forceinline__ int ccx(int k, int cid) { return k * NCP + cid + ((k & 1) ^ 1); }
 };
 
@@ -1279,16 +1283,30 @@ __device__ __forceinline__ void rhs_tile(const MeshGeom &g, const FemCoef<T> &fc
     }
 }
 
+// One CTA per tile; one thread fetches the v_corr window as a TMA box (rows
+// outside the mesh read as zero) while the others classify the cells of
+// boundary tiles.  The wait is bounded: on time-out the mesh status gets
+// DNNMG_DEVERR_TIMEOUT and the CTA returns once its copy has landed.
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
-k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf) {
+k_rhs(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap tmV, T *__restrict__ bf) {
     using L = RhsLayout;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *vs = reinterpret_cast<T *>(smem_raw);   // [2][HY][HX]
-    T *cc = vs + L::VS;                        // [8][NCP]
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128u - (ptx::smem_u32(smem_raw) & 127u)) & 127u);
+    T *vs = reinterpret_cast<T *>(base);   // [2][HY][HX]
+    T *cc = vs + L::VS;                    // [8][NCP]
     unsigned char *cf = reinterpret_cast<unsigned char *>(cc + L::CC);   // [CY][CX]
+    uint64_t *mb = reinterpret_cast<uint64_t *>(base + (sizeof(T) * (L::VS + L::CC) + L::NCELL + 7) / 8 * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(mb + 1);
+    const uint32_t mb_u = ptx::smem_u32(mb);
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
-    stage_window<T, 2, L::HY, L::HX>(g, vcorr, I0 - L::XO, J0 - L::YO, vs);
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(mb_u, 1);
+        *abort_flag = 0;
+        ptx::mbar_init_fence();
+        ptx::expect_tx(mb_u, (uint32_t)(sizeof(T) * L::VS));
+        ptx::tma_load_3d(ptx::smem_u32(vs), &tmV, I0 - L::XO, J0 - L::YO, 0, mb_u);
+    }
     const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 2);
     if (!fast) {
         for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
@@ -1296,8 +1314,16 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ vcorr, T *__restrict__ bf
             cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
         }
     }
-    cp_async_wait_all();
-    __syncthreads();
+    __syncthreads();   // the barrier is initialised; cf is visible
+    const bool ok = ptx::mbar_test(mb_u, 0) || ptx::mbar_wait(mb_u, 0, abort_flag);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(g.status, DNNMG_DEVERR_TIMEOUT);
+            volatile int no_abort = 0;   // let the copy land before leaving
+            ptx::mbar_wait(mb_u, 0, &no_abort);
+        }
+        return;
+    }
     rhs_tile(g, fc, vs, cc, cf, fast, I0, J0, bf);
 }
 
@@ -1710,19 +1736,27 @@ cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const
     return run_scatter(g, (const float *)d, (const float *)xf, xc, w, (float *)vcorr, st);
 }
 
+template <typename T>
+cudaError_t run_rhs(const MeshGeom &g, const FemCoef<T> &fc, const T *vcorr, T *bf, cudaStream_t st) {
+    using L = RhsLayout;
+    // v_corr [2][nyf+1][pitch]: boxes of the tile's node window
+    CUtensorMap tm;
+    const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nxf + 1, (cuuint64_t)g.nyf + 1, 2};
+    const cuuint64_t str[2] = {(cuuint64_t)g.pitch * sizeof(T), (cuuint64_t)g.plane * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)L::HX, (cuuint32_t)L::HY, 2};
+    if (!tma_encode_tiled(&tm, dt, 3, const_cast<T *>(vcorr), dims, str, box)) return cudaErrorInvalidValue;
+    const size_t sm = L::bytes<T>();
+    cudaError_t e = set_smem(k_rhs<T>, sm);
+    if (e != cudaSuccess) return e;
+    k_rhs<T><<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, tm, bf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
                        const FemCoef<float> &f32, const void *vcorr, void *bf, cudaStream_t st) {
-    cudaError_t e;
-    if (prec == DNNMG_F64) {
-        const size_t sm = RhsLayout::bytes<double>();
-        if ((e = set_smem(k_rhs<double>, sm)) != cudaSuccess) return e;
-        k_rhs<double><<<tile_grid(g), NTHREADS, sm, st>>>(g, f64, (const double *)vcorr, (double *)bf);
-    } else {
-        const size_t sm = RhsLayout::bytes<float>();
-        if ((e = set_smem(k_rhs<float>, sm)) != cudaSuccess) return e;
-        k_rhs<float><<<tile_grid(g), NTHREADS, sm, st>>>(g, f32, (const float *)vcorr, (float *)bf);
-    }
-    return cudaGetLastError();
+    if (prec == DNNMG_F64) return run_rhs(g, f64, (const double *)vcorr, (double *)bf, st);
+    return run_rhs(g, f32, (const float *)vcorr, (float *)bf, st);
 }
 
 template <typename T, int R>
