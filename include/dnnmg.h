@@ -211,10 +211,11 @@ int dnnmg_rhs(dnnmg_mesh_t mesh, const void *vcorr, void *bf, cudaStream_t strea
 /*
  * S5 + S6 fused, Algorithm 2 lines 7-8: bf = Rhs(v~ + averaged d) with
  * v~ = P xc at time t formed inside each tile (as dnnmg_scatter_avg with xc
- * followed by dnnmg_rhs, same arithmetic); v_corr never reaches memory,
- * at the price of averaging every tile's one-node halo again.
- *   d [P][n_out] real (in; ignored if P = 0), xc [3][Nc] double (in),
- *   bf [2][plane] real (out).
+ * followed by dnnmg_rhs, same arithmetic and bits); v_corr never reaches
+ * memory.  Each tile copies the d rows of the patches around it to shared
+ * memory and averages its one-node halo again.
+ *   d [P][n_out] real (in, 8-byte aligned; ignored if P = 0), xc [3][Nc]
+ *   double (in), bf [2][plane] real (out).
  */
 int dnnmg_scatter_rhs(dnnmg_mesh_t mesh, const void *d, const double *xc, double t, void *bf,
                       cudaStream_t stream);

@@ -633,6 +633,7 @@ int dnnmg_scatter_rhs(dnnmg_mesh_t mesh, const void *d, const double *xc, double
     if (int e = check_mesh(mesh)) return e;
     if ((!d && mesh->info.P) || !xc || !bf) return fail(DNNMG_EINVAL, "NULL array");
     if (!aligned16(bf)) return fail(DNNMG_EINVAL, "fine fields must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(d) % 8) return fail(DNNMG_EINVAL, "d must be 8-byte aligned");
     DNNMG_CUDA_TRY(launch_avg_rhs(mesh->g, mesh->info.precision, mesh->fem64, mesh->fem32, d, xc, t, bf, stream));
     return DNNMG_OK;
 }
@@ -698,8 +699,9 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
     // S1 is fused into S2+S3 and into S5: both interpolate x~ from xc inside
     // their tiles, so x~ never goes to memory; S2+S3 reads x_c as a padded
     // copy in the fine type, fetched by TMA.  (S5+S6 as one kernel keeps
-    // v_corr on chip but recomputes the averaging on every tile's halo, which
-    // costs more than the v_corr round trip; see dnnmg_scatter_rhs.)
+    // v_corr on chip but averages every tile's halo again and waits on two
+    // dependent global fetches per tile; it measured slower than the v_corr
+    // round trip.  See dnnmg_scatter_rhs.)
     DNNMG_CUDA_TRY(launch_coarse_pad(g, prec, xc, w.xcp, s));
     DNNMG_CUDA_TRY(mark());
     DNNMG_CUDA_TRY(launch_residual_step(g, prec, mesh->fem64, mesh->fem32, w.xcp, t, bf, w.X, s));

@@ -74,6 +74,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_b
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Asynchronous 8-byte copy global -> shared (both 8-byte aligned).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
 
 // Stage a window of NCOMP component planes: rows J0 .. J0+NROWS-1, columns
 // Ia .. Ia+W-1 (Ia and W multiples of 16 bytes) into dst[c][row][W].  Pieces
@@ -1037,15 +1042,6 @@ struct PatchWin {
             v += sv * inv;
         }
     }
-    template <typename T>
-    __device__ __forceinline__ void add_mean(const MeshGeom &g, const T *__restrict__ d, int I, int J, T &u,
-                                             T &v) const {
-        T su, sv;
-        int cnt;
-        own_patch(g, d, I, J, su, sv, cnt);
-        edge_patches(g, d, I, J, su, sv, cnt);
-        add_sum(su, sv, cnt, u, v);
-    }
 };
 
 // A CTA owns 64 x 16 nodes; lanes take consecutive nodes of a row (so the
@@ -1329,29 +1325,58 @@ k_rhs(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap tmV, T *__r
 
 // S5 + S6 fused for the correction step: the v_corr window of a right-hand
 // side tile (x~ = P x_c plus the patch mean of d, Dirichlet values at the
-// boundary) is formed in shared memory and never reaches HBM.  The coarse
-// window and the patch numbers live in the cell-contribution buffer until
-// the window is complete.  Same arithmetic as S5 followed by S6.
+// boundary) is formed in shared memory and never reaches HBM.  The network
+// outputs of every patch holding a node of the window are copied into
+// shared memory first (one warp per patch row of d, coalesced), so the
+// means are formed from shared memory.  Same arithmetic and order as S5
+// followed by S6, hence the same bits.
+//
+// Shared memory: the v_corr window, then a region that first holds the
+// coarse window, the window's patch numbers and its d rows, and afterwards
+// the cell contributions of the right-hand side, then the cell codes.
+template <typename T>
+struct AvgRhsLayout {
+    using L = RhsLayout;
+    // patches holding the nodes I0-1 .. I0+33, J0-1 .. J0+17 that S6 reads
+    static __host__ __device__ int npw(int lS) { return ((TXC + 1) >> lS) + 2; }
+    static __host__ __device__ int nph(int lS) { return ((TYC + 1) >> lS) + 2; }
+    static __host__ size_t region(int R, int lS, int n_out) {
+        const size_t cwin = 2 * ((L::HX - 1) / R + 3) * ((L::HY - 1) / R + 3);
+        const size_t slots = (size_t)npw(lS) * nph(lS);
+        const size_t stage = cwin + slots + slots * n_out;   // pid slots counted as T
+        return stage > (size_t)L::CC ? stage : (size_t)L::CC;
+    }
+    static __host__ size_t bytes(int R, int lS, int n_out) {
+        return sizeof(T) * (L::VS + region(R, lS, n_out)) + L::NCELL;
+    }
+};
+
 template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS)
 k_avg_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ d, const double *__restrict__ xc, double inflow_peak,
-          T *__restrict__ bf) {
+          T *__restrict__ bf, int region) {
     using L = RhsLayout;
+    using AL = AvgRhsLayout<T>;
     using CWin = CoarseWin<T, R, L::HX, L::HY, 2>;
-    constexpr int MAXPID = ((L::HX + 3) / 2 + 2) * ((L::HY + 1) / 2 + 2);
-    static_assert(CWin::N * sizeof(T) + MAXPID * sizeof(int) <= L::CC * sizeof(T), "staging fits in cc");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *vs = reinterpret_cast<T *>(smem_raw);   // [2][HY][HX]
-    T *cc = vs + L::VS;                        // [8][NCP]; first the coarse window and the patch numbers
-    unsigned char *cf = reinterpret_cast<unsigned char *>(cc + L::CC);   // [CY][CX]
+    T *cc = vs + L::VS;                        // region: staging, then [8][NCP]
+    unsigned char *cf = reinterpret_cast<unsigned char *>(cc + region);   // [CY][CX]
     const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
     const int Ilo = I0 - L::XO, Jlo = J0 - L::YO;
+    const int lS = g.K + g.s - 1, S = 1 << lS;   // S = s 2^K with s = 1, 2
+    const int npw = AL::npw(lS), nph = AL::nph(lS), nslot = npw * nph;
+    const int pxlo = (I0 - 1) >> lS, pylo = (J0 - 1) >> lS;
     CWin cw;
     cw.cs = cc;
     cw.stage(g, xc, Ilo, Jlo);
-    PatchWin pw;
-    pw.pid = reinterpret_cast<int *>(cc + CWin::N);
-    pw.stage(g, Ilo, Ilo + L::HX - 1, Jlo, Jlo + L::HY - 1);
+    int *spid = reinterpret_cast<int *>(cc + CWin::N);   // [nph][npw]
+    T *dw = cc + CWin::N + nslot;                        // [nph][npw][n_out]
+    for (int e = threadIdx.x; e < nslot; e += blockDim.x) {
+        const int b = e / npw, a = e - b * npw;
+        const int pi = pxlo + a, pj = pylo + b;
+        spid[e] = (pi >= 0 && pj >= 0 && pi < g.npx && pj < g.npy) ? __ldg(g.patch_id + pj * g.npx + pi) : -1;
+    }
     const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 2);
     if (!fast) {
         for (int idx = threadIdx.x; idx < L::NCELL; idx += blockDim.x) {
@@ -1359,17 +1384,29 @@ k_avg_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ d, const double *__re
             cf[idx] = (unsigned char)cell_code(g, I0 - 1 + ii, J0 - 1 + jj);
         }
     }
-    const double up = inflow_peak;
     __syncthreads();
-    // a fixed trip count lets the loads of all rounds be in flight together
-#pragma unroll
-    for (int rnd = 0; rnd < (L::HP + NTHREADS - 1) / NTHREADS; ++rnd) {
-        const int e = threadIdx.x + rnd * NTHREADS;
-        if (e >= L::HP) break;
+    // the d rows of the window's patches, one warp per patch, as asynchronous
+    // 8-byte copies all in flight at once (rows are 8-byte aligned: n_out is even)
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const int pieces = (g.n_out * (int)sizeof(T)) / 8, per = 8 / (int)sizeof(T);
+        for (int e = warp; e < nslot; e += nw) {
+            const int id = spid[e];
+            if (id < 0) continue;
+            const T *src = d + (size_t)id * g.n_out;
+            T *dst = dw + e * g.n_out;
+            for (int k = lane; k < pieces; k += 32) cp_async8(dst + k * per, src + k * per);
+        }
+    }
+    const double up = inflow_peak;
+    cp_async_wait_all();
+    __syncthreads();
+    for (int e = threadIdx.x; e < L::HP; e += blockDim.x) {
         const int row = e / L::HX, col = e - row * L::HX;
         const int I = Ilo + col, J = Jlo + row;
         T u = T(0), v = T(0);
-        if (I >= 0 && J >= 0 && I <= g.nxf && J <= g.nyf) {
+        // S6 reads nodes I0-1 .. I0+33; the window's outer columns stay zero
+        if (I >= I0 - 1 && I <= I0 + TXC + 1 && I >= 0 && J >= 0 && I <= g.nxf && J <= g.nyf) {
             T x[2];
             cw.interp(I, J, x);
             u = x[0];
@@ -1379,7 +1416,23 @@ k_avg_rhs(MeshGeom g, FemCoef<T> fc, const T *__restrict__ d, const double *__re
                 u = uD;
                 v = vD;
             } else {
-                pw.add_mean(g, d, I, J, u, v);
+                // the mean of d over the fluid patches holding the node: own patch
+                // first, then on patch edges the left, lower and lower-left ones
+                const int sr = (J >> lS) - pylo, sc = (I >> lS) - pxlo, lj = J & (S - 1), li = I & (S - 1);
+                T su = T(0), sv = T(0);
+                int cnt = 0;
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {   // (ox, oy) = (0, 0), (1, 0), (0, 1), (1, 1)
+                    const int ox = o & 1, oy = o >> 1;
+                    if ((ox && li != 0) || (oy && lj != 0)) continue;
+                    const int slot = (sr - oy) * npw + sc - ox;
+                    if (spid[slot] < 0) continue;
+                    const T *q = dw + slot * g.n_out + (lj + oy * S) * (S + 1) + li + ox * S;
+                    su += q[0];
+                    sv += q[g.nf];
+                    ++cnt;
+                }
+                PatchWin::add_sum(su, sv, cnt, u, v);
             }
         }
         vs[e] = u;
@@ -1762,10 +1815,12 @@ cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
 template <typename T, int R>
 cudaError_t run_avg_rhs(const MeshGeom &g, const FemCoef<T> &fc, const T *d, const double *xc, double up, T *bf,
                         cudaStream_t st) {
-    const size_t sm = RhsLayout::bytes<T>();
+    const int lS = g.K + g.s - 1;
+    const size_t region = AvgRhsLayout<T>::region(R, lS, g.n_out);
+    const size_t sm = AvgRhsLayout<T>::bytes(R, lS, g.n_out);
     cudaError_t e = set_smem(k_avg_rhs<T, R>, sm);
     if (e != cudaSuccess) return e;
-    k_avg_rhs<T, R><<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, d, xc, up, bf);
+    k_avg_rhs<T, R><<<tile_grid(g), NTHREADS, sm, st>>>(g, fc, d, xc, up, bf, (int)region);
     return cudaGetLastError();
 }
 
