@@ -1486,19 +1486,40 @@ struct RestrictAcc64 {
 // covers ci r +- (r-1) for the tile's 128/r coarse columns when r <= 8).
 constexpr int RFW = 128 + 16, RXO = 8;
 
+// One thread fetches the tile's fine window as a TMA box (rows and columns
+// outside the mesh read as zero); the wait is bounded (on time-out the mesh
+// status gets DNNMG_DEVERR_TIMEOUT and the CTA returns once the copy has landed).
 template <typename T, typename Acc, int R>
 __global__ void __launch_bounds__(NTHREADS)
-k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
+k_restrict(MeshGeom g, const __grid_constant__ CUtensorMap tmB, double *__restrict__ bc) {
     using Row = typename Acc::Row;
     constexpr int TCX = 128 / R, TCY = 32 / R;              // coarse nodes per tile
     constexpr int FH = TCY * R + R - 1;                     // fine rows staged
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *fs = reinterpret_cast<T *>(smem_raw);                // [2][FH][RFW]
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128u - (ptx::smem_u32(smem_raw) & 127u)) & 127u);
+    T *fs = reinterpret_cast<T *>(base);                    // [2][FH][RFW]
     Row *rs = reinterpret_cast<Row *>(fs + 2 * FH * RFW);   // [2][FH][TCX] x-restricted rows
+    uint64_t *mb = reinterpret_cast<uint64_t *>(rs + 2 * FH * TCX);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(mb + 1);
+    const uint32_t mb_u = ptx::smem_u32(mb);
     const int ci0 = blockIdx.x * TCX, cj0 = blockIdx.y * TCY;
-    stage_window<T, 2, FH, RFW>(g, bf, ci0 * R - RXO, cj0 * R - (R - 1), fs);
-    cp_async_wait_all();
-    __syncthreads();
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(mb_u, 1);
+        *abort_flag = 0;
+        ptx::mbar_init_fence();
+        ptx::expect_tx(mb_u, (uint32_t)(sizeof(T) * 2 * FH * RFW));
+        ptx::tma_load_3d(ptx::smem_u32(fs), &tmB, ci0 * R - RXO, cj0 * R - (R - 1), 0, mb_u);
+    }
+    __syncthreads();   // the barrier is initialised
+    const bool ok = ptx::mbar_test(mb_u, 0) || ptx::mbar_wait(mb_u, 0, abort_flag);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(g.status, DNNMG_DEVERR_TIMEOUT);
+            volatile int no_abort = 0;   // let the copy land before leaving
+            ptx::mbar_wait(mb_u, 0, &no_abort);
+        }
+        return;
+    }
     constexpr T inv_r = T(1) / T(R);
     for (int e = threadIdx.x; e < 2 * FH * TCX; e += blockDim.x) {
         const int c = e / (FH * TCX), rem = e - c * (FH * TCX);
@@ -1542,17 +1563,25 @@ k_restrict(MeshGeom g, const T *__restrict__ bf, double *__restrict__ bc) {
 template <typename T, typename Acc, int R>
 size_t restrict_smem() {
     const size_t FH = (size_t)(32 / R) * R + R - 1;
-    return 2 * FH * RFW * sizeof(T) + 2 * FH * (128 / R) * sizeof(typename Acc::Row);
+    // fine window (TMA box), x-restricted rows, barrier and abort flag, alignment slack
+    return 2 * FH * RFW * sizeof(T) + 2 * FH * (128 / R) * sizeof(typename Acc::Row) + 16 + 128;
 }
 
 template <typename T, typename Acc, int R>
 cudaError_t run_restrict(const MeshGeom &g, const T *bf, double *bc, cudaStream_t st) {
-    constexpr int TCX = 128 / R, TCY = 32 / R;
+    constexpr int TCX = 128 / R, TCY = 32 / R, FH = TCY * R + R - 1;
+    // b_f [2][nyf+1][pitch]: boxes of RFW columns x FH rows x 2 components
+    CUtensorMap tm;
+    const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nxf + 1, (cuuint64_t)g.nyf + 1, 2};
+    const cuuint64_t str[2] = {(cuuint64_t)g.pitch * sizeof(T), (cuuint64_t)g.plane * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)RFW, (cuuint32_t)FH, 2};
+    if (!tma_encode_tiled(&tm, dt, 3, const_cast<T *>(bf), dims, str, box)) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((g.nxc + TCX) / TCX), (unsigned)((g.nyc + TCY) / TCY));
     const size_t sm = restrict_smem<T, Acc, R>();
     cudaError_t e = cudaFuncSetAttribute(k_restrict<T, Acc, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_restrict<T, Acc, R><<<grid, NTHREADS, sm, st>>>(g, bf, bc);
+    k_restrict<T, Acc, R><<<grid, NTHREADS, sm, st>>>(g, tm, bc);
     return cudaGetLastError();
 }
 
