@@ -158,6 +158,25 @@ struct CoarseWin {
             out[c] = lerp(lerp(q[0], q[1], a), lerp(q[CW], q[CW + 1], a), b);
         }
     }
+    // interp at the 4 nodes Ib .. Ib+3 of row J, Ib a multiple of 4 (same
+    // arithmetic, so the same bits; the cell and weights are compile-time
+    // offsets for R <= 4, and for R = 8 the run lies in one cell).
+    __device__ __forceinline__ void interp4(int Ib, int J, T (&out)[NC][4]) const {
+        constexpr T inv_r = T(1) / T(R);
+        const int r0 = R <= 4 ? 0 : (Ib & (R - 1));
+        const T b = T(J & (R - 1)) * inv_r;
+        const int o = ((J >> K) - cj0) * CW + ((Ib >> K) - ci0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const T *q = cs + c * CW * CH + o;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                const int e = r0 + n, dc = R >= 4 ? 0 : (e >> K);
+                const T a = T(e & (R - 1)) * inv_r;
+                out[c][n] = lerp(lerp(q[dc], q[dc + 1], a), lerp(q[dc + CW], q[dc + CW + 1], a), b);
+            }
+        }
+    }
 };
 
 // Parabolic inflow u = up 4 y (ly - y) / ly^2 at fine row J, up the (ramped)
@@ -1038,31 +1057,122 @@ struct PatchWin {
         if (cnt) {
             // 1, 1/2 and 1/4 are exact
             const T inv = cnt == 1 ? T(1) : cnt == 2 ? T(0.5) : cnt == 4 ? T(0.25) : T(1) / T(cnt);
-            u += su * inv;
-            v += sv * inv;
+            u = fma_t(su, inv, u);
+            v = fma_t(sv, inv, v);
+        }
+    }
+    // The same sums for the run of 4 nodes (Ib .. Ib+3, J), Ib a multiple of
+    // 4, on a tile where no node is a Dirichlet node (every node has its four
+    // cells, so the patches it lies in exist) and S >= 4: the run lies in one
+    // patch row, and only its first node can sit on a vertical patch edge.
+    // Patch numbers come straight from the global patch map, so the loads can
+    // be issued before the tile's staging barrier.  Sums are formed in the
+    // order of own_patch + edge_patches (same bits).
+    template <typename T>
+    static __device__ __forceinline__ void run4(const MeshGeom &g, const T *__restrict__ d, int lS, int Ib, int J,
+                                                T (&su)[4], T (&sv)[4], int (&cnt)[4]) {
+        const int S = 1 << lS, S1 = S + 1, nf = g.nf;
+        const int pi = Ib >> lS, pj = J >> lS, li = Ib & (S - 1), lj = J & (S - 1);
+        const int *pm = g.patch_id + (size_t)pj * g.npx + pi;
+        const int id = __ldg(pm);
+        const bool left = li == 0 && pi > 0, below = lj == 0 && pj > 0;
+        const int il = left ? __ldg(pm - 1) : -1, ib = below ? __ldg(pm - g.npx) : -1;
+        const int ibl = left && below ? __ldg(pm - g.npx - 1) : -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            su[q] = sv[q] = T(0);
+            cnt[q] = 0;
+        }
+        if (id >= 0) {
+            const T *p = d + (size_t)id * g.n_out + lj * S1 + li;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                su[q] = __ldg(p + q);
+                sv[q] = __ldg(p + nf + q);
+                cnt[q] = 1;
+            }
+        }
+        if (il >= 0) {   // left patch, its last column
+            const T *p = d + (size_t)il * g.n_out + lj * S1 + S;
+            su[0] += __ldg(p);
+            sv[0] += __ldg(p + nf);
+            ++cnt[0];
+        }
+        if (ib >= 0) {   // lower patch, its last row
+            const T *p = d + (size_t)ib * g.n_out + S * S1 + li;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                su[q] += __ldg(p + q);
+                sv[q] += __ldg(p + nf + q);
+                ++cnt[q];
+            }
+        }
+        if (ibl >= 0) {   // lower-left patch, its last node
+            const T *p = d + (size_t)ibl * g.n_out + S * S1 + S;
+            su[0] += __ldg(p);
+            sv[0] += __ldg(p + nf);
+            ++cnt[0];
         }
     }
 };
 
-// A CTA owns 64 x 16 nodes; lanes take consecutive nodes of a row (so the
+// All-fluid tiles when S >= 4 (no Dirichlet node; every node's patches
+// exist): one 4-node run of one row per thread, with the patch numbers read
+// from the global patch map so that the loads of d are in flight while the
+// coarse window is staged.  Same arithmetic as the general path, same bits.
+template <typename T, int R, typename CWin>
+__device__ __forceinline__ void scatter_fast_tile(const MeshGeom &g, const T *__restrict__ d, const T *__restrict__ xf,
+                                                  const double *__restrict__ xc, T *__restrict__ vc, CWin &cw,
+                                                  int I0, int J0) {
+    static_assert(NTHREADS == (PTX / 4) * PTY, "one run per thread");
+    const int Ib = I0 + 4 * (threadIdx.x & (PTX / 4 - 1)), J = J0 + threadIdx.x / (PTX / 4);
+    const size_t node = (size_t)J * g.pitch + Ib;   // 4-aligned in a 64-aligned row
+    T su[4], sv[4];
+    int cnt[4];
+    PatchWin::run4(g, d, g.K + g.s - 1, Ib, J, su, sv, cnt);
+    T x[2][4];
+    if constexpr (R > 0) {
+        cw.stage(g, xc, I0, J0);
+        __syncthreads();   // publishes the staged coarse nodes
+        cw.interp4(Ib, J, x);
+    } else {
+        load4(xf + node, x[0]);
+        load4(xf + g.plane + node, x[1]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) PatchWin::add_sum(su[q], sv[q], cnt[q], x[0][q], x[1][q]);
+    store4(vc + node, x[0]);
+    store4(vc + g.plane + node, x[1]);
+}
+
+// A CTA owns 64 x 16 nodes.  All-fluid tiles with S >= 4 take
+// scatter_fast_tile; otherwise lanes take consecutive nodes of a row (so the
 // reads of d are contiguous runs of each patch row), each thread 4 rows.
 // R = 0: v~ is read from xf; R = 2, 4, 8: v~ is interpolated from xc inside
-// the tile (S1 fused).
+// the tile (S1 fused).  Registers are capped for the fast tiles' occupancy;
+// the rare general tiles may spill.
 template <typename T, int R>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 4)
 k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, const double *__restrict__ xc,
               double inflow_peak, T *__restrict__ vc) {
     using CWin = CoarseWin<T, (R > 0 ? R : 2), PTX, PTY, 2>;
     __shared__ T cs_mem[R > 0 ? CWin::N : 1];
     __shared__ int pid_s[(PTX / 2 + 2) * (PTY / 2 + 2)];   // S = 2 holds the most patches
-    const int I0 = blockIdx.x * PTX, J0 = blockIdx.y * PTY;
+    // the first and the two last tile rows (walls: general tiles, the slowest)
+    // are scheduled first, so that they do not form the grid's tail
+    const int ny = gridDim.y, by = blockIdx.y < 3 ? (blockIdx.y ? ny - blockIdx.y : 0) : blockIdx.y - 2;
+    const int I0 = blockIdx.x * PTX, J0 = by * PTY;
+    const bool fast = node_tile_fluid(g, blockIdx.x, by);
+    CWin cw;
+    cw.cs = cs_mem;
+    if (fast && g.K + g.s - 1 >= 2) {
+        scatter_fast_tile<T, R>(g, d, xf, xc, vc, cw, I0, J0);
+        return;
+    }
     PatchWin pw;
     pw.pid = pid_s;
     pw.stage(g, I0, I0 + PTX - 1, J0, J0 + PTY - 1);
-    CWin cw;
-    cw.cs = cs_mem;
     if constexpr (R > 0) cw.stage(g, xc, I0, J0);
-    const bool fast = node_tile_fluid(g, blockIdx.x, blockIdx.y);
     const double up = inflow_peak;
     __syncthreads();   // publishes pid_s and the staged coarse nodes
     const int I = I0 + (threadIdx.x & (PTX - 1));
@@ -1798,14 +1908,15 @@ cudaError_t launch_residual_step(const MeshGeom &g, int prec, const FemCoef<doub
 template <typename T>
 cudaError_t run_scatter(const MeshGeom &g, const T *d, const T *xf, const double *xc, double w, T *vc,
                         cudaStream_t st) {
+    const dim3 grid = node_tile_grid(g);
     if (!xc) {
-        k_scatter_avg<T, 0><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc);
+        k_scatter_avg<T, 0><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc);
         return cudaGetLastError();
     }
     switch (g.r) {
-        case 2: k_scatter_avg<T, 2><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
-        case 4: k_scatter_avg<T, 4><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
-        case 8: k_scatter_avg<T, 8><<<node_tile_grid(g), NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
+        case 2: k_scatter_avg<T, 2><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
+        case 4: k_scatter_avg<T, 4><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
+        case 8: k_scatter_avg<T, 8><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
