@@ -314,6 +314,70 @@ int dnnmg_step_timed(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
                      void *workspace, size_t workspace_bytes, double t, cudaEvent_t *events, int n_events,
                      cudaStream_t stream);
 
+/*
+ * ---- Serving: batched steps of many instances ------------------------------
+ *
+ * A server runs Algorithm 2 lines 6-9 for several flow instances at once
+ * (meshes of any size, each with its own GRU state h, all using one net): the
+ * stencil passes run per instance, the network (Eq. gru and the output
+ * layer, Sec. 6.2) runs once over the patches of every instance in the batch
+ * as one tensor-core launch.  The paper runs one instance; batching is this
+ * library's, and an instance's results have the same bits alone (dnnmg_step
+ * with the same inputs and state) and in any batch.
+ *
+ * The server owns, on the device: a state pool of max_rows patch rows (FP32,
+ * net H columns), a feature matrix and an output matrix of max_rows rows, and
+ * scratch for the largest admitted mesh.  dnnmg_server_bytes() gives the pool
+ * and matrix bytes for a budget check.  Instances take segments of the pool in
+ * whole 128-row tiles.  A server is used from one host thread at a time.
+ *
+ * Requires a DNNMG_BF16NET net with the tensor-core kernel (H a multiple of
+ * 32, at most 128); otherwise DNNMG_EUNSUPPORTED.
+ */
+typedef struct dnnmg_server_s *dnnmg_server_t;
+
+/* Device bytes of a server's pool and matrices for max_rows patch rows (0 on a NULL net). */
+size_t dnnmg_server_bytes(dnnmg_net_t net, int max_rows);
+/* Create a server for `net` holding up to max_rows patch rows in total (rounded up to 128). */
+int dnnmg_server_create(dnnmg_net_t net, int max_rows, dnnmg_server_t *out);
+/* Wait for the device, then free everything the server owns (NULL is allowed). */
+int dnnmg_server_destroy(dnnmg_server_t server);
+/*
+ * Admit an instance on `mesh` (DNNMG_BF16NET, n_in / n_out equal to the net's;
+ * the caller keeps the mesh alive until release).  Its state segment, of its
+ * fluid patch count rounded up to 128 rows, starts at h = 0 (Sec. 6.2).
+ * DNNMG_ENOMEM when no free segment is large enough (the pool is the budget).
+ * May synchronise the device (scratch growth).  *slot: the instance's id.
+ */
+int dnnmg_server_admit(dnnmg_server_t server, dnnmg_mesh_t mesh, int *slot);
+/* Synchronise the device, then free the instance's segment; its slot id may be reused. */
+int dnnmg_server_release(dnnmg_server_t server, int slot);
+/* Device pointer to the instance's state rows, [P][H] FP32 (valid until release). */
+int dnnmg_server_state(dnnmg_server_t server, int slot, float **h);
+/*
+ * One step of each of the n distinct instances slots[0..n-1], asynchronous on
+ * `stream`.  Host arrays of device pointers, one entry per instance, with the
+ * meaning of dnnmg_step: xc[i] [3][Nc] FP64 coarse solution, bf[i] the
+ * instance's b_f (read, then overwritten; 16-byte aligned), bc[i] [3][Nc]
+ * FP64 out, t[i] the instance's time t_n.  The state lives in the server.
+ * Calls on one server must be issued on one stream (or ordered by the caller).
+ */
+int dnnmg_server_step(dnnmg_server_t server, int n, const int *slots, const double *const *xc, void *const *bf,
+                      double *const *bc, const double *t, cudaStream_t stream);
+
+/*
+ * Host-only row-range allocator the server uses for its state pool: first fit
+ * over ranges of whole units of `unit` rows, frees coalesce with their free
+ * neighbours.  No GPU needed.  alloc: DNNMG_ENOMEM when no free range holds
+ * the rounded request; free: DNNMG_EINVAL if no allocated range starts there.
+ */
+typedef struct dnnmg_pool_s *dnnmg_pool_t;
+int dnnmg_pool_create(int capacity_rows, int unit, dnnmg_pool_t *out);
+int dnnmg_pool_alloc(dnnmg_pool_t pool, int rows, int *start);
+int dnnmg_pool_free(dnnmg_pool_t pool, int start);
+int dnnmg_pool_stats(dnnmg_pool_t pool, int *used_rows, int *largest_free);
+void dnnmg_pool_destroy(dnnmg_pool_t pool);
+
 /* Last error message of the calling thread ("" if none). */
 const char *dnnmg_last_error(void);
 

@@ -11,10 +11,6 @@
 
 #include "common.cuh"
 
-// Opaque handle types of the C ABI are the internal structures.
-struct dnnmg_mesh_s : dnnmg::Mesh {};
-struct dnnmg_net_s : dnnmg::Net {};
-
 namespace dnnmg {
 
 namespace {

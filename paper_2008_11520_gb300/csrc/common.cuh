@@ -153,6 +153,8 @@ cudaError_t launch_gru(const Net &net, const void *X, void *h, void *d, int P, c
 int gru_launch_count(const Net &net);
 cudaError_t launch_gru_cuda_core(const Net &n, const void *X, void *h, void *d, int P, cudaStream_t st);
 cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, cudaStream_t st);
+cudaError_t launch_gru_tc_rows(const Net &n, const void *X, void *h, void *d, int P, const int *hrow, int h_rows,
+                               cudaStream_t st);
 bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc);
 void tc_release(Net &n);
 // Per feature column: (kind << 24) | offset into the residual / node tiles of stencil.cu.
@@ -167,3 +169,8 @@ int step_on_workspace(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void
                       void *workspace, size_t workspace_bytes, double t, cudaStream_t stream);
 
 }  // namespace dnnmg
+
+// The C-ABI handle types are the library's own structures.
+struct dnnmg_mesh_s : dnnmg::Mesh {};
+struct dnnmg_net_s : dnnmg::Net {};
+

@@ -142,7 +142,8 @@ __device__ __forceinline__ void store_h16(uint8_t *sAh, int row, int c0, const f
 template <int H>
 __global__ void __launch_bounds__(NTH, 1)
 k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap tmX,
-         const __grid_constant__ CUtensorMap tmH, float *__restrict__ h, float *__restrict__ d, int P) {
+         const __grid_constant__ CUtensorMap tmH, float *__restrict__ h, float *__restrict__ d, int P,
+         const int *__restrict__ hrow) {
     constexpr int NH = H / 2;           // state columns per epilogue thread
     extern __shared__ uint8_t smem_raw[];
     // aligned by an offset from the shared-memory symbol itself, so that every
@@ -159,6 +160,9 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p0 = blockIdx.x * TM;
+    // first row of this tile's state: its own rows, or (batched instances) the
+    // tile's rows in a shared state pool
+    const int hp0 = hrow ? __ldg(hrow + blockIdx.x) : p0;
     const uint32_t sX_u = smem_u32(sX), sAh_u = smem_u32(sAh), sW_u = smem_u32(sW);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSTAGE);
     const uint32_t x_full = smem_u32(bars + 2 * NSTAGE), ah_bar = x_full + 8, d1_bar = x_full + 16,
@@ -208,7 +212,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
             expect_tx(x_full, (uint32_t)(p.nxc * CHUNK));
             for (int kc = 0; kc < p.nxc; ++kc) tma_load_2d(sX_u + kc * CHUNK, &tmX, kc * KC, p0, x_full);
             expect_tx(h_full, (uint32_t)(HB * CHUNK));
-            for (int q = 0; q < HB; ++q) tma_load_2d(smem_u32(sH) + q * CHUNK, &tmH, 32 * q, p0, h_full);
+            for (int q = 0; q < HB; ++q) tma_load_2d(smem_u32(sH) + q * CHUNK, &tmH, 32 * q, hp0, h_full);
             int issued = 0;
             uint32_t s = 0, ph = 1;   // ring stage and the parity of its previous release
             for (int i = 0; i < p.nitems; ++i) {
@@ -352,7 +356,7 @@ k_gru_tc(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap
         // named barriers are passed by every epilogue warp, whatever its state
         epilogue_sync();
         if (ok && warp == 2 && lane == 0 && !*abort_flag) {
-            for (int q = 0; q < HB; ++q) tma_store_2d(&tmH, 32 * q, p0, sX_u + q * CHUNK);
+            for (int q = 0; q < HB; ++q) tma_store_2d(&tmH, 32 * q, hp0, sX_u + q * CHUNK);
             bulk_commit();
         }
         if (ok) {
@@ -555,6 +559,13 @@ void tc_release(Net &n) {
 }
 
 cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, cudaStream_t st) {
+    return launch_gru_tc_rows(n, X, h, d, P, nullptr, P, st);
+}
+
+// hrow (device, may be null): per 128-row tile, the first row of its state in
+// h, which then holds h_rows rows (a pool shared by batched instances).
+cudaError_t launch_gru_tc_rows(const Net &n, const void *X, void *h, void *d, int P, const int *hrow, int h_rows,
+                               cudaStream_t st) {
     const TcParams &p = static_cast<const TcNet *>(n.tc)->p;
     // X [P][ldx] bf16: boxes of 64 K-elements x 128 rows, 128-byte swizzle, zero fill outside
     CUtensorMap tm;
@@ -568,7 +579,7 @@ cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, 
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     // h [P][H] fp32: boxes of 32 columns x 128 rows, 128-byte swizzle (load and store)
     CUtensorMap th;
-    const cuuint64_t hdims[2] = {(cuuint64_t)p.H, (cuuint64_t)P};
+    const cuuint64_t hdims[2] = {(cuuint64_t)p.H, (cuuint64_t)h_rows};
     const cuuint64_t hstrides[1] = {(cuuint64_t)p.H * 4};
     const cuuint32_t hbox[2] = {32, (cuuint32_t)TM};
     r = encode_fn()(&th, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h, hdims, hstrides, hbox, estr,
@@ -582,7 +593,7 @@ cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, 
     case HH:                                                                                                 \
         e = cudaFuncSetAttribute(k_gru_tc<HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
         if (e != cudaSuccess) return e;                                                                      \
-        k_gru_tc<HH><<<grid, NTH, smem, st>>>(p, tm, th, (float *)h, (float *)d, P);                         \
+        k_gru_tc<HH><<<grid, NTH, smem, st>>>(p, tm, th, (float *)h, (float *)d, P, hrow);                   \
         break;
     switch (p.H) {
         DNNMG_LAUNCH_H(32)

@@ -84,11 +84,26 @@ def _load():
         "dnnmg_net_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_mesh_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_net_uses_tensor_cores": [P],
+        "dnnmg_server_create": [P, I, ctypes.POINTER(P)],
+        "dnnmg_server_destroy": [P],
+        "dnnmg_server_admit": [P, P, ctypes.POINTER(I)],
+        "dnnmg_server_release": [P, I],
+        "dnnmg_server_state": [P, I, ctypes.POINTER(P)],
+        "dnnmg_server_step": [P, I, ctypes.POINTER(I), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                              ctypes.POINTER(D), P],
+        "dnnmg_pool_create": [I, I, ctypes.POINTER(P)],
+        "dnnmg_pool_alloc": [P, I, ctypes.POINTER(I)],
+        "dnnmg_pool_free": [P, I],
+        "dnnmg_pool_stats": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.dnnmg_server_bytes.argtypes = [P, I]
+    lib.dnnmg_server_bytes.restype = ctypes.c_size_t
+    lib.dnnmg_pool_destroy.argtypes = [P]
+    lib.dnnmg_pool_destroy.restype = None
     lib.dnnmg_static_scratch_bytes.argtypes = []
     lib.dnnmg_static_scratch_bytes.restype = ctypes.c_size_t
     lib.dnnmg_last_error.argtypes = []
@@ -408,3 +423,110 @@ def dnnmg_step_host(mesh, net, xc_host, h, bf, bc_host, workspace, t, stream=Non
 
 def dnnmg_step_launches(mesh, net):
     return _lib.dnnmg_step_launches(mesh.handle, net.handle)
+
+
+# ---------------------------------------------------------------- serving
+class RowPool:
+    """Host-only row-range allocator of the server's state pool (dnnmg_pool_*)."""
+
+    def __init__(self, capacity_rows, unit=128):
+        h = ctypes.c_void_p()
+        _check(_lib.dnnmg_pool_create(int(capacity_rows), int(unit), ctypes.byref(h)))
+        self.handle = h
+
+    def alloc(self, rows):
+        start = ctypes.c_int()
+        _check(_lib.dnnmg_pool_alloc(self.handle, int(rows), ctypes.byref(start)))
+        return start.value
+
+    def free(self, start):
+        _check(_lib.dnnmg_pool_free(self.handle, int(start)))
+
+    def stats(self):
+        used, largest = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.dnnmg_pool_stats(self.handle, ctypes.byref(used), ctypes.byref(largest)))
+        return used.value, largest.value
+
+    def close(self):
+        if self.handle:
+            _lib.dnnmg_pool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dnnmg_server_bytes(net, max_rows):
+    return _lib.dnnmg_server_bytes(net.handle, int(max_rows))
+
+
+class Server:
+    """Owning wrapper of a dnnmg_server_t: batched steps of admitted instances.
+
+    admit(mesh) -> slot; step([(slot, xc, bf, bc, t), ...]) runs one step of
+    each listed instance (S4 as one launch over all of them); state(slot) is
+    the instance's h as a [P][H] tensor view of the server's pool.
+    """
+
+    def __init__(self, net, max_rows):
+        h = ctypes.c_void_p()
+        _check(_lib.dnnmg_server_create(net.handle, int(max_rows), ctypes.byref(h)))
+        self.handle = h
+        self.net = net
+        self.meshes = {}
+
+    def admit(self, mesh):
+        slot = ctypes.c_int()
+        _check(_lib.dnnmg_server_admit(self.handle, mesh.handle, ctypes.byref(slot)))
+        self.meshes[slot.value] = mesh
+        return slot.value
+
+    def release(self, slot):
+        _check(_lib.dnnmg_server_release(self.handle, int(slot)))
+        self.meshes.pop(slot, None)
+
+    def state(self, slot):
+        p = ctypes.c_void_p()
+        _check(_lib.dnnmg_server_state(self.handle, int(slot), ctypes.byref(p)))
+        P, H = self.meshes[slot].info.P, self.net.H
+        if P == 0:
+            return torch.empty(0, H, dtype=torch.float32, device="cuda")
+        return _view_f32(p.value, P * H).view(P, H)
+
+    def step(self, items, stream=None):
+        """items: (slot, xc, bf, bc, t) per instance; xc/bc [3 Nc] FP64, bf [2][plane] FP32."""
+        n = len(items)
+        slots = (ctypes.c_int * n)()
+        xcs, bfs, bcs = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
+        ts = (ctypes.c_double * n)()
+        for i, (slot, xc, bf, bc, t) in enumerate(items):
+            I = self.meshes[slot].info
+            _need(xc, torch.float64, 3 * I.Nc, "xc")
+            _need(bf, torch.float32, 2 * I.plane, "bf")
+            _need(bc, torch.float64, 3 * I.Nc, "bc")
+            slots[i], ts[i] = slot, float(t)
+            xcs[i], bfs[i], bcs[i] = xc.data_ptr(), bf.data_ptr(), bc.data_ptr()
+        _check(_lib.dnnmg_server_step(self.handle, n, slots, xcs, bfs, bcs, ts, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            _lib.dnnmg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _view_f32(addr, numel):
+    """A float32 CUDA tensor over device memory the library owns (no copy)."""
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (numel,), "typestr": "<f4", "data": (addr, False), "version": 2,
+                                    "strides": None}
+    return torch.as_tensor(_Holder(), device="cuda")
+

@@ -14,6 +14,10 @@ nu = 1e-3, k = 0.01, inflow peak 1.5):
               semi-axes 0.05 x U[0.03, 0.05] from the seed; FP32 or BF16 net.
 * ``large``   2048 x 512, K = 2 (8192 x 2048 fine), 2 x 2-cell patches,
               H = 128, BF16 net with FP32 accumulation; ellipse as channel256.
+* serving     64 instances, coarse grids drawn uniformly from 64 x 16 to
+              512 x 128 (nyc = nxc / 4), K in {1, 2}, one-cell patches,
+              ellipse a_x = 0.05 with a_y / a_x ~ U[0.5, 1]; H = 64, BF16
+              net; Poisson step requests at a mean 200 steps/s in total.
 
 The synthetic flow is a Poiseuille profile with its linear pressure drop, plus
 eight Gaussian vortices of amplitude 0.1 * u_max whose positions, radii and
@@ -149,3 +153,27 @@ def hidden_state(P, H, seed, scale=0.5):
     """A random GRU state [P][H] in (-scale, scale) for parity tests."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-scale, scale, (P, H))
+
+
+def serving_instances(n, seed):
+    """n instance descriptions of the serving workload (see the module docstring)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nxc = int(rng.integers(64 // 16, 512 // 16 + 1)) * 16
+        K = int(rng.integers(1, 3))
+        ratio = float(rng.uniform(0.5, 1.0))
+        out.append(dict(nxc=nxc, nyc=nxc // 4, K=K, s=1, ellipse=(0.2, 0.2, 0.05, 0.05 * ratio),
+                        seed=int(rng.integers(0, 2 ** 31 - 1))))
+    return out
+
+
+def poisson_requests(rate, duration, n_instances, seed):
+    """Step requests of a Poisson process of `rate` per second over `duration`
+    seconds, each for an instance drawn uniformly: (arrival times [s], instance
+    indices), sorted by time."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.poisson(rate * duration))
+    t = np.sort(rng.uniform(0.0, duration, n))
+    return t, rng.integers(0, n_instances, n)
+
