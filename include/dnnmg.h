@@ -360,7 +360,11 @@ int dnnmg_server_state(dnnmg_server_t server, int slot, float **h);
  * meaning of dnnmg_step: xc[i] [3][Nc] FP64 coarse solution, bf[i] the
  * instance's b_f (read, then overwritten; 16-byte aligned), bc[i] [3][Nc]
  * FP64 out, t[i] the instance's time t_n.  The state lives in the server.
- * Calls on one server must be issued on one stream (or ordered by the caller).
+ * The per-instance passes run on the server's 8 side streams (round robin),
+ * forked from `stream` and joined back into it before and after S4, so the
+ * call is ordered on `stream` like a single kernel sequence (and can be
+ * captured into a graph from it).  Calls on one server must be issued on one
+ * stream (or ordered by the caller).
  */
 int dnnmg_server_step(dnnmg_server_t server, int n, const int *slots, const double *const *xc, void *const *bf,
                       double *const *bc, const double *t, cudaStream_t stream);

@@ -10,7 +10,10 @@
 // and batch rows are whole 128-row tiles, so every GRU tile belongs to one
 // instance; a per-tile table gives the tile's first state row in the pool.
 // A patch row's arithmetic does not depend on the other rows of its tile, so
-// an instance gets the same bits alone (dnnmg_step) and in any batch.
+// an instance gets the same bits alone (dnnmg_step) and in any batch.  The
+// per-instance passes of up to kLanes instances run side by side on the
+// server's own streams (small meshes fill few SMs each), each stream with its
+// own scratch; the caller's stream forks to them and joins back around S4.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -23,6 +26,7 @@ namespace dnnmg {
 namespace {
 
 constexpr int kTileRows = 128;   // rows of one GRU tile
+constexpr int kLanes = 8;        // side streams: the per-instance passes of up to 8 instances overlap
 
 // First-fit allocator of row ranges in units of `unit` rows; frees coalesce.
 struct RowPool {
@@ -104,7 +108,11 @@ struct dnnmg_server_s {
     int *tiles_host[2] = {nullptr, nullptr};   // pinned staging, used in turn
     cudaEvent_t tiles_ev[2] = {nullptr, nullptr};
     int flip = 0;
-    void *scratch = nullptr;  // v_corr and the padded x_c of the largest admitted mesh
+    // per side stream: v_corr and the padded x_c of the largest admitted mesh
+    cudaStream_t lane[dnnmg::kLanes] = {};
+    cudaEvent_t lane_done[dnnmg::kLanes] = {};
+    cudaEvent_t fork = nullptr;
+    void *scratch[dnnmg::kLanes] = {};
     size_t scratch_bytes = 0;
     struct Slot {
         dnnmg_mesh_t mesh;
@@ -128,7 +136,12 @@ void server_free(dnnmg_server_s *s) {
     cudaFree(s->X);
     cudaFree(s->d);
     cudaFree(s->tiles_dev);
-    cudaFree(s->scratch);
+    for (int j = 0; j < kLanes; ++j) {
+        cudaFree(s->scratch[j]);
+        if (s->lane[j]) cudaStreamDestroy(s->lane[j]);
+        if (s->lane_done[j]) cudaEventDestroy(s->lane_done[j]);
+    }
+    if (s->fork) cudaEventDestroy(s->fork);
     for (int b = 0; b < 2; ++b) {
         if (s->tiles_host[b]) cudaFreeHost(s->tiles_host[b]);
         if (s->tiles_ev[b]) cudaEventDestroy(s->tiles_ev[b]);
@@ -227,6 +240,10 @@ int dnnmg_server_create(dnnmg_net_t net, int max_rows, dnnmg_server_t *out) {
     for (int b = 0; ok && b < 2; ++b)
         ok = cudaMallocHost(&s->tiles_host[b], ntiles * sizeof(int)) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->tiles_ev[b], cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; ok && j < kLanes; ++j)
+        ok = cudaStreamCreateWithFlags(&s->lane[j], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->lane_done[j], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) == cudaSuccess;
     // feature rows past an instance's patches are read by its last GRU tile:
     // keep them finite (their results land only in the instance's padding)
     ok = ok && cudaMemset(s->X, 0, rows * net->ldx * 2) == cudaSuccess;
@@ -269,15 +286,18 @@ int dnnmg_server_admit(dnnmg_server_t s, dnnmg_mesh_t mesh, int *slot) {
     if (need > s->scratch_bytes) {
         // the scratch may be in use by steps in flight
         cudaError_t e = cudaDeviceSynchronize();
-        void *p = nullptr;
-        if (e == cudaSuccess) e = cudaMalloc(&p, need);
+        void *p[kLanes] = {};
+        for (int j = 0; e == cudaSuccess && j < kLanes; ++j) e = cudaMalloc(&p[j], need);
         if (e != cudaSuccess) {
+            for (int j = 0; j < kLanes; ++j) cudaFree(p[j]);
             if (rows > 0) s->pool.release(start);
             cudaGetLastError();
-            return fail(DNNMG_ENOMEM, "scratch of %zu bytes: %s", need, cudaGetErrorString(e));
+            return fail(DNNMG_ENOMEM, "scratch of %d x %zu bytes: %s", kLanes, need, cudaGetErrorString(e));
         }
-        cudaFree(s->scratch);
-        s->scratch = p;
+        for (int j = 0; j < kLanes; ++j) {
+            cudaFree(s->scratch[j]);
+            s->scratch[j] = p[j];
+        }
         s->scratch_bytes = need;
     }
     // h0 = 0 (Sec. 6.2), padding rows included
@@ -353,29 +373,50 @@ int dnnmg_server_step(dnnmg_server_t s, int n, const int *slots, const double *c
                                        cudaMemcpyHostToDevice, stream));
         DNNMG_CUDA_TRY(cudaEventRecord(s->tiles_ev[b], stream));
     }
-    char *vc = static_cast<char *>(s->scratch);
+    // the per-instance passes go round-robin to the side streams, which fork
+    // from and join back into the caller's stream around each phase
+    const int nl = n < kLanes ? n : kLanes;
+    auto fork = [&]() -> int {
+        DNNMG_CUDA_TRY(cudaEventRecord(s->fork, stream));
+        for (int j = 0; j < nl; ++j) DNNMG_CUDA_TRY(cudaStreamWaitEvent(s->lane[j], s->fork, 0));
+        return DNNMG_OK;
+    };
+    auto join = [&]() -> int {
+        for (int j = 0; j < nl; ++j) {
+            DNNMG_CUDA_TRY(cudaEventRecord(s->lane_done[j], s->lane[j]));
+            DNNMG_CUDA_TRY(cudaStreamWaitEvent(stream, s->lane_done[j], 0));
+        }
+        return DNNMG_OK;
+    };
     uint16_t *X = static_cast<uint16_t *>(s->X);
     // S1 + S2 + S3 per instance, into its rows of X
+    if (int e = fork()) return e;
     for (int i = 0; i < n; ++i) {
         const dnnmg_mesh_s &m = *s->slots[slots[i]].mesh;
         const dnnmg_mesh_info &I = m.info;
-        void *xcp = vc + align256(2 * (size_t)I.plane * I.real_bytes);
-        DNNMG_CUDA_TRY(launch_coarse_pad(m.g, I.precision, xc[i], xcp, stream));
+        cudaStream_t st = s->lane[i % kLanes];
+        void *xcp = static_cast<char *>(s->scratch[i % kLanes]) + align256(2 * (size_t)I.plane * I.real_bytes);
+        DNNMG_CUDA_TRY(launch_coarse_pad(m.g, I.precision, xc[i], xcp, st));
         DNNMG_CUDA_TRY(launch_residual_step(m.g, I.precision, m.fem64, m.fem32, xcp, t[i], bf[i],
-                                            X + (size_t)row0[i] * net.ldx, stream));
+                                            X + (size_t)row0[i] * net.ldx, st));
     }
+    if (int e = join()) return e;
     // S4 once over every instance's rows
     if (total > 0)
         DNNMG_CUDA_TRY(launch_gru_tc_rows(net, s->X, s->hpool, s->d, total, s->tiles_dev, s->cap_rows, stream));
     // S5, S6, S7 per instance, from its rows of d
+    if (int e = fork()) return e;
     for (int i = 0; i < n; ++i) {
         const dnnmg_mesh_s &m = *s->slots[slots[i]].mesh;
         const dnnmg_mesh_info &I = m.info;
+        cudaStream_t st = s->lane[i % kLanes];
+        void *vc = s->scratch[i % kLanes];
         const float *d = s->d + (size_t)row0[i] * net.n_out;
-        DNNMG_CUDA_TRY(launch_scatter_avg(m.g, I.precision, d, nullptr, xc[i], t[i], vc, stream));
-        DNNMG_CUDA_TRY(launch_rhs(m.g, I.precision, m.fem64, m.fem32, vc, bf[i], stream));
-        DNNMG_CUDA_TRY(launch_restrict(m.g, I.precision, bf[i], bc[i], stream));
+        DNNMG_CUDA_TRY(launch_scatter_avg(m.g, I.precision, d, nullptr, xc[i], t[i], vc, st));
+        DNNMG_CUDA_TRY(launch_rhs(m.g, I.precision, m.fem64, m.fem32, vc, bf[i], st));
+        DNNMG_CUDA_TRY(launch_restrict(m.g, I.precision, bf[i], bc[i], st));
     }
+    if (int e = join()) return e;
     return DNNMG_OK;
 }
 

@@ -154,8 +154,8 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--instances", type=int, default=64)
-    ap.add_argument("--rate", type=float, default=200.0, help="offered step requests per second")
-    ap.add_argument("--duration", type=float, default=5.0, help="seconds of arrivals")
+    ap.add_argument("--rates", default="200,2000,8000", help="offered step requests per second, one run each")
+    ap.add_argument("--duration", type=float, default=3.0, help="seconds of arrivals per run")
     ap.add_argument("--budget-gb", type=float, default=8.0, help="device memory for admitted instances")
     ap.add_argument("--max-rows", type=int, default=None, help="cap on one server batch's patch rows")
     ap.add_argument("--H", type=int, default=64)
@@ -166,8 +166,9 @@ def main(argv=None):
     specs, infos, servers, inst, group_of, rows_of, admitted = _gpu_setup(
         args.instances, args.seed, args.H, int(args.budget_gb * 2 ** 30))
     k = synth.DT
+    adm = sorted(inst)
 
-    def execute(batch):
+    def launch(batch, inst_of):
         for g, reqs in batch.items():
             items = []
             for r in reqs:
@@ -175,61 +176,69 @@ def main(argv=None):
                 items.append((s["slot"], s["xc"], s["bf"], s["bc"], s["t"]))
                 s["t"] += k
             servers[g].step(items)
+
+    every = np.array(adm)
+    full = Batcher(every, group_of, rows_of).take(deque(range(len(adm))))
+    launch(full, every)   # warm-up: every admitted instance once
+    torch.cuda.synchronize()
+
+    runs = []
+    for rate in (float(x) for x in args.rates.split(",")):
+        arrival, which = synth.poisson_requests(rate, args.duration, len(adm), args.seed)
+        inst_of = every[which]
+        t0 = time.perf_counter()
+        clock = lambda: time.perf_counter() - t0
+
+        def wait_until(t):
+            while clock() < t:
+                pass
+
+        def execute(batch):
+            launch(batch, inst_of)
+            torch.cuda.synchronize()
+
+        latency, sizes = run_loop(arrival, Batcher(inst_of, group_of, rows_of, args.max_rows), execute, clock,
+                                  wait_until)
+        wall = clock()
+        lat_ms = latency * 1e3
+        runs.append({"offered_steps_per_s": rate, "requests": int(len(arrival)),
+                     "served_steps_per_s": len(arrival) / wall,
+                     "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                     "mean_ms": float(lat_ms.mean()), "mean_batch": float(np.mean(sizes)), "batches": len(sizes)})
+
+    # saturated: every admitted instance in every round, as one batch per
+    # server, against the same steps issued one instance per call
+    def timed(rounds, per_round):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(rounds):
+            per_round()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / rounds
 
-    # warm-up: every admitted instance once, as one batch per server
-    adm = sorted(inst)
-    inst_of = np.array(adm)
-    execute(Batcher(inst_of, group_of, rows_of).take(deque(range(len(adm)))))
-
-    # offered load: Poisson arrivals over the admitted instances
-    arrival, which = synth.poisson_requests(args.rate, args.duration, len(adm), args.seed)
-    inst_of = np.array(adm)[which]
-    t0 = time.perf_counter()
-    clock = lambda: time.perf_counter() - t0
-
-    def wait_until(t):
-        while clock() < t:
-            pass
-
-    latency, sizes = run_loop(arrival, Batcher(inst_of, group_of, rows_of, args.max_rows), execute, clock,
-                              wait_until)
-    wall = clock()
-
-    # saturated: every admitted instance in every batch
-    inst_of = np.array(adm)
-    full = Batcher(inst_of, group_of, rows_of).take(deque(range(len(adm))))
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record()
-    for _ in range(args.sat_iters):
-        for g, reqs in full.items():
-            items = []
-            for r in reqs:
-                s = inst[inst_of[r]]
-                items.append((s["slot"], s["xc"], s["bf"], s["bc"], s["t"]))
-                s["t"] += k
-            servers[g].step(items)
-    ev1.record()
-    torch.cuda.synchronize()
-    sat_s = ev0.elapsed_time(ev1) / 1e3
+    singles = [{g: [r]} for g, reqs in full.items() for r in reqs]
+    batched_s = timed(args.sat_iters, lambda: launch(full, every))
+    single_s = timed(args.sat_iters, lambda: [launch(b, every) for b in singles])
     dof = sum(inst[i]["dof"] for i in adm)
     for s in inst.values():
         assert torch.isfinite(s["bc"]).all()
-    lat_ms = np.sort(latency) * 1e3
+    first = runs[0]
     line = {
         "metric": "serving step latency", "unit": "ms",
-        "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-        "mean_ms": float(lat_ms.mean()), "requests": int(len(arrival)),
-        "offered_steps_per_s": args.rate, "served_steps_per_s": len(arrival) / wall,
-        "mean_batch": float(np.mean(sizes)), "batches": len(sizes),
+        "p50_ms": first["p50_ms"], "p99_ms": first["p99_ms"], "offered_steps_per_s": first["offered_steps_per_s"],
+        "loads": runs,
         "instances": args.instances, "admitted": len(adm), "budget_gb": args.budget_gb,
         "servers": {f"n_in={g[0]},n_out={g[1]}": sum(1 for i in adm if group_of[i] == g) for g in servers},
-        "saturated": {"steps_per_s": len(adm) * args.sat_iters / sat_s,
-                      "fine_dof_per_s": dof * args.sat_iters / sat_s,
-                      "ms_per_round": sat_s * 1e3 / args.sat_iters},
-        "workload": "serving: %d instances, coarse 64x16..512x128, K in {1,2}, H=%d, BF16 net, Poisson %g/s"
-                    % (args.instances, args.H, args.rate),
+        "fine_dof_per_round": dof,
+        "saturated": {"batched": {"steps_per_s": len(adm) / batched_s, "fine_dof_per_s": dof / batched_s,
+                                  "ms_per_round": batched_s * 1e3},
+                      "one_instance_per_call": {"steps_per_s": len(adm) / single_s,
+                                                "fine_dof_per_s": dof / single_s,
+                                                "ms_per_round": single_s * 1e3}},
+        "workload": "serving: %d instances, coarse 64x16..512x128, K in {1,2}, H=%d, BF16 net, Poisson arrivals"
+                    % (args.instances, args.H),
         "data": "synthetic",
     }
     print(json.dumps(line))
