@@ -382,6 +382,51 @@ int dnnmg_pool_free(dnnmg_pool_t pool, int start);
 int dnnmg_pool_stats(dnnmg_pool_t pool, int *used_rows, int *largest_free);
 void dnnmg_pool_destroy(dnnmg_pool_t pool);
 
+/*
+ * ---- Training the patch network (GRU + output layer) -----------------------
+ *
+ * Forward and backward of Eq. gru followed by the output layer (Sec. 6.2),
+ * unrolled over a window of T steps of P patch rows, for truncated
+ * backpropagation through time; the l2 loss of Sec. 6.5 and its gradient;
+ * Adam with the Tikhonov term of Sec. 6.5.  FP32 throughout (CUDA cores);
+ * weight-gradient sums are split over the T P rows in a fixed order, so
+ * results repeat bit for bit.  All arrays are caller-owned device memory:
+ *   X [T][P][ldx] (columns n_in..ldx-1 ignored), h0 / dh0 [P][H],
+ *   Wx / gWx [3H][n_in], Uh / gUh [3H][H] (gates z, r, h), Wfc / gWfc [n_out][H],
+ *   D / dD [T][P][n_out].
+ * A trainer owns the activations of one window (about T P (12 H) floats) and
+ * serves one forward/backward pair at a time.
+ */
+typedef struct dnnmg_trainer_s *dnnmg_trainer_t;
+int dnnmg_trainer_create(int n_in, int ldx, int H, int n_out, int T, int P, dnnmg_trainer_t *out);
+/* Wait for the device, then free the trainer (NULL is allowed). */
+int dnnmg_trainer_destroy(dnnmg_trainer_t trainer);
+/* D = outputs of the T steps from state h0 (NULL: h0 = 0); keeps the activations for the backward. */
+int dnnmg_gru_seq_forward(dnnmg_trainer_t trainer, const float *X, const float *h0, const float *Wx, const float *Uh,
+                          const float *Wfc, float *D, cudaStream_t stream);
+/* Device pointer to h_T of the last forward (the next window's h0), [P][H]. */
+int dnnmg_gru_seq_state(dnnmg_trainer_t trainer, float **hT);
+/*
+ * Gradients of sum(dD * D) over the last forward's window with respect to the
+ * weights (written, not accumulated) and, if dh0 is not NULL, to h0.  X, Uh
+ * and Wfc must be the arrays of that forward.
+ */
+int dnnmg_gru_seq_backward(dnnmg_trainer_t trainer, const float *dD, const float *X, const float *Uh, const float *Wfc,
+                           float *gWx, float *gUh, float *gWfc, float *dh0, cudaStream_t stream);
+/*
+ * Loss of Sec. 6.5 over n = T P n_out outputs: *loss (device double) =
+ * sum (D - Y)^2 / P, and dD = 2 (D - Y) / P if dD is not NULL.
+ */
+int dnnmg_l2_loss(const float *D, const float *Y, long long n, int P, float *dD, double *loss, cudaStream_t stream);
+/* *out (device double) = sum of x^2 (the Tikhonov term divided by alpha). */
+int dnnmg_sumsq(const float *x, long long n, double *out, cudaStream_t stream);
+/*
+ * One Adam update (step >= 1) of n parameters p with gradient g + 2 alpha p
+ * (alpha: Tikhonov factor) and moments m, v (start at 0).
+ */
+int dnnmg_adam_step(float *p, const float *g, float *m, float *v, long long n, int step, float lr, float beta1,
+                    float beta2, float eps, float alpha, cudaStream_t stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char *dnnmg_last_error(void);
 

@@ -1,0 +1,448 @@
+// Training the patch network (Eq. gru + output layer, Sec. 6.2 and 6.5):
+// the GRU unrolled over a window of T steps, and its gradient by truncated
+// backpropagation through time, in FP32 on the CUDA cores.
+//
+// Every product of the network is a matrix product over the patch rows, so a
+// window is a short sequence of GEMMs and fused pointwise kernels:
+//   forward   GX = X W_x^T for all steps at once; per step t
+//             GH = h_{t-1} [U_z; U_r]^T, gates (z, r, r*h), AH = (r*h) U_h^T,
+//             candidate and new state; then D = H W_fc^T for all steps.
+//   backward  dH = dD W_fc for all steps; per step t (last first) the gate
+//             gradients and the carried state gradient; then each weight
+//             gradient is one product over all steps and patches
+//             (K = T P), split over K in a fixed order, so results repeat
+//             bit for bit.
+// The trainer handle owns the saved activations of one window.
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "common.cuh"
+
+namespace dnnmg {
+namespace {
+
+// ---------------------------------------------------------------- GEMM
+// C[M][N] (row stride ldc) = op(A) op(B), or += when accumulate.
+//   TA false: A is [M][K] (lda);  TA true: A is stored [K][M] (lda).
+//   TB false: B is [K][N] (ldb);  TB true: B is stored [N][K] (ldb).
+// 64 x 64 tiles, K in steps of 16, 256 threads with 4 x 4 outputs each.
+// blockIdx.z takes K range [z kchunk, (z+1) kchunk) and writes its partial
+// result to C + z cstride (split K; reduced by k_reduce_splits).
+constexpr int GBM = 64, GBN = 64, GBK = 16, GTH = 256;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(GTH) k_sgemm(int M, int N, int K, const float *__restrict__ A, int lda,
+                                              const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
+                                              int accumulate, int kchunk, long long cstride) {
+    __shared__ __align__(16) float As[GBK][GBM + 4];
+    __shared__ __align__(16) float Bs[GBK][GBN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    float acc[4][4] = {};
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = tid + i * GTH;   // 0 .. 1023
+            int m, k;
+            if (TA) { k = idx >> 6; m = idx & 63; }   // coalesced along m
+            else    { m = idx >> 4; k = idx & 15; }   // coalesced along k
+            const int gm = m0 + m, gk = k0 + k;
+            As[k][m] = (gm < M && gk < ke) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.0f;
+            int n, kk;
+            if (TB) { n = idx >> 4; kk = idx & 15; }
+            else    { kk = idx >> 6; n = idx & 63; }
+            const int gn = n0 + n, gkk = k0 + kk;
+            Bs[kk][n] = (gn < N && gkk < ke) ? (TB ? B[(size_t)gn * ldb + gkk] : B[(size_t)gkk * ldb + gn]) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GBK; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float *Cz = C + (size_t)blockIdx.z * cstride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty * 4 + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx * 4 + j;
+            if (gn >= N) continue;
+            float *c = Cz + (size_t)gm * ldc + gn;
+            *c = accumulate ? *c + acc[i][j] : acc[i][j];
+        }
+    }
+}
+
+// C[m][n] (=|+=) the sum over s = 0 .. splits-1, in that order, of part[s][m][n].
+__global__ void k_reduce_splits(int M, int N, int splits, const float *__restrict__ part, float *__restrict__ C,
+                                int ldc, int accumulate) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)M * N) return;
+    const int m = (int)(e / N), n = (int)(e - (long long)m * N);
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * M * N + e];
+    float *c = C + (size_t)m * ldc + n;
+    *c = accumulate ? *c + s : s;
+}
+
+template <bool TA, bool TB>
+cudaError_t gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                 bool accumulate, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, 1);
+    k_sgemm<TA, TB><<<grid, GTH, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0, K > 0 ? K : 1, 0);
+    return cudaGetLastError();
+}
+
+// op(A) op(B) with K split into `splits` ranges; part holds splits x M x N floats.
+template <bool TA, bool TB>
+cudaError_t gemm_splitk(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                        int splits, float *part, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
+    const int sz = (K + kchunk - 1) / kchunk;
+    const dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, sz);
+    k_sgemm<TA, TB><<<grid, GTH, 0, st>>>(M, N, K, A, lda, B, ldb, part, N, 0, kchunk, (long long)M * N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)M * N;
+    k_reduce_splits<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, N, sz, part, C, ldc, 0);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// ---------------------------------------------------------------- pointwise
+// z, r and r * h_{t-1} from the input part GX [P][3H] and the recurrent part GH [P][2H].
+__global__ void k_gates_fwd(int P, int H, const float *__restrict__ GX, const float *__restrict__ GH,
+                            const float *__restrict__ hp, float *__restrict__ z, float *__restrict__ r,
+                            float *__restrict__ rh) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)P * H) return;
+    const int p = (int)(e / H), j = (int)(e - (long long)p * H);
+    const float zz = sigm(GX[(size_t)p * 3 * H + j] + GH[(size_t)p * 2 * H + j]);
+    const float rr = sigm(GX[(size_t)p * 3 * H + H + j] + GH[(size_t)p * 2 * H + H + j]);
+    z[e] = zz;
+    r[e] = rr;
+    rh[e] = rr * hp[e];
+}
+
+// c = tanh(W_h x + U_h (r h)) and h_t = z h_{t-1} + (1 - z) c.
+__global__ void k_cand_fwd(int P, int H, const float *__restrict__ GX, const float *__restrict__ AH,
+                           const float *__restrict__ z, const float *__restrict__ hp, float *__restrict__ c,
+                           float *__restrict__ h) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)P * H) return;
+    const int p = (int)(e / H), j = (int)(e - (long long)p * H);
+    const float cc = tanhf(GX[(size_t)p * 3 * H + 2 * H + j] + AH[e]);
+    const float zz = z[e];
+    c[e] = cc;
+    h[e] = zz * hp[e] + (1.0f - zz) * cc;
+}
+
+// Backward through the state update of step t: dh = dHfc + carry is the
+// gradient reaching h_t; writes the gradients of the z and candidate
+// pre-activations into dG [P][3H] (columns 0..H-1 and 2H..3H-1) and keeps dh.
+__global__ void k_bwd_state(int P, int H, const float *__restrict__ dHfc, const float *__restrict__ carry,
+                            const float *__restrict__ z, const float *__restrict__ c, const float *__restrict__ hp,
+                            float *__restrict__ dG, float *__restrict__ dh_out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)P * H) return;
+    const int p = (int)(e / H), j = (int)(e - (long long)p * H);
+    const float dh = dHfc[e] + carry[e];
+    const float zz = z[e], cc = c[e];
+    const float dc = dh * (1.0f - zz);
+    const float dz = dh * (hp[e] - cc);
+    dG[(size_t)p * 3 * H + j] = dz * zz * (1.0f - zz);
+    dG[(size_t)p * 3 * H + 2 * H + j] = dc * (1.0f - cc * cc);
+    dh_out[e] = dh;
+}
+
+// Backward through the reset gate: drh = d(r h_{t-1}); the r pre-activation
+// gradient into dG columns H..2H-1, and the part of the carried gradient that
+// does not pass through U_z, U_r: dh z + drh r.
+__global__ void k_bwd_reset(int P, int H, const float *__restrict__ drh, const float *__restrict__ hp,
+                            const float *__restrict__ r, const float *__restrict__ z, const float *__restrict__ dh,
+                            float *__restrict__ dG, float *__restrict__ carry) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)P * H) return;
+    const int p = (int)(e / H), j = (int)(e - (long long)p * H);
+    const float rr = r[e], g = drh[e];
+    dG[(size_t)p * 3 * H + H + j] = g * hp[e] * rr * (1.0f - rr);
+    carry[e] = dh[e] * z[e] + g * rr;
+}
+
+// ---------------------------------------------------------------- loss, Adam
+// dD = 2 (D - Y) / P and per-block partial sums of (D - Y)^2 / P (FP64).
+__global__ void k_l2_loss(long long n, int P, const float *__restrict__ D, const float *__restrict__ Y,
+                          float *__restrict__ dD, double *__restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double diff = (double)D[e] - (double)Y[e];   // exact for FP32 inputs
+        if (dD) dD[e] = (float)(2.0 * diff / P);
+        s += diff * diff;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0] / P;
+}
+
+// Sum of squares of x, as per-block partials (FP64).
+__global__ void k_sumsq(long long n, const float *__restrict__ x, double *__restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        s += (double)x[e] * x[e];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// out = sum of part[0 .. n-1], in order (one thread).
+__global__ void k_sum_parts(int n, const double *__restrict__ part, double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+}
+
+// Adam with the Tikhonov term: g' = g + 2 alpha p; bias corrections c1 = 1 - b1^s, c2 = 1 - b2^s.
+__global__ void k_adam(long long n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, float lr, float b1, float b2, float eps, float alpha, float c1,
+                       float c2) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float pe = p[e];
+    const float ge = g[e] + 2.0f * alpha * pe;
+    const float me = b1 * m[e] + (1.0f - b1) * ge;
+    const float ve = b2 * v[e] + (1.0f - b2) * ge * ge;
+    m[e] = me;
+    v[e] = ve;
+    p[e] = pe - lr * (me / c1) / (sqrtf(ve / c2) + eps);
+}
+
+constexpr int kRedBlocks = 512;
+
+unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+}  // namespace dnnmg
+
+struct dnnmg_trainer_s {
+    int n_in, ldx, H, n_out, T, P, device;
+    // saved activations of the last forward window
+    float *GX;      // [T P][3H]
+    float *hs;      // [(T+1) P][H]: h_0 .. h_T
+    float *z, *r, *rh, *c;   // [T P][H] each
+    // scratch
+    float *GH;      // [P][2H]
+    float *AH;      // [P][H]
+    float *dHfc;    // [T P][H]
+    float *dG;      // [T P][3H]
+    float *dh, *drh, *carry;   // [P][H]
+    float *part;    // split-K partials
+    size_t part_floats;
+    double *red;    // reduction partials [kRedBlocks]
+    int splits;
+};
+
+namespace dnnmg {
+namespace {
+
+void trainer_free(dnnmg_trainer_s *t) {
+    if (!t) return;
+    float *bufs[] = {t->GX, t->hs, t->z, t->r, t->rh, t->c, t->GH, t->AH, t->dHfc, t->dG, t->dh, t->drh, t->carry,
+                     t->part};
+    for (float *b : bufs) cudaFree(b);
+    cudaFree(t->red);
+    delete t;
+}
+
+int check_trainer(dnnmg_trainer_s *t) {
+    if (!t) return fail(DNNMG_EINVAL, "trainer handle is NULL");
+    int cur = -1;
+    DNNMG_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != t->device) return fail(DNNMG_EINVAL, "trainer belongs to device %d but device %d is current", t->device, cur);
+    return DNNMG_OK;
+}
+
+}  // namespace
+}  // namespace dnnmg
+
+using namespace dnnmg;
+
+extern "C" {
+
+int dnnmg_trainer_create(int n_in, int ldx, int H, int n_out, int T, int P, dnnmg_trainer_t *out) {
+    clear_error();
+    if (!out) return fail(DNNMG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_in < 1 || ldx < n_in || H < 1 || n_out < 1 || T < 1 || P < 1)
+        return fail(DNNMG_EINVAL, "n_in %d, ldx %d, H %d, n_out %d, T %d, P %d", n_in, ldx, H, n_out, T, P);
+    if ((long long)T * P * 3 * H > (1LL << 31) - 1) return fail(DNNMG_EINVAL, "window too large (T P 3H >= 2^31)");
+    dnnmg_trainer_s *t = new (std::nothrow) dnnmg_trainer_s();
+    if (!t) return fail(DNNMG_ENOMEM, "host allocation failed");
+    *t = dnnmg_trainer_s{};
+    t->n_in = n_in; t->ldx = ldx; t->H = H; t->n_out = n_out; t->T = T; t->P = P;
+    DNNMG_CUDA_TRY(cudaGetDevice(&t->device));
+    const size_t TP = (size_t)T * P;
+    // split the weight-gradient products over K = T P in ranges of about 4096 rows
+    t->splits = (int)std::min<size_t>(256, std::max<size_t>(1, TP / 4096));
+    const size_t mx = (size_t)std::max(3 * H, n_out) * std::max(std::max(n_in, H), 1);
+    t->part_floats = (size_t)t->splits * mx;
+    struct { float **p; size_t n; } req[] = {
+        {&t->GX, TP * 3 * H}, {&t->hs, (TP + P) * H}, {&t->z, TP * H}, {&t->r, TP * H}, {&t->rh, TP * H},
+        {&t->c, TP * H}, {&t->GH, (size_t)P * 2 * H}, {&t->AH, (size_t)P * H}, {&t->dHfc, TP * H},
+        {&t->dG, TP * 3 * H}, {&t->dh, (size_t)P * H}, {&t->drh, (size_t)P * H}, {&t->carry, (size_t)P * H},
+        {&t->part, t->part_floats}};
+    bool ok = true;
+    for (auto &q : req) ok = ok && cudaMalloc(q.p, q.n * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&t->red, kRedBlocks * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        trainer_free(t);
+        cudaGetLastError();
+        return fail(DNNMG_ENOMEM, "device allocation of the training window (T %d, P %d, H %d) failed", T, P, H);
+    }
+    *out = t;
+    return DNNMG_OK;
+}
+
+int dnnmg_trainer_destroy(dnnmg_trainer_t t) {
+    clear_error();
+    if (!t) return DNNMG_OK;
+    cudaDeviceSynchronize();
+    trainer_free(t);
+    return DNNMG_OK;
+}
+
+int dnnmg_gru_seq_forward(dnnmg_trainer_t t, const float *X, const float *h0, const float *Wx, const float *Uh,
+                          const float *Wfc, float *D, cudaStream_t st) {
+    clear_error();
+    if (int e = check_trainer(t)) return e;
+    if (!X || !Wx || !Uh || !Wfc || !D) return fail(DNNMG_EINVAL, "NULL array");
+    const int H = t->H, P = t->P, T = t->T;
+    const size_t PH = (size_t)P * H;
+    const int TP = T * P;
+    // h_0 (zero when h0 is NULL)
+    if (h0) DNNMG_CUDA_TRY(cudaMemcpyAsync(t->hs, h0, PH * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else DNNMG_CUDA_TRY(cudaMemsetAsync(t->hs, 0, PH * sizeof(float), st));
+    // input parts of every gate, all steps: GX = X W_x^T
+    DNNMG_CUDA_TRY((gemm<false, true>(TP, 3 * H, t->n_in, X, t->ldx, Wx, t->n_in, t->GX, 3 * H, false, st)));
+    for (int s = 0; s < T; ++s) {
+        const float *hp = t->hs + (size_t)s * PH;
+        const float *GX = t->GX + (size_t)s * P * 3 * H;
+        float *z = t->z + (size_t)s * PH, *r = t->r + (size_t)s * PH, *rh = t->rh + (size_t)s * PH;
+        float *c = t->c + (size_t)s * PH, *h = t->hs + (size_t)(s + 1) * PH;
+        DNNMG_CUDA_TRY((gemm<false, true>(P, 2 * H, H, hp, H, Uh, H, t->GH, 2 * H, false, st)));
+        k_gates_fwd<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, GX, t->GH, hp, z, r, rh);
+        DNNMG_CUDA_TRY(cudaGetLastError());
+        DNNMG_CUDA_TRY((gemm<false, true>(P, H, H, rh, H, Uh + (size_t)2 * H * H, H, t->AH, H, false, st)));
+        k_cand_fwd<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, GX, t->AH, z, hp, c, h);
+        DNNMG_CUDA_TRY(cudaGetLastError());
+    }
+    // outputs of every step: D = [h_1 .. h_T] W_fc^T
+    DNNMG_CUDA_TRY((gemm<false, true>(TP, t->n_out, H, t->hs + PH, H, Wfc, H, D, t->n_out, false, st)));
+    return DNNMG_OK;
+}
+
+int dnnmg_gru_seq_state(dnnmg_trainer_t t, float **hT) {
+    clear_error();
+    if (!t || !hT) return fail(DNNMG_EINVAL, "NULL argument");
+    *hT = t->hs + (size_t)t->T * t->P * t->H;
+    return DNNMG_OK;
+}
+
+int dnnmg_gru_seq_backward(dnnmg_trainer_t t, const float *dD, const float *X, const float *Uh, const float *Wfc,
+                           float *gWx, float *gUh, float *gWfc, float *dh0, cudaStream_t st) {
+    clear_error();
+    if (int e = check_trainer(t)) return e;
+    if (!dD || !X || !Uh || !Wfc || !gWx || !gUh || !gWfc) return fail(DNNMG_EINVAL, "NULL array");
+    const int H = t->H, P = t->P, T = t->T, n_out = t->n_out, n_in = t->n_in;
+    const size_t PH = (size_t)P * H;
+    const int TP = T * P;
+    // gradient reaching each h_t from its own output: dD W_fc, all steps
+    DNNMG_CUDA_TRY((gemm<false, false>(TP, H, n_out, dD, n_out, Wfc, H, t->dHfc, H, false, st)));
+    DNNMG_CUDA_TRY(cudaMemsetAsync(t->carry, 0, PH * sizeof(float), st));
+    for (int s = T - 1; s >= 0; --s) {
+        const float *hp = t->hs + (size_t)s * PH;
+        const float *z = t->z + (size_t)s * PH, *r = t->r + (size_t)s * PH, *c = t->c + (size_t)s * PH;
+        float *dG = t->dG + (size_t)s * P * 3 * H;
+        k_bwd_state<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, t->dHfc + (size_t)s * PH, t->carry, z, c, hp,
+                                                                dG, t->dh);
+        DNNMG_CUDA_TRY(cudaGetLastError());
+        // d(r h_{t-1}) = dA_c U_h
+        DNNMG_CUDA_TRY((gemm<false, false>(P, H, H, dG + 2 * H, 3 * H, Uh + (size_t)2 * H * H, H, t->drh, H, false,
+                                           st)));
+        k_bwd_reset<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, t->drh, hp, r, z, t->dh, dG, t->carry);
+        DNNMG_CUDA_TRY(cudaGetLastError());
+        // carry += [dA_z, dA_r] [U_z; U_r]
+        DNNMG_CUDA_TRY((gemm<false, false>(P, H, 2 * H, dG, 3 * H, Uh, H, t->carry, H, true, st)));
+    }
+    if (dh0) DNNMG_CUDA_TRY(cudaMemcpyAsync(dh0, t->carry, PH * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    // weight gradients: products over all steps and patches
+    DNNMG_CUDA_TRY((gemm_splitk<true, false>(3 * H, n_in, TP, t->dG, 3 * H, X, t->ldx, gWx, n_in, t->splits,
+                                              t->part, st)));
+    DNNMG_CUDA_TRY((gemm_splitk<true, false>(2 * H, H, TP, t->dG, 3 * H, t->hs, H, gUh, H, t->splits, t->part,
+                                              st)));
+    DNNMG_CUDA_TRY((gemm_splitk<true, false>(H, H, TP, t->dG + 2 * H, 3 * H, t->rh, H, gUh + (size_t)2 * H * H, H,
+                                              t->splits, t->part, st)));
+    DNNMG_CUDA_TRY((gemm_splitk<true, false>(n_out, H, TP, dD, n_out, t->hs + PH, H, gWfc, H, t->splits, t->part,
+                                              st)));
+    return DNNMG_OK;
+}
+
+int dnnmg_l2_loss(const float *D, const float *Y, long long n, int P, float *dD, double *loss, cudaStream_t st) {
+    clear_error();
+    if (!D || !Y || !loss || n < 0 || P < 1) return fail(DNNMG_EINVAL, "bad argument");
+    double *part = nullptr;
+    DNNMG_CUDA_TRY(cudaMallocAsync(&part, kRedBlocks * sizeof(double), st));
+    k_l2_loss<<<kRedBlocks, 256, 0, st>>>(n, P, D, Y, dD, part);
+    k_sum_parts<<<1, 32, 0, st>>>(kRedBlocks, part, loss);
+    DNNMG_CUDA_TRY(cudaGetLastError());
+    DNNMG_CUDA_TRY(cudaFreeAsync(part, st));
+    return DNNMG_OK;
+}
+
+int dnnmg_sumsq(const float *x, long long n, double *out, cudaStream_t st) {
+    clear_error();
+    if (!x || !out || n < 0) return fail(DNNMG_EINVAL, "bad argument");
+    double *part = nullptr;
+    DNNMG_CUDA_TRY(cudaMallocAsync(&part, kRedBlocks * sizeof(double), st));
+    k_sumsq<<<kRedBlocks, 256, 0, st>>>(n, x, part);
+    k_sum_parts<<<1, 32, 0, st>>>(kRedBlocks, part, out);
+    DNNMG_CUDA_TRY(cudaGetLastError());
+    DNNMG_CUDA_TRY(cudaFreeAsync(part, st));
+    return DNNMG_OK;
+}
+
+int dnnmg_adam_step(float *p, const float *g, float *m, float *v, long long n, int step, float lr, float b1,
+                    float b2, float eps, float alpha, cudaStream_t st) {
+    clear_error();
+    if (!p || !g || !m || !v || n < 0 || step < 1) return fail(DNNMG_EINVAL, "bad argument");
+    const float c1 = (float)(1.0 - std::pow((double)b1, step)), c2 = (float)(1.0 - std::pow((double)b2, step));
+    if (n > 0) k_adam<<<blocks_for(n), 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, alpha, c1, c2);
+    DNNMG_CUDA_TRY(cudaGetLastError());
+    return DNNMG_OK;
+}
+
+}  // extern "C"

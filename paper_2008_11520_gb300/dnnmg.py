@@ -95,6 +95,15 @@ def _load():
         "dnnmg_pool_alloc": [P, I, ctypes.POINTER(I)],
         "dnnmg_pool_free": [P, I],
         "dnnmg_pool_stats": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
+        "dnnmg_trainer_create": [I, I, I, I, I, I, ctypes.POINTER(P)],
+        "dnnmg_trainer_destroy": [P],
+        "dnnmg_gru_seq_forward": [P, P, P, P, P, P, P, P],
+        "dnnmg_gru_seq_state": [P, ctypes.POINTER(P)],
+        "dnnmg_gru_seq_backward": [P, P, P, P, P, P, P, P, P, P],
+        "dnnmg_l2_loss": [P, P, ctypes.c_longlong, I, P, P, P],
+        "dnnmg_sumsq": [P, ctypes.c_longlong, P, P],
+        "dnnmg_adam_step": [P, P, P, P, ctypes.c_longlong, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, ctypes.c_float, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -529,4 +538,81 @@ def _view_f32(addr, numel):
         __cuda_array_interface__ = {"shape": (numel,), "typestr": "<f4", "data": (addr, False), "version": 2,
                                     "strides": None}
     return torch.as_tensor(_Holder(), device="cuda")
+
+
+# ---------------------------------------------------------------- training
+class Trainer:
+    """Owning wrapper of a dnnmg_trainer_t: the activations of one window of
+    T steps of P patch rows (FP32), for dnnmg_gru_seq_forward / _backward."""
+
+    def __init__(self, n_in, ldx, H, n_out, T, P):
+        h = ctypes.c_void_p()
+        _check(_lib.dnnmg_trainer_create(n_in, ldx, H, n_out, T, P, ctypes.byref(h)))
+        self.handle = h
+        self.n_in, self.ldx, self.H, self.n_out, self.T, self.P = n_in, ldx, H, n_out, T, P
+
+    def close(self):
+        if self.handle:
+            _lib.dnnmg_trainer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _weights(self, Wx, Uh, Wfc):
+        _need(Wx, torch.float32, 3 * self.H * self.n_in, "Wx")
+        _need(Uh, torch.float32, 3 * self.H * self.H, "Uh")
+        _need(Wfc, torch.float32, self.n_out * self.H, "Wfc")
+
+    def forward(self, X, h0, Wx, Uh, Wfc, D, stream=None):
+        _need(X, torch.float32, self.T * self.P * self.ldx, "X")
+        if h0 is not None:
+            _need(h0, torch.float32, self.P * self.H, "h0")
+        self._weights(Wx, Uh, Wfc)
+        _need(D, torch.float32, self.T * self.P * self.n_out, "D")
+        _check(_lib.dnnmg_gru_seq_forward(self.handle, _ptr(X), _ptr(h0), _ptr(Wx), _ptr(Uh), _ptr(Wfc), _ptr(D),
+                                          _stream(stream)))
+
+    def state(self):
+        """h_T of the last forward as a [P][H] view (valid until the next forward)."""
+        p = ctypes.c_void_p()
+        _check(_lib.dnnmg_gru_seq_state(self.handle, ctypes.byref(p)))
+        return _view_f32(p.value, self.P * self.H).view(self.P, self.H)
+
+    def backward(self, dD, X, Uh, Wfc, gWx, gUh, gWfc, dh0=None, stream=None):
+        _need(dD, torch.float32, self.T * self.P * self.n_out, "dD")
+        _need(X, torch.float32, self.T * self.P * self.ldx, "X")
+        for name, g, W in (("gWx", gWx, 3 * self.H * self.n_in), ("gUh", gUh, 3 * self.H * self.H),
+                           ("gWfc", gWfc, self.n_out * self.H)):
+            _need(g, torch.float32, W, name)
+        if dh0 is not None:
+            _need(dh0, torch.float32, self.P * self.H, "dh0")
+        _check(_lib.dnnmg_gru_seq_backward(self.handle, _ptr(dD), _ptr(X), _ptr(Uh), _ptr(Wfc), _ptr(gWx),
+                                           _ptr(gUh), _ptr(gWfc), _ptr(dh0), _stream(stream)))
+
+
+def dnnmg_l2_loss(D, Y, P, dD=None, stream=None):
+    """Loss of Sec. 6.5 (device double tensor of one element) and, optionally, dD."""
+    _need(Y, torch.float32, D.numel(), "Y")
+    if dD is not None:
+        _need(dD, torch.float32, D.numel(), "dD")
+    out = torch.empty(1, dtype=torch.float64, device=D.device)
+    _check(_lib.dnnmg_l2_loss(_ptr(D), _ptr(Y), D.numel(), int(P), _ptr(dD), _ptr(out), _stream(stream)))
+    return out
+
+
+def dnnmg_sumsq(x, stream=None):
+    out = torch.empty(1, dtype=torch.float64, device=x.device)
+    _check(_lib.dnnmg_sumsq(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
+    return out
+
+
+def dnnmg_adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, alpha=0.0, stream=None):
+    for name, t in (("g", g), ("m", m), ("v", v)):
+        _need(t, torch.float32, p.numel(), name)
+    _check(_lib.dnnmg_adam_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step), lr, beta1, beta2, eps,
+                                alpha, _stream(stream)))
 
