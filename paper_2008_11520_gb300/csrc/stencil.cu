@@ -396,6 +396,9 @@ struct ResLayout {
     static constexpr int UN = LC > MAXCS ? LC : MAXCS;
     static constexpr int MAXP = (TXC / 2) * (TYC / 2);         // patches of a tile (S = 2)
     static constexpr int NBX = TXC / 2 + 1, NBY = TYC / 2 + 1, NB = NBX * NBY;   // 2x2 node blocks
+    // node residuals of a fast tile in the feature type: [3][NYN][RXP] (the
+    // feature table's residual offsets use this layout from a patch's origin)
+    static constexpr int RXP = NXN + 1, RPL = NYN * RXP;
     static constexpr int MAX_LDX = 1024;                       // feature columns supported
     template <typename T> static constexpr size_t bytes() {
         return sizeof(T) * (XS + BS + CC + UN) + sizeof(int) * MAXP + FX * FY;
@@ -504,6 +507,25 @@ __device__ __forceinline__ void put_block(const MeshGeom &g, TX *__restrict__ X,
                 }
 }
 
+// Two adjacent feature values at an even column (4-byte aligned for BF16).
+template <typename TX> __device__ __forceinline__ void put_pair(TX *p, TX a, TX b) {
+    p[0] = a;
+    p[1] = b;
+}
+template <> __device__ __forceinline__ void put_pair<__nv_bfloat16>(__nv_bfloat16 *p, __nv_bfloat16 a,
+                                                                   __nv_bfloat16 b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(a, b);
+}
+
+// Two adjacent feature values (p even-aligned), converted to the feature type.
+template <typename TX, typename T> __device__ __forceinline__ void store_pair(TX *p, T a, T b) {
+    p[0] = store_as<TX, T>(a);
+    p[1] = store_as<TX, T>(b);
+}
+template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float>(__nv_bfloat16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+
 __device__ __forceinline__ void store2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
 __device__ __forceinline__ void store2(double *p, double a, double b) {
     *reinterpret_cast<double2 *>(p) = make_double2(a, b);
@@ -531,7 +553,7 @@ template <typename T, typename TX>
 __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<T> &fc, const T *xs,
                                                const T *bs, const T *cc, const int *pid, int tpx, int tpy,
                                                int lS, int I0, int J0, int bx, int by, T *__restrict__ rf,
-                                               TX *__restrict__ X) {
+                                               TX *__restrict__ X, TX *rres) {
     using L = ResLayout;
     T Au[2][2], Av[2][2], Ap[2][2];   // [dy][dx]: velocity rows and pressure row of A(x~) x~
 #pragma unroll
@@ -624,6 +646,18 @@ __device__ __forceinline__ void block_residual(const MeshGeom &g, const FemCoef<
             store2(rf + 2 * g.plane + node, rp[dy][0], rp[dy][1]);
         }
     }
+    if (rres) {
+        // the tile's node residuals, once each (the feature pass gathers the rows)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            if (dy == 1 && !yin) continue;
+            const int e = (2 * by + dy) * L::RXP + 2 * bx;   // even: aligned pairs (column 33 is padding)
+            store_pair(rres + e, ru[dy][0], ru[dy][1]);
+            store_pair(rres + L::RPL + e, rv[dy][0], rv[dy][1]);
+            store_pair(rres + 2 * L::RPL + e, rp[dy][0], rp[dy][1]);
+        }
+        return;
+    }
     put_block(g, X, pid, tpx, tpy, lS, bx, by, ru, rv, rp);
 }
 
@@ -688,6 +722,40 @@ __device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T
             }
         }
     };
+    // Every feature row of a fast tile, residual columns gathered from the
+    // tile's node residuals rres: one warp per patch, lanes on pairs of
+    // consecutive columns (coalesced 2-element stores).
+    auto patch_rows = [&](const TX *rres) {
+        const int S = 1 << lS, nw = (int)(blockDim.x >> 5);
+        const int warp = (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+        for (int tp = warp; tp < tpx * tpy; tp += nw) {
+            const int id = pid[tp];
+            if (id < 0) continue;
+            const int lpy = tp >> (5 - lS), lpx = tp & (tpx - 1);
+            const T *xbase = xs + lpy * S * L::HX + lpx * S;
+            const TX *rbase = rres + lpy * S * L::RXP + lpx * S;
+            TX *row = X + (size_t)id * g.ldx;
+            for (int c = 2 * lane; c < g.ldx; c += 64) {
+                const int2 ee = __ldg(reinterpret_cast<const int2 *>(g.feat_tab + c));
+                TX out[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int e = k ? ee.y : ee.x;
+                    const int kind = e >> 24, off = e & 0xFFFFFF;
+                    if (kind == FEAT_RES) {
+                        out[k] = rbase[off];
+                    } else {
+                        const int o = kind <= FEAT_PECLET ? off : 0;
+                        const T a = xbase[o], b = xbase[o + L::HP];
+                        T val = kind == FEAT_VEL ? a : (kind == FEAT_GEO ? geo_s[off < 12 ? off : 0] : T(0));
+                        if (kind == FEAT_PECLET) val = fc.q_over_nu * sqrt(a * a + b * b);
+                        out[k] = store_as<TX, T>(val);
+                    }
+                }
+                put_pair(row + c, out[0], out[1]);
+            }
+        }
+    };
 
     if (fast) {
         // convection contributions of every cell around the tile's nodes,
@@ -719,6 +787,13 @@ __device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T
             }
         }
         __syncthreads();
+        // Node residuals in the feature type fit in the LPS / coarse-window
+        // buffer that fast tiles no longer need when the features are BF16:
+        // each node's residual is then written once and the rows gathered
+        // afterwards.  Otherwise every node is written into each patch row
+        // that holds it while idle warps write the other columns.
+        constexpr bool kGather = 3 * L::RPL * sizeof(TX) <= L::LC * sizeof(T);
+        TX *rres = kGather ? reinterpret_cast<TX *>(un) : nullptr;
         // 16 blocks of one row per half-warp (contiguous pairs: conflict-free
         // 64-bit loads), then the last block column
         constexpr int BW = (L::NB + 31) / 32;   // warps of the block pass
@@ -726,9 +801,13 @@ __device__ __forceinline__ void residual_tile(const MeshGeom &g, const FemCoef<T
             const int t = threadIdx.x;
             const bool main = t < 16 * L::NBY;
             const int bx = main ? (t & 15) : L::NBX - 1, by = main ? (t >> 4) : t - 16 * L::NBY;
-            block_residual(g, fc, xs, bs, cc, pid, tpx, tpy, lS, I0, J0, bx, by, rf, X);
-        } else if (threadIdx.x >= 32 * BW) {
+            block_residual(g, fc, xs, bs, cc, pid, tpx, tpy, lS, I0, J0, bx, by, rf, X, rres);
+        } else if (!kGather && threadIdx.x >= 32 * BW) {
             patch_inputs(BW, (int)(blockDim.x >> 5) - BW);
+        }
+        if constexpr (kGather) {
+            __syncthreads();
+            patch_rows(rres);
         }
         return;
     }
@@ -1754,7 +1833,7 @@ void feature_table(const MeshGeom &g, int *tab) {
     int c = 0;
     for (int comp = 0; comp < 3; ++comp)
         for (int b = 0; b < S1; ++b)
-            for (int a = 0; a < S1; ++a) tab[c++] = (FEAT_RES << 24) | (comp * NYN * NXN + b * NXN + a);
+            for (int a = 0; a < S1; ++a) tab[c++] = (FEAT_RES << 24) | (comp * L::RPL + b * L::RXP + a);
     for (int comp = 0; comp < 3; ++comp)
         for (int b = 0; b < s1; ++b)
             for (int a = 0; a < s1; ++a) {
