@@ -18,10 +18,35 @@ CASES = {
     "k3_f64": dict(nxc=12, nyc=6, K=3, s=1, H=8, prec="f64", ellipse=(0.5, 0.2, 0.2, 0.1)),
     "k2s2_f32_channel": dict(nxc=20, nyc=6, K=2, s=2, H=8, prec="f32", ellipse=None),
     "k1s2_f64_mask": dict(nxc=24, nyc=8, K=1, s=2, H=8, prec="f64", ellipse=None, mask_seed=3),
+    # geometries of Sec. 6.7 as coarse-cell masks: two obstacles centred at
+    # (0.2, 0.18) and (0.6, 0.24) with axes 0.11 x 0.09 (the printed "1.1" and
+    # "0.9" read as 0.11 and 0.09), and an L-shaped channel (the upper half of
+    # the right half solid)
+    "two_obstacles_bf16": dict(nxc=64, nyc=12, K=2, s=1, H=32, prec="bf16", ellipse=None, geometry="two"),
+    "lshape_f32": dict(nxc=40, nyc=10, K=1, s=2, H=16, prec="f32", ellipse=None, geometry="L"),
 }
 
 
+def geometry_mask(case):
+    """Coarse solid mask [nyc][nxc] of a named geometry (cell centroids)."""
+    nxc, nyc = case["nxc"], case["nyc"]
+    hx, hy = 2.2 / nxc, 0.41 / nyc
+    x = (np.arange(nxc) + 0.5) * hx
+    y = (np.arange(nyc) + 0.5) * hy
+    X, Y = np.meshgrid(x, y)
+    if case["geometry"] == "two":
+        m = np.zeros((nyc, nxc), dtype=bool)
+        for cx, cy in ((0.2, 0.18), (0.6, 0.24)):
+            m |= ((X - cx) / 0.055) ** 2 + ((Y - cy) / 0.045) ** 2 < 1.0
+        return m
+    if case["geometry"] == "L":
+        return (X > 1.1) & (Y > 0.205)
+    raise ValueError(case["geometry"])
+
+
 def mask_for(case):
+    if "geometry" in case:
+        return geometry_mask(case)
     if "mask_seed" not in case:
         return None
     rng = np.random.default_rng(case["mask_seed"])
