@@ -26,53 +26,95 @@ namespace {
 // C[M][N] (row stride ldc) = op(A) op(B), or += when accumulate.
 //   TA false: A is [M][K] (lda);  TA true: A is stored [K][M] (lda).
 //   TB false: B is [K][N] (ldb);  TB true: B is stored [N][K] (ldb).
-// 64 x 64 tiles, K in steps of 16, 256 threads with 4 x 4 outputs each.
-// blockIdx.z takes K range [z kchunk, (z+1) kchunk) and writes its partial
-// result to C + z cstride (split K; reduced by k_reduce_splits).
-constexpr int GBM = 64, GBN = 64, GBK = 16, GTH = 256;
+// 128 x 64 tiles, K in steps of 16, 256 threads with 8 x 4 outputs each; the
+// next K step is read into registers while the current one is multiplied
+// out of the other half of a double buffer.  blockIdx.z takes K range
+// [z kchunk, (z+1) kchunk) and writes its partial result to C + z cstride
+// (split K; reduced by k_reduce_splits).
+constexpr int GBM = 128, GBN = 64, GBK = 16, GTH = 256;
+constexpr int GA = GBM * GBK / GTH, GB = GBN * GBK / GTH;   // elements each thread stages per step
 
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(GTH) k_sgemm(int M, int N, int K, const float *__restrict__ A, int lda,
                                               const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
                                               int accumulate, int kchunk, long long cstride) {
-    __shared__ __align__(16) float As[GBK][GBM + 4];
-    __shared__ __align__(16) float Bs[GBK][GBN + 4];
+    __shared__ __align__(16) float As[2][GBK][GBM + 4];
+    __shared__ __align__(16) float Bs[2][GBK][GBN + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    float acc[4][4] = {};
-    for (int k0 = kb; k0 < ke; k0 += GBK) {
+    float ra[GA], rb[GB];
+    // the (m, k) / (k, n) element each staged value belongs to (coalesced along
+    // the stored fastest dimension)
+    auto a_at = [&](int i, int &m, int &k) {
+        const int idx = tid + i * GTH;
+        if (TA) { k = idx / GBM; m = idx % GBM; }
+        else    { m = idx / GBK; k = idx % GBK; }
+    };
+    auto b_at = [&](int i, int &n, int &k) {
+        const int idx = tid + i * GTH;
+        if (TB) { n = idx / GBK; k = idx % GBK; }
+        else    { k = idx / GBN; n = idx % GBN; }
+    };
+    auto fetch = [&](int k0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int idx = tid + i * GTH;   // 0 .. 1023
+        for (int i = 0; i < GA; ++i) {
             int m, k;
-            if (TA) { k = idx >> 6; m = idx & 63; }   // coalesced along m
-            else    { m = idx >> 4; k = idx & 15; }   // coalesced along k
+            a_at(i, m, k);
             const int gm = m0 + m, gk = k0 + k;
-            As[k][m] = (gm < M && gk < ke) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.0f;
-            int n, kk;
-            if (TB) { n = idx >> 4; kk = idx & 15; }
-            else    { kk = idx >> 6; n = idx & 63; }
-            const int gn = n0 + n, gkk = k0 + kk;
-            Bs[kk][n] = (gn < N && gkk < ke) ? (TB ? B[(size_t)gn * ldb + gkk] : B[(size_t)gkk * ldb + gn]) : 0.0f;
+            ra[i] = (gm < M && gk < ke) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.0f;
         }
-        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < GB; ++i) {
+            int n, k;
+            b_at(i, n, k);
+            const int gn = n0 + n, gk = k0 + k;
+            rb[i] = (gn < N && gk < ke) ? (TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : 0.0f;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < GA; ++i) {
+            int m, k;
+            a_at(i, m, k);
+            As[buf][k][m] = ra[i];
+        }
+#pragma unroll
+        for (int i = 0; i < GB; ++i) {
+            int n, k;
+            b_at(i, n, k);
+            Bs[buf][k][n] = rb[i];
+        }
+    };
+    float acc[8][4] = {};
+    int buf = 0;
+    if (kb < ke) {
+        fetch(kb);
+        stash(0);
+    }
+    __syncthreads();
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
+        const bool more = k0 + GBK < ke;
+        if (more) fetch(k0 + GBK);
 #pragma unroll
         for (int k = 0; k < GBK; ++k) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
-            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8 + 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
+        if (more) stash(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
     float *Cz = C + (size_t)blockIdx.z * cstride;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + ty * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+        const int gm = m0 + ty * 8 + i;
         if (gm >= M) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -184,15 +226,16 @@ __global__ void k_bwd_reset(int P, int H, const float *__restrict__ drh, const f
 }
 
 // ---------------------------------------------------------------- loss, Adam
-// dD = 2 (D - Y) / P and per-block partial sums of (D - Y)^2 / P (FP64).
-__global__ void k_l2_loss(long long n, int P, const float *__restrict__ D, const float *__restrict__ Y,
-                          float *__restrict__ dD, double *__restrict__ part) {
+// dD = 2 (D - Y) / P (FP32) and per-block partial sums of (D - Y)^2 / P,
+// accumulated in FP64.
+__global__ void k_l2_loss(long long n, int P, float two_over_p, const float *__restrict__ D,
+                          const float *__restrict__ Y, float *__restrict__ dD, double *__restrict__ part) {
     __shared__ double red[256];
     double s = 0.0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const double diff = (double)D[e] - (double)Y[e];   // exact for FP32 inputs
-        if (dD) dD[e] = (float)(2.0 * diff / P);
-        s += diff * diff;
+        const float diff = D[e] - Y[e];
+        if (dD) dD[e] = diff * two_over_p;
+        s += (double)(diff * diff);
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -218,12 +261,17 @@ __global__ void k_sumsq(long long n, const float *__restrict__ x, double *__rest
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// out = sum of part[0 .. n-1], in order (one thread).
+// out = sum of part[0 .. n-1] (n <= 512) by a fixed tree in one block of 256 threads.
 __global__ void k_sum_parts(int n, const double *__restrict__ part, double *__restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
+    __shared__ double red[256];
+    const int t = threadIdx.x;
+    red[t] = (t < n ? part[t] : 0.0) + (t + 256 < n ? part[t + 256] : 0.0);
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) *out = red[0];
 }
 
 // Adam with the Tikhonov term: g' = g + 2 alpha p; bias corrections c1 = 1 - b1^s, c2 = 1 - b2^s.
@@ -416,8 +464,8 @@ int dnnmg_l2_loss(const float *D, const float *Y, long long n, int P, float *dD,
     if (!D || !Y || !loss || n < 0 || P < 1) return fail(DNNMG_EINVAL, "bad argument");
     double *part = nullptr;
     DNNMG_CUDA_TRY(cudaMallocAsync(&part, kRedBlocks * sizeof(double), st));
-    k_l2_loss<<<kRedBlocks, 256, 0, st>>>(n, P, D, Y, dD, part);
-    k_sum_parts<<<1, 32, 0, st>>>(kRedBlocks, part, loss);
+    k_l2_loss<<<kRedBlocks, 256, 0, st>>>(n, P, (float)(2.0 / P), D, Y, dD, part);
+    k_sum_parts<<<1, 256, 0, st>>>(kRedBlocks, part, loss);
     DNNMG_CUDA_TRY(cudaGetLastError());
     DNNMG_CUDA_TRY(cudaFreeAsync(part, st));
     return DNNMG_OK;
@@ -429,7 +477,7 @@ int dnnmg_sumsq(const float *x, long long n, double *out, cudaStream_t st) {
     double *part = nullptr;
     DNNMG_CUDA_TRY(cudaMallocAsync(&part, kRedBlocks * sizeof(double), st));
     k_sumsq<<<kRedBlocks, 256, 0, st>>>(n, x, part);
-    k_sum_parts<<<1, 32, 0, st>>>(kRedBlocks, part, out);
+    k_sum_parts<<<1, 256, 0, st>>>(kRedBlocks, part, out);
     DNNMG_CUDA_TRY(cudaGetLastError());
     DNNMG_CUDA_TRY(cudaFreeAsync(part, st));
     return DNNMG_OK;

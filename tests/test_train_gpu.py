@@ -84,7 +84,8 @@ def test_zero_state_and_loss_kernel(dn):
     torch.cuda.synchronize()
     Dn = D.cpu().numpy().astype(np.float64)
     assert rel_l2(Dn, Do) <= TOL
-    assert L.item() == pytest.approx(otrain.loss(Dn, Y, Wx, Uh, Wfc, alpha=0.0), rel=1e-12)
+    # FP32 differences and squares, FP64 sums
+    assert L.item() == pytest.approx(otrain.loss(Dn, Y, Wx, Uh, Wfc, alpha=0.0), rel=1e-6)
     assert rel_l2(dD.cpu().numpy(), otrain.loss_grad_D(Dn, Y)) <= 1e-6
     s = dn.dnnmg_sumsq(cu(Wx))
     assert s.item() == pytest.approx(float(np.sum(Wx ** 2)), rel=1e-12)
