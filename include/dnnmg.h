@@ -427,6 +427,17 @@ int dnnmg_sumsq(const float *x, long long n, double *out, cudaStream_t stream);
 int dnnmg_adam_step(float *p, const float *g, float *m, float *v, long long n, int step, float lr, float beta1,
                     float beta2, float eps, float alpha, cudaStream_t stream);
 
+/*
+ * Self-test of the bounded waits (synchronous; no counterpart in the paper).
+ * One block of 64 threads waits on an mbarrier phase that nothing completes:
+ * thread 0 gives up after limit_ns (1 ns .. 1 s), sets DNNMG_DEVERR_TIMEOUT
+ * in a device status word and the CTA's abort flag; the other threads (limit
+ * 2 s) must leave through the flag.  *status: the status word read back;
+ * waited_ns[0]: thread 0's wait, waited_ns[1]: the last thread's.  Nothing
+ * is left in flight, so the context stays usable.
+ */
+int dnnmg_selftest_wait_timeout(long long limit_ns, int *status, long long *waited_ns);
+
 /* Last error message of the calling thread ("" if none). */
 const char *dnnmg_last_error(void);
 

@@ -48,15 +48,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait on an mbarrier phase; false (abort flag set) on time-out or
-// when another thread has aborted.
-__device__ __noinline__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+// Bounded wait on an mbarrier phase; false (abort flag set) on time-out
+// (limit_ns) or when another thread has aborted.
+__device__ __noinline__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                              unsigned long long limit_ns = kWaitNs) {
     const unsigned long long t0 = now_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 255) == 255) {
             if (*abort_flag) return false;
-            if (now_ns() - t0 > kWaitNs) {
+            if (now_ns() - t0 > limit_ns) {
                 *abort_flag = 1;
                 return false;
             }

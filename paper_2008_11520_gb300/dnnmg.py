@@ -102,6 +102,7 @@ def _load():
         "dnnmg_gru_seq_backward": [P, P, P, P, P, P, P, P, P, P],
         "dnnmg_l2_loss": [P, P, ctypes.c_longlong, I, P, P, P],
         "dnnmg_sumsq": [P, ctypes.c_longlong, P, P],
+        "dnnmg_selftest_wait_timeout": [ctypes.c_longlong, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)],
         "dnnmg_adam_step": [P, P, P, P, ctypes.c_longlong, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             ctypes.c_float, ctypes.c_float, P],
     }
@@ -615,4 +616,12 @@ def dnnmg_adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
         _need(t, torch.float32, p.numel(), name)
     _check(_lib.dnnmg_adam_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step), lr, beta1, beta2, eps,
                                 alpha, _stream(stream)))
+
+
+def dnnmg_selftest_wait_timeout(limit_ns):
+    """Run the bounded-wait self-test; returns (status word, [thread 0 wait ns, last thread wait ns])."""
+    st = ctypes.c_int()
+    w = (ctypes.c_longlong * 2)()
+    _check(_lib.dnnmg_selftest_wait_timeout(int(limit_ns), ctypes.byref(st), w))
+    return st.value, [w[0], w[1]]
 

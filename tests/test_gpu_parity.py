@@ -278,6 +278,21 @@ def test_step_leaves_mesh_status_clear(dn):
     assert dn.dnnmg_net_status(net) == 0
 
 
+def test_bounded_wait_times_out_and_context_survives(dn):
+    # a wait that nothing satisfies gives up after its limit, reports the
+    # time-out in the status word and releases the CTA's other waiters
+    limit = 20_000_000   # 20 ms
+    status, waited = dn.dnnmg_selftest_wait_timeout(limit)
+    assert status == 1                                 # DNNMG_DEVERR_TIMEOUT
+    assert limit <= waited[0] < limit + 200_000_000
+    assert 0 < waited[1] < limit + 200_000_000         # left through the abort flag, not its own 2 s limit
+    with pytest.raises(dn.DnnmgError):
+        dn.dnnmg_selftest_wait_timeout(0)
+    # the context is still usable: a step afterwards is clean and correct
+    errs = run_steps(dn, CASES["k2_f32"], 1)
+    assert max(errs[0].values()) <= TOL["f32"]
+
+
 def test_step_timed_matches_step(dn):
     # the instrumented step records one event per kernel and computes the same bits
     case = CASES["k2s2_bf16"]
