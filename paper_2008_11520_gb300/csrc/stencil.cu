@@ -985,14 +985,18 @@ k_residual_features(MeshGeom g, FemCoef<T> fc, const T *__restrict__ xf, const d
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
 k_coarse_pad(MeshGeom g, const double *__restrict__ xc, T *__restrict__ xcp, int pc) {
-    const size_t nc1 = (size_t)g.nxc + 1;
-    const int rows = 3 * (g.nyc + 1);
-    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
-        const int c = row / (g.nyc + 1), j = row - c * (g.nyc + 1);
-        const double *src = xc + ((size_t)c * (g.nyc + 1) + j) * nc1;
-        T *dst = xcp + (size_t)row * pc;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pc; i += gridDim.x * blockDim.x)
-            dst[i] = i < (int)nc1 ? (T)__ldg(src + i) : T(0);
+    // four consecutive outputs of one padded row per thread (pc is a multiple
+    // of 32, so they never straddle rows and leave as one aligned store)
+    const int nc1 = g.nxc + 1, quads = pc / 4;
+    const long long nq = 3LL * (g.nyc + 1) * quads;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += (long long)gridDim.x * blockDim.x) {
+        const long long row = e / quads;
+        const int i = (int)(e - row * quads) * 4;
+        const double *src = xc + row * nc1;   // rows of [3][nyc+1][nxc+1] are consecutive
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = i + k < nc1 ? (T)__ldg(src + i + k) : T(0);
+        store4(xcp + row * pc + i, v);
     }
 }
 
@@ -1927,8 +1931,10 @@ int coarse_pitch(const MeshGeom &g) { return round_up(g.nxc + 1, 32); }
 
 template <typename T>
 cudaError_t run_coarse_pad(const MeshGeom &g, const double *xc, T *xcp, cudaStream_t st) {
-    const int pc = coarse_pitch(g), rows = 3 * (g.nyc + 1);
-    const dim3 grid((unsigned)((pc + NTHREADS - 1) / NTHREADS), (unsigned)(rows < 65535 ? rows : 65535));
+    const int pc = coarse_pitch(g);
+    const long long nq = 3LL * (g.nyc + 1) * (pc / 4);
+    const long long need = (nq + NTHREADS - 1) / NTHREADS;
+    const unsigned grid = (unsigned)(need < 152 * 8 ? need : 152 * 8);   // 8 CTAs per SM, grid-stride
     k_coarse_pad<T><<<grid, NTHREADS, 0, st>>>(g, xc, xcp, pc);
     return cudaGetLastError();
 }
