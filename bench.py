@@ -126,7 +126,8 @@ def algorithmic_work(info, H):
         "residual_features": {"bytes": 3 * Nc * rb + 2 * Nf * rb + P * ldx * fb},
         "gru": {"bytes": P * ldx * fb + 2 * P * H * rb + P * n_out * rb,
                 "flops": 2 * P * (3 * H * (n_in + H) + H * n_out)},
-        "scatter_avg": {"bytes": P * n_out * rb + 3 * Nc * 8 + 2 * Nf * rb},
+        # the coarse window comes from the padded fine-type copy (u and v)
+        "scatter_avg": {"bytes": P * n_out * rb + 2 * Nc * rb + 2 * Nf * rb},
         "rhs": {"bytes": 2 * Nf * rb + 2 * Nf * rb},
         "restrict": {"bytes": 2 * Nf * rb + 3 * Nc * 8},
     }

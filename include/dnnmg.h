@@ -243,11 +243,13 @@ int dnnmg_step(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, vo
                cudaStream_t stream);
 
 /*
- * dnnmg_step with the coarse vectors in HOST memory: copies xc_host
- * [3][Nc] to the device, runs the step, copies bc back to bc_host [3][Nc],
- * all enqueued on `stream`.  Both host buffers must stay valid until the
- * stream reaches this point; page-locked buffers make the copies
- * asynchronous.  h and bf stay device-resident.
+ * dnnmg_step with the coarse vectors in HOST memory, xc_host and bc_host
+ * [3][Nc], all enqueued on `stream`.  If both buffers are page-locked and
+ * mapped (cudaHostAlloc / pinned memory under unified addressing), the step's
+ * kernels read x_c and write b_c there directly over the CPU-GPU link;
+ * otherwise xc_host is copied into the workspace before the step and bc
+ * copied back after it.  Both host buffers must stay valid until the stream
+ * reaches this point.  h and bf stay device-resident.
  */
 int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, void *h,
                     void *bf, double *bc_host, void *workspace, size_t workspace_bytes,

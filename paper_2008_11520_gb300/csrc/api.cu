@@ -706,7 +706,7 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
         DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
         DNNMG_CUDA_TRY(mark());
     }
-    DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, nullptr, xc, t, w.vc, s));
+    DNNMG_CUDA_TRY(launch_scatter_avg(g, prec, w.d, nullptr, xc, t, w.vc, s, w.xcp));
     DNNMG_CUDA_TRY(mark());
     DNNMG_CUDA_TRY(launch_rhs(g, prec, mesh->fem64, mesh->fem32, w.vc, bf, s));
     DNNMG_CUDA_TRY(mark());
@@ -744,6 +744,20 @@ int dnnmg_step_host(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc_host, v
     if (int e = step_checks(mesh, net, h, bf, workspace, workspace_bytes)) return e;
     if (!xc_host || !bc_host) return fail(DNNMG_EINVAL, "NULL array");
     const Workspace w = carve(mesh->info, workspace);
+    // Page-locked (mapped) host buffers are read and written by the step's
+    // kernels directly over the CPU-GPU link: x_c only by the coarse copy
+    // (the averaging reads the padded copy), b_c only by the restriction.
+    auto mapped = [](const void *p) -> void * {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+    };
+    const double *xc_dev = static_cast<const double *>(mapped(xc_host));
+    double *bc_dev = static_cast<double *>(mapped(bc_host));
+    if (xc_dev && bc_dev) return step_body(mesh, net, xc_dev, h, bf, bc_dev, w, t, stream);
     const size_t nbytes = 3 * (size_t)mesh->info.Nc * sizeof(double);
     DNNMG_CUDA_TRY(cudaMemcpyAsync(w.xc, xc_host, nbytes, cudaMemcpyHostToDevice, stream));
     if (int e = step_body(mesh, net, w.xc, h, bf, w.bc, w, t, stream)) return e;

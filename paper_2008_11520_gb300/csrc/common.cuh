@@ -128,8 +128,10 @@ cudaError_t launch_prolongate(const MeshGeom &g, int prec, const double *xc, voi
 cudaError_t launch_residual_features(const MeshGeom &g, int prec, const FemCoef<double> &f64,
                                      const FemCoef<float> &f32, const void *xf, const double *xc, double t,
                                      const void *bf, void *rf, void *X, cudaStream_t st);
+// xcp (may be null): the step's padded copy of x_c in the fine type, read
+// instead of xc for the coarse window (the same values)
 cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf, const double *xc,
-                               double t, void *vcorr, cudaStream_t st);
+                               double t, void *vcorr, cudaStream_t st, const void *xcp = nullptr);
 cudaError_t launch_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64,
                        const FemCoef<float> &f32, const void *vcorr, void *bf, cudaStream_t st);
 // The coarse vector in the fine arithmetic type, rows padded to pc (a

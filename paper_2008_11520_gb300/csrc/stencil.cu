@@ -145,6 +145,22 @@ struct CoarseWin {
             cs[e] = v;
         }
     }
+    // The same window from the padded copy [NC..][nyc+1][pc] of x_c in the
+    // fine type that the step keeps (the same values: both round x_c once).
+    __device__ __forceinline__ void stage_padded(const MeshGeom &g, const T *__restrict__ xcp, int pc, int Ilo,
+                                                 int Jlo) {
+        ci0 = Ilo >> K;
+        cj0 = Jlo >> K;
+        const size_t cplane = (size_t)pc * (g.nyc + 1);
+        for (int e = threadIdx.x; e < N; e += blockDim.x) {
+            const int c = e / (CW * CH), rem = e - c * (CW * CH);
+            const int b = rem / CW, a = rem - b * CW;
+            const int ci = ci0 + a, cj = cj0 + b;
+            T v = T(0);
+            if (ci >= 0 && cj >= 0 && ci <= g.nxc && cj <= g.nyc) v = __ldg(xcp + c * cplane + (size_t)cj * pc + ci);
+            cs[e] = v;
+        }
+    }
     // Bilinear value of the staged fields at fine node (I, J) (raw P, no BC):
     // blends along x on the cell's bottom and top edges, then along y.
     __device__ __forceinline__ void interp(int I, int J, T (&out)[NC]) const {
@@ -1205,8 +1221,8 @@ struct PatchWin {
 // coarse window is staged.  Same arithmetic as the general path, same bits.
 template <typename T, int R, typename CWin>
 __device__ __forceinline__ void scatter_fast_tile(const MeshGeom &g, const T *__restrict__ d, const T *__restrict__ xf,
-                                                  const double *__restrict__ xc, T *__restrict__ vc, CWin &cw,
-                                                  int I0, int J0) {
+                                                  const double *__restrict__ xc, const T *__restrict__ xcp, int pc,
+                                                  T *__restrict__ vc, CWin &cw, int I0, int J0) {
     static_assert(NTHREADS == (PTX / 4) * PTY, "one run per thread");
     const int Ib = I0 + 4 * (threadIdx.x & (PTX / 4 - 1)), J = J0 + threadIdx.x / (PTX / 4);
     const size_t node = (size_t)J * g.pitch + Ib;   // 4-aligned in a 64-aligned row
@@ -1215,7 +1231,8 @@ __device__ __forceinline__ void scatter_fast_tile(const MeshGeom &g, const T *__
     PatchWin::run4(g, d, g.K + g.s - 1, Ib, J, su, sv, cnt);
     T x[2][4];
     if constexpr (R > 0) {
-        cw.stage(g, xc, I0, J0);
+        if (xcp) cw.stage_padded(g, xcp, pc, I0, J0);
+        else cw.stage(g, xc, I0, J0);
         __syncthreads();   // publishes the staged coarse nodes
         cw.interp4(Ib, J, x);
     } else {
@@ -1237,7 +1254,7 @@ __device__ __forceinline__ void scatter_fast_tile(const MeshGeom &g, const T *__
 template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 6 : 4)
 k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, const double *__restrict__ xc,
-              double inflow_peak, T *__restrict__ vc) {
+              const T *__restrict__ xcp, int pc, double inflow_peak, T *__restrict__ vc) {
     using CWin = CoarseWin<T, (R > 0 ? R : 2), PTX, PTY, 2>;
     __shared__ T cs_mem[R > 0 ? CWin::N : 1];
     __shared__ int pid_s[(PTX / 2 + 2) * (PTY / 2 + 2)];   // S = 2 holds the most patches
@@ -1249,13 +1266,16 @@ k_scatter_avg(MeshGeom g, const T *__restrict__ d, const T *__restrict__ xf, con
     CWin cw;
     cw.cs = cs_mem;
     if (fast && g.K + g.s - 1 >= 2) {
-        scatter_fast_tile<T, R>(g, d, xf, xc, vc, cw, I0, J0);
+        scatter_fast_tile<T, R>(g, d, xf, xc, xcp, pc, vc, cw, I0, J0);
         return;
     }
     PatchWin pw;
     pw.pid = pid_s;
     pw.stage(g, I0, I0 + PTX - 1, J0, J0 + PTY - 1);
-    if constexpr (R > 0) cw.stage(g, xc, I0, J0);
+    if constexpr (R > 0) {
+        if (xcp) cw.stage_padded(g, xcp, pc, I0, J0);
+        else cw.stage(g, xc, I0, J0);
+    }
     const double up = inflow_peak;
     __syncthreads();   // publishes pid_s and the staged coarse nodes
     const int I = I0 + (threadIdx.x & (PTX - 1));
@@ -1991,27 +2011,29 @@ cudaError_t launch_residual_step(const MeshGeom &g, int prec, const FemCoef<doub
 }
 
 template <typename T>
-cudaError_t run_scatter(const MeshGeom &g, const T *d, const T *xf, const double *xc, double w, T *vc,
+cudaError_t run_scatter(const MeshGeom &g, const T *d, const T *xf, const double *xc, const T *xcp, double w, T *vc,
                         cudaStream_t st) {
     const dim3 grid = node_tile_grid(g);
-    if (!xc) {
-        k_scatter_avg<T, 0><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc);
+    const int pc = coarse_pitch(g);
+    if (!xc && !xcp) {
+        k_scatter_avg<T, 0><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, xcp, pc, w, vc);
         return cudaGetLastError();
     }
     switch (g.r) {
-        case 2: k_scatter_avg<T, 2><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
-        case 4: k_scatter_avg<T, 4><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
-        case 8: k_scatter_avg<T, 8><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, w, vc); break;
+        case 2: k_scatter_avg<T, 2><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, xcp, pc, w, vc); break;
+        case 4: k_scatter_avg<T, 4><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, xcp, pc, w, vc); break;
+        case 8: k_scatter_avg<T, 8><<<grid, NTHREADS, 0, st>>>(g, d, xf, xc, xcp, pc, w, vc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_avg(const MeshGeom &g, int prec, const void *d, const void *xf, const double *xc,
-                               double t, void *vcorr, cudaStream_t st) {
+                               double t, void *vcorr, cudaStream_t st, const void *xcp) {
     const double w = inflow_peak(g, t);
-    if (prec == DNNMG_F64) return run_scatter(g, (const double *)d, (const double *)xf, xc, w, (double *)vcorr, st);
-    return run_scatter(g, (const float *)d, (const float *)xf, xc, w, (float *)vcorr, st);
+    if (prec == DNNMG_F64)
+        return run_scatter(g, (const double *)d, (const double *)xf, xc, (const double *)xcp, w, (double *)vcorr, st);
+    return run_scatter(g, (const float *)d, (const float *)xf, xc, (const float *)xcp, w, (float *)vcorr, st);
 }
 
 template <typename T>

@@ -241,23 +241,27 @@ def test_step_is_deterministic_and_host_variant_agrees(dn):
     h0 = torch.rand(om.P, case["H"], device="cuda") - 0.5
     bf0 = m.fine(2)
     bcs = []
-    for variant in range(3):
+    # device buffers twice; pinned host buffers (the kernels read x_c and write
+    # b_c over the host link); pageable host buffers (copied through the workspace)
+    for variant in range(4):
         h, bf = h0.clone(), bf0.clone()
         bc = m.coarse(3)
         ws = m.workspace()
         if variant < 2:
             dn.dnnmg_step(m, net, cuda(xc, torch.float64), h, bf, bc, ws, 0.0)
         else:
-            xch = torch.as_tensor(xc).pin_memory()
-            bch = torch.zeros(3 * m.info.Nc, dtype=torch.float64).pin_memory()
+            xch = torch.as_tensor(xc).clone()
+            bch = torch.full((3 * m.info.Nc,), -1.0, dtype=torch.float64)
+            if variant == 2:
+                xch, bch = xch.pin_memory(), bch.pin_memory()
             dn.dnnmg_step_host(m, net, xch, h, bf, bch, ws, 0.0)
             torch.cuda.synchronize()
             bc = bch.cuda()
         torch.cuda.synchronize()
         bcs.append((bc.cpu().numpy().ravel(), h.cpu().numpy(), bf.cpu().numpy()))
-    for k in range(3):
-        assert np.array_equal(bcs[0][k], bcs[1][k])
-        assert np.array_equal(bcs[0][k], bcs[2][k])
+    for v in range(1, 4):
+        for k in range(3):
+            assert np.array_equal(bcs[0][k], bcs[v][k]), (v, k)
 
 
 def test_step_leaves_mesh_status_clear(dn):
