@@ -115,7 +115,7 @@ def measured_traffic(stage):
 
 
 def algorithmic_work(info, H):
-    """Bytes each stage must move and the GEMM flops, per step."""
+    """Bytes each stage must move (nodes, not the row padding) and the GEMM flops, per step."""
     Nf, Nc, P, ldx, n_in, n_out = info.Nf, info.Nc, info.P, info.ldx, info.n_in, info.n_out
     # algorithmic bytes count nodes, not the row padding of the pitched layout
     rb, fb = info.real_bytes, info.feature_bytes

@@ -46,7 +46,7 @@ extern "C" {
 #define DNNMG_OK 0
 #define DNNMG_EINVAL 1       /* null pointer, size or parameter out of range */
 #define DNNMG_ECUDA 2        /* a CUDA runtime call or kernel launch failed */
-#define DNNMG_EUNSUPPORTED 3 /* valid request this build does not implement */
+#define DNNMG_EUNSUPPORTED 3 /* valid request the library does not implement */
 #define DNNMG_ENOMEM 4       /* device allocation in *_create failed */
 
 /* precision of the fine fields and of the patch network */
