@@ -9,6 +9,10 @@ Algorithm 2 lines 6-9, in the paper's order:
   b^L    <- R(b^L+K)                    (line 9; S7)
 The residual of S2 uses the fine right-hand side b_f of the current step,
 i.e. the one assembled by the previous step's line 8.
+
+Parity unpinned: the composed step has no closed form of its own; each part
+it calls is pinned separately, and with a zero network the step reduces to
+S1 followed by S6 and S7 (checked against the GPU path bit for bit).
 """
 
 from .average import scatter_average
