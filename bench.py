@@ -114,6 +114,22 @@ def measured_traffic(stage):
         return None
 
 
+def max_over_ranks(values, world, device="cpu"):
+    """Element-wise maximum of per-rank timings over the process group: the
+    job takes as long as its slowest rank."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(world, units_per_rank, steps, ms):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (replicas, weak scaling)."""
+    return world * units_per_rank * steps / (ms / 1e3)
+
+
 def algorithmic_work(info, H):
     """Bytes each stage must move (nodes, not the row padding) and the GEMM flops, per step."""
     Nf, Nc, P, ldx, n_in, n_out = info.Nf, info.Nc, info.P, info.ldx, info.n_in, info.n_out
@@ -212,10 +228,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = e0.elapsed_time(e1)
     assert np.isfinite(bch.numpy()).all()
 
-    times = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    total_ms, e2e_ms = times.tolist()
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], world, dev)
     return dict(cfg=c, info=I, per_step=per_step, total_ms=total_ms, stage_ms=stage_ms, clocks=clocks,
                 e2e_ms=e2e_ms, wall=wall, launches=dnnmg.dnnmg_step_launches(mesh, net))
 
@@ -300,7 +313,7 @@ def main():
     I = r["info"]
     dof = 2 * I.Nf
     step_ms = r["total_ms"] / args.steps
-    value = world * dof * args.steps / (r["total_ms"] / 1e3)
+    value = job_rate(world, dof, args.steps, r["total_ms"])
     pk = peaks()
     work = algorithmic_work(I, c["H"])
     # dominant kernel: the stage with the largest share of the step
@@ -337,7 +350,7 @@ def main():
                    "l2": "no flush: each step moves ~2.5 GB, inputs larger than the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "p50_ms": per[len(per) // 2], "p99_ms": per[min(len(per) - 1, int(0.99 * len(per)))],
-        "e2e": {"value": world * dof * args.steps / (r["e2e_ms"] / 1e3), "unit": UNIT,
+        "e2e": {"value": job_rate(world, dof, args.steps, r["e2e_ms"]), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * I.Nc * 8, "d2h_bytes_per_step": 3 * I.Nc * 8},
         "gpu_launches": r["launches"] * args.steps,
         "roofline": roof, "stages": stages, "clocks": r["clocks"],
