@@ -233,7 +233,8 @@ int dnnmg_restrict(dnnmg_mesh_t mesh, const void *bf, double *bc, cudaStream_t s
 /*
  * S1-S7 in order (Algorithm 2 lines 6-9) on one stream: S2+S3 and S5 with
  * S1 fused (x~ is formed inside their tiles from xc), then S4, S6, S7.
- *   xc [3][Nc] double (in), h [P][H] (in/out), bf [2][plane] (in: this step's
+ *   xc [3][Nc] double (in), h [P][H] (in/out; may be NULL when P = 0, a mesh
+ *   without fluid patches, whose step skips S4), bf [2][plane] (in: this step's
  *   fine right-hand side; out: the next step's), bc [3][Nc] double (out),
  *   workspace >= info.workspace_bytes device bytes (scratch, caller-owned,
  *   256-byte aligned), t = t_n for the inflow values.

@@ -674,7 +674,8 @@ static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, vo
     if (net->precision != I.precision)
         return fail(DNNMG_EINVAL, "network precision %d differs from mesh precision %d",
                     net->precision, I.precision);
-    if (!h || !bf || !workspace) return fail(DNNMG_EINVAL, "NULL array");
+    // h has P rows: a mesh without fluid patches has no state
+    if ((!h && I.P > 0) || !bf || !workspace) return fail(DNNMG_EINVAL, "NULL array");
     if (!aligned16(bf) || !aligned16(h)) return fail(DNNMG_EINVAL, "bf and h must be 16-byte aligned");
     if (workspace_bytes < I.workspace_bytes)
         return fail(DNNMG_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, I.workspace_bytes);

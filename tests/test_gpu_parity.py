@@ -475,3 +475,36 @@ def test_rhs_alone_equals_rhs_of_rhs_restrict(dn):
     dn.dnnmg_rhs(m, v, b2)
     torch.cuda.synchronize()
     assert torch.equal(b1, b2)
+
+
+def test_mesh_without_fluid_patches(dn):
+    # degenerate case: every coarse cell solid, so there are no fluid patches
+    # (P = 0): the step skips the network, every velocity row is a Dirichlet
+    # row, and the result still matches the oracle; a server admits the
+    # instance with an empty state segment
+    case = dict(nxc=16, nyc=4, K=1, s=1, H=32, prec="bf16", ellipse=None)
+    from oracle.mesh import Mesh as OMesh
+    solid = np.ones((case["nyc"], case["nxc"]), dtype=bool)
+    m = dn.Mesh(dn.make_desc(case["nxc"], case["nyc"], case["K"], case["s"], None, precision="bf16", solid=solid))
+    om = OMesh(case["nxc"], case["nyc"], case["K"], case["s"], solid=solid)
+    assert m.info.P == 0 and om.P == 0
+    Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
+    net = dn.Net(Wx, Uh, Wfc, "bf16")
+    assert dn.dnnmg_step_launches(m, net) == 5
+    xc = coarse_input(case, t=0.0)
+    v0 = fine_velocity(case)[:2].astype(np.float32).astype(np.float64)
+    bf = m.fine(2)
+    bc = m.coarse(3)
+    dn.dnnmg_rhs_restrict(m, m.pack(v0), bf, bc)
+    h = torch.zeros(0, case["H"], device="cuda")
+    dn.dnnmg_step(m, net, cuda(xc, torch.float64), h, bf, bc, m.workspace(), 0.0)
+    out = step.dnnmg_step(om, PRM, (Wx, Uh, Wfc), xc, np.zeros((0, case["H"])), fem.rhs(om, PRM, v0), 0.0)
+    torch.cuda.synchronize()
+    assert rel_l2(host(bc).reshape(3, -1), out["bc"]) <= TOL["bf16"]
+    assert rel_l2(m.unpack(bf), out["bf"]) <= TOL["bf16"]
+    srv = dn.Server(net, 128)
+    slot = srv.admit(m)
+    assert srv.state(slot).shape == (0, case["H"])
+    srv.step([(slot, cuda(xc, torch.float64), bf, bc, 0.0)])
+    torch.cuda.synchronize()
+    srv.close()
