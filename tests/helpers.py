@@ -24,6 +24,8 @@ CASES = {
     # the right half solid)
     "two_obstacles_bf16": dict(nxc=64, nyc=12, K=2, s=1, H=32, prec="bf16", ellipse=None, geometry="two"),
     "lshape_f32": dict(nxc=40, nyc=10, K=1, s=2, H=16, prec="f32", ellipse=None, geometry="L"),
+    # the largest patches: K = 3, s = 2 (16 x 16 fine cells, 906 inputs, 578 outputs)
+    "k3s2_f32_max": dict(nxc=12, nyc=4, K=3, s=2, H=32, prec="f32", ellipse=(0.5, 0.2, 0.12, 0.08)),
 }
 
 
