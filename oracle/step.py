@@ -10,9 +10,12 @@ Algorithm 2 lines 6-9, in the paper's order:
 The residual of S2 uses the fine right-hand side b_f of the current step,
 i.e. the one assembled by the previous step's line 8.
 
-Parity unpinned: the composed step has no closed form of its own; each part
-it calls is pinned separately, and with a zero network the step reduces to
-S1 followed by S6 and S7 (checked against the GPU path bit for bit).
+Pins: with a zero network (d = 0) the step's coarse right-hand side equals
+the coarse level's own Crank-Nicolson right-hand side of x_c (a Galerkin
+identity of the nested Q1 spaces, exact in the quadrature used), pinned on the
+CPU for K = 1, 2, 3 and s = 1, 2.  Parity unpinned for a nonzero network: the
+composition then has no closed form of its own, and each part it calls is
+pinned separately.
 """
 
 from .average import scatter_average

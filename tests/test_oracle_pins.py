@@ -428,3 +428,38 @@ def test_window_matches_full_mesh_in_interior():
     # interior patches' hidden states are exact
     inner = (win.patches[:, 0] >= 3) & (win.patches[:, 0] <= 4)
     assert np.allclose(ow["h"][inner], of["h"][gidx[inner]], rtol=1e-13, atol=1e-14)
+
+
+# ------------------------------------------------------- whole step, d = 0
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+@pytest.mark.parametrize("s", [1, 2])
+def test_zero_correction_step_gives_coarse_rhs(K, s):
+    # With d = 0 the method falls back to the coarse solver (Sec. 5.1), so the
+    # coarse right-hand side it hands on must be the coarse level's own.
+    # For nested Q1 spaces a coarse function is exactly a fine function
+    # (S1), and R = P^T sums fine tests into coarse tests (S7).  Every term of
+    # Eq. 4cranknicholson3 is then integrated exactly on both levels, since
+    # 2-point Gauss is exact up to degree 3 per direction and (v.grad v) phi
+    # is at most cubic.  So R Rhs_f(P x_c) = Rhs_c(x_c) on every coarse row
+    # once x_c holds zero Dirichlet data (ramp at t = 0: zero inflow); fine
+    # Dirichlet rows lie where the coarse tests of free nodes vanish.
+    from oracle.step import dnnmg_step
+    ell = (0.6, 0.2, 0.3, 0.12)
+    m = Mesh(8, 4, K, s, ellipse=ell)
+    mc = Mesh(8, 4, 0, s, ellipse=ell)          # the coarse level on its own
+    assert m.solid_coarse.any()
+    prm = Params(ramp=True)
+    rng = np.random.default_rng(100 + 10 * K + s)
+    xc = rng.normal(size=(3, m.Nc))
+    xc[:2, m.dirichlet_c.ravel()] = 0.0
+    H = 4
+    W = (rng.normal(size=(3 * H, m.n_in)) * 0.1, rng.normal(size=(3 * H, H)) * 0.1,
+         np.zeros((m.n_out, H)))
+    out = dnnmg_step(m, prm, W, xc, rng.normal(size=(m.P, H)),
+                     rng.normal(size=(2, m.Nf)), 0.0)
+    assert np.abs(out["d"]).max() == 0.0
+    bc_coarse = fem.rhs(mc, prm, xc[:2])
+    scale = np.abs(bc_coarse).max()
+    assert np.allclose(out["bc"][:2], bc_coarse, rtol=0, atol=1e-13 * scale)
+    assert not out["bc"][2].any()
