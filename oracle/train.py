@@ -1,4 +1,4 @@
-"""Oracle for training the patch network (§8(f) NEXT-1): the GRU of Eq. gru
+"""Oracle for training the patch network: the GRU of Eq. gru
 unrolled over a window of time steps, the l2 training loss of Sec. 6.5 with
 Tikhonov regularisation, its gradient by backpropagation through time, and one
 Adam update.

@@ -1,0 +1,188 @@
+"""DNN-MG time stepping end to end (Algorithm 2): host coarse solve, library correction.
+
+Each time step solves the coarse level's Crank-Nicolson system on the host in
+FP64 (line 5, ``solver.Level.solve``), then runs the correction step
+(lines 6-9: prolongation, residual and features, GRU network, averaging,
+fine right-hand side, restriction) in one ``dnnmg_step`` call on the GPU,
+whose restricted right-hand side the next coarse solve uses.  The GRU state
+and the fine right-hand side stay on the device between steps; only x_c goes
+down and b_c comes back.
+
+``python -m paper_2008_11520_gb300.timeloop`` trains the patch network on
+solved flows of a small channel and prints E_rel(v) (Sec. 6.6) of the method
+with the trained and with a zero network against the plain fine-level solve
+(``accuracy_experiment``).
+"""
+
+import numpy as np
+import torch
+
+from . import dnnmg, solver
+
+
+class LibraryCorrection:
+    """Lines 6-9 of Algorithm 2 through the library: a callable (x_c, t_n) -> b_c.
+
+    x_c is the coarse solution at t_n, [3][Nc] float64 (host); the result is
+    the restricted right-hand side for the solve at t_{n+1}, [3][Nc] float64
+    (host).  The handle keeps h [P][H] and the fine right-hand side b_f on the
+    device; b_f starts at b_f0 (node-ordered [2][Nf], default 0: the fluid at
+    rest) and h at 0.  By default one ``dnnmg_step`` call does the work; with
+    keep_fine the same kernels run through their single-step entry points and
+    the corrected fine velocity v~ + d_bar stays available (``v_corr``).
+    """
+
+    def __init__(self, mesh, net, bf0=None, keep_fine=False):
+        I = mesh.info
+        self.mesh, self.net, self.keep_fine = mesh, net, keep_fine
+        self.h = torch.zeros(I.P * net.H, dtype=mesh.real, device="cuda")
+        self.bf = mesh.fine(2) if bf0 is None else mesh.pack(bf0)
+        self.bc = torch.zeros(3 * I.Nc, dtype=torch.float64, device="cuda")
+        self.xc = torch.zeros(3 * I.Nc, dtype=torch.float64, device="cuda")
+        if keep_fine:
+            self.xf, self.vc = mesh.fine(3), mesh.fine(2)
+            self.X = mesh.features()
+            self.d = torch.zeros(I.P * I.n_out, dtype=mesh.real, device="cuda")
+        else:
+            self.ws = mesh.workspace()
+
+    def __call__(self, xc, t):
+        m, I = self.mesh, self.mesh.info
+        self.xc.copy_(torch.from_numpy(np.ascontiguousarray(xc, dtype=np.float64).reshape(-1)))
+        if not self.keep_fine:
+            dnnmg.dnnmg_step(m, self.net, self.xc, self.h, self.bf, self.bc, self.ws, t)
+        else:
+            dnnmg.dnnmg_prolongate(m, self.xc, self.xf, t)
+            dnnmg.dnnmg_patch_features(m, self.xf, self.bf, self.X)
+            dnnmg.dnnmg_gru_step(self.net, self.X, self.h, self.d, I.P)
+            dnnmg.dnnmg_scatter_avg(m, self.d, self.xf, self.vc)
+            dnnmg.dnnmg_rhs_restrict(m, self.vc, self.bf, self.bc)
+        return self.bc.cpu().numpy().reshape(3, -1)
+
+    def v_corr(self):
+        """The last step's corrected fine velocity, node-ordered [2][Nf] float64."""
+        if not self.keep_fine:
+            raise RuntimeError("v_corr needs keep_fine=True")
+        return self.mesh.unpack(self.vc)
+
+
+def coarse_level(mesh_desc):
+    """The host Level of a mesh descriptor's coarse level (same geometry and parameters)."""
+    d = mesh_desc
+    if d.solid:
+        solid = np.ctypeslib.as_array(d.solid, shape=(d.nyc, d.nxc)).astype(bool)
+    else:
+        ell = (d.obst_cx, d.obst_cy, d.obst_ax, d.obst_ay)
+        solid = solver.ellipse_mask(d.nxc, d.nyc, ell, d.lx, d.ly)
+    return solver.Level(d.nxc, d.nyc, solid, d.lx, d.ly, nu=d.nu, k=d.k, alpha0=d.alpha0,
+                        u_max=d.u_max, ramp=bool(d.ramp))
+
+
+def fine_level(mesh_desc):
+    """The host Level of a mesh descriptor's fine level L+K (nested mask)."""
+    c = coarse_level(mesh_desc)
+    r = 2 ** mesh_desc.K
+    return solver.Level(c.nx * r, c.ny * r, solver.refine_mask(c.solid, mesh_desc.K), c.lx, c.ly,
+                        nu=c.nu, k=c.k, alpha0=c.alpha0, u_max=c.u_max, ramp=c.ramp)
+
+
+def e_rel(v, ref):
+    """|v - v_bar| / |v_bar| over the fine velocity DOFs (Sec. 6.6)."""
+    return float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
+
+
+def _held_out_errors(mesh, net, coarse_states, fine_states, k):
+    """E_rel(v) per step of v~ + d_bar with the coarse states given (teacher
+    forcing), through the inference kernels, the GRU state carried."""
+    I = mesh.info
+    h = torch.zeros(I.P * net.H, dtype=mesh.real, device="cuda")
+    d = torch.zeros(I.P * I.n_out, dtype=mesh.real, device="cuda")
+    X = mesh.features()
+    xf, bf, vc = mesh.fine(3), mesh.fine(2), mesh.fine(2)
+    errs = []
+    for n, xc in enumerate(coarse_states):
+        t = (n + 1) * k
+        xcd = torch.as_tensor(np.ascontiguousarray(xc).reshape(-1)).cuda()
+        dnnmg.dnnmg_prolongate(mesh, xcd, xf, t)
+        dnnmg.dnnmg_rhs(mesh, mesh.pack(fine_states[n][:2]), bf)
+        dnnmg.dnnmg_patch_features(mesh, xf, bf, X)
+        dnnmg.dnnmg_gru_step(net, X, h, d, I.P)
+        dnnmg.dnnmg_scatter_avg(mesh, d, xf, vc)
+        errs.append(e_rel(mesh.unpack(vc), fine_states[n + 1][:2]))
+    return errs
+
+
+def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1e-3,
+                        u_train=(1.2, 1.5, 1.8), u_held=1.35, steps=20, T=10, H=32,
+                        epochs=300, lr=1e-3, seed=0):
+    """Train the patch network on solved flows and measure what it gains.
+
+    The paper's accuracy study (Sec. 6.5-6.6) in small: fine-level (L+K)
+    solutions of the start-up flow at the inflow peaks u_train are the
+    ground truth, plain coarse-level solutions the network's inputs
+    (``train.solution_windows``); windows of T steps, Adam with the Tikhonov
+    term, the state carried from one window to the next.  On a flow with the
+    held-out peak u_held it reports E_rel(v) (Sec. 6.6, fine velocity DOFs,
+    mean over the steps):
+
+    * ``teacher``: v~ + d_bar on the plain coarse solutions, trained net vs d = 0;
+    * ``loop``: Algorithm 2 end to end (host coarse solve, library correction
+      step, its right-hand side fed back), trained net vs zero net, which
+      reduces the method to the plain coarse solve.
+    """
+    from . import train
+
+    def setup(u):
+        desc = dnnmg.make_desc(nxc, nyc, K, 1, ellipse=ellipse, precision="f32", ramp=True,
+                               nu=nu, u_max=u)
+        mesh = dnnmg.Mesh(desc)
+        coarse, fine = coarse_level(desc), fine_level(desc)
+        xf = [np.zeros((3, fine.N))] + solver.simulate(fine, steps)
+        xc = solver.simulate(coarse, steps)
+        return mesh, coarse, xf, xc
+
+    data = []
+    for u in u_train:
+        mesh, _, xf, xc = setup(u)
+        data.append(train.solution_windows(mesh, xf, xc, k=mesh.desc.k))
+    I = mesh.info
+    tn = train.PatchNetTrainer(I.n_in, I.ldx, H, I.n_out, T, I.P, seed=seed, std=0.02, out_std=0.0, lr=lr)
+    for _ in range(epochs):
+        for X, Y in data:
+            h = None
+            for w in range(steps // T):
+                _, h = tn.train_window(X[w * T:(w + 1) * T].contiguous(), Y[w * T:(w + 1) * T].contiguous(), h)
+    W = tn.weights()
+    zero = [W[0], W[1], np.zeros_like(W[2])]
+    mesh, coarse, xf, xc = setup(u_held)
+    out = {"updates": tn.step_no}
+    for name, weights in (("trained", W), ("zero", zero)):
+        net = dnnmg.Net(*weights, precision="f32")
+        teacher = _held_out_errors(mesh, net, xc, xf, coarse.k)
+        corr = LibraryCorrection(mesh, net, keep_fine=True)
+        loop = []
+
+        def step(x, t, corr=corr, loop=loop):
+            bc = corr(x, t)
+            loop.append(e_rel(corr.v_corr(), xf[len(loop) + 1][:2]))
+            return bc
+
+        solver.dnnmg_run(coarse, step, steps)
+        out[name] = {"teacher": float(np.mean(teacher)), "loop": float(np.mean(loop)),
+                     "loop_last": loop[-1]}
+    return out
+
+
+def main():
+    import json
+    import time
+    t0 = time.time()
+    out = accuracy_experiment()
+    print(json.dumps({"workload": "32x8 coarse cells, K = 1, nu = 1e-3, start-up flow, 20 steps; "
+                                  "trained on inflow peaks 1.2, 1.5, 1.8, evaluated at 1.35",
+                      "metric": "E_rel(v), mean over steps", **out,
+                      "seconds": round(time.time() - t0, 1)}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,4 +1,4 @@
-"""Training the patch network (§8(f) NEXT-1), on the library's own kernels.
+"""Training the patch network, on the library's own kernels.
 
 * ``GruWindow`` -- a ``torch.autograd.Function`` whose forward and backward are
   libdnnmg's GRU window kernels (Eq. gru + output layer unrolled over T steps,
@@ -15,6 +15,10 @@
   Dirichlet values at Dirichlet nodes (as a fine-level solution has them; the
   analytic flow follows the exact ellipse, the mesh its staircase): it stands
   in for the paper's (L+1)-level multigrid solutions.
+* ``solution_windows`` -- the same windows from solved flows: the fine-level
+  solution of ``solver`` as v_bar and a coarse solution (the fine one at the
+  coarse nodes, ``coarse_nodes``, or a coarse-level simulation) as x_c, the
+  paper's two-level training data.
 * ``e_rel`` -- E_rel(v) of Sec. 6.6 for a net, through the inference path
   (dnnmg_gru_step, dnnmg_scatter_avg).
 
@@ -163,6 +167,49 @@ def flow_windows(mesh, spec, nsteps, k=synth.DT, t0=0.0):
         Y[n] = (ref.reshape(-1)[idx] - xf[:2].reshape(-1)[idx])
         prev = ref
     return X, Y
+
+
+def solution_windows(mesh, fine_states, coarse_states, k=synth.DT, t0=0.0):
+    """Features X [T][P][ldx] and targets Y [T][P][n_out] from solved flows.
+
+    The training data of Sec. 5.3 ("Training of DNN-MG"): fine_states =
+    [x_bar(t_0), ..., x_bar(t_T)], the fine-level solution (node-ordered
+    [3][Nf] float64, e.g. ``solver.simulate`` on the fine level; entry 0 is
+    the state before the window), and coarse_states = [x_c(t_1), ...,
+    x_c(t_T)] ([3][Nc] float64): the coarse solution the network sees, either
+    the fine solution at the coarse nodes or a coarse-level simulation.
+    Step n: x~ = P x_c(t_n) with the Dirichlet values at t_n, b_f =
+    Rhs(v_bar(t_{n-1})), features from the library's S2+S3, and targets
+    y = v_bar(t_n) - x~ on every patch's fine nodes.
+    """
+    I = mesh.info
+    assert mesh.real == torch.float32 and mesh.feat == torch.float32, "training needs a DNNMG_F32 mesh"
+    T = len(coarse_states)
+    if len(fine_states) != T + 1:
+        raise ValueError("fine_states needs one state more than coarse_states")
+    idx = patch_node_index(mesh)
+    X = torch.empty(T, I.P, I.ldx, dtype=torch.float32, device="cuda")
+    Y = torch.empty(T, I.P, I.n_out, dtype=torch.float32, device="cuda")
+    xf, bf = mesh.fine(3), mesh.fine(2)
+    for n in range(T):
+        t = t0 + (n + 1) * k
+        xc = torch.as_tensor(np.ascontiguousarray(coarse_states[n], dtype=np.float64).reshape(-1)).cuda()
+        dnnmg.dnnmg_prolongate(mesh, xc, xf, t)
+        dnnmg.dnnmg_rhs(mesh, mesh.pack(np.asarray(fine_states[n])[:2]), bf)
+        dnnmg.dnnmg_patch_features(mesh, xf, bf, X[n])
+        ref = mesh.pack(np.asarray(fine_states[n + 1])[:2])
+        Y[n] = ref.reshape(-1)[idx] - xf[:2].reshape(-1)[idx]
+    return X, Y
+
+
+def coarse_nodes(mesh, fine_state):
+    """The fine-level state at the coarse nodes ([3][Nf] -> [3][Nc]), which
+    coincide with every 2^K-th fine node: the coarse member of a two-level
+    representation of one fine solution."""
+    I = mesh.info
+    r = 2 ** I.K
+    a = np.asarray(fine_state).reshape(3, I.nyf + 1, I.nxf + 1)[:, ::r, ::r]
+    return np.ascontiguousarray(a).reshape(3, -1)
 
 
 def e_rel(mesh, weights, spec, steps, H, k=synth.DT, t0=0.0):

@@ -1,0 +1,165 @@
+"""The host level solver (Algorithm 2 line 5 and the fine reference solve).
+
+The solver is supporting code outside the correction step; these tests pin
+it to the oracle's definition of the discrete system and to what the
+mathematics fixes (exact Newton matrix of a quadratic map, quadratic
+convergence, the Poiseuille steady state, and the zero-network reduction of
+Algorithm 2 to the plain coarse solve).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fem, transfer
+from oracle.mesh import Mesh, Params
+from oracle.step import dnnmg_step
+from paper_2008_11520_gb300 import solver
+
+ELL = (0.6, 0.2, 0.3, 0.12)
+
+
+def pair(nx=16, ny=8, ellipse=ELL, **kw):
+    """The same level as a solver Level and as the fine level of an oracle Mesh
+    one refinement above (nested masks, as on every level above the coarse one)."""
+    prm = Params(**kw)
+    solid = solver.refine_mask(solver.ellipse_mask(nx // 2, ny // 2, ellipse), 1)
+    lvl = solver.Level(nx, ny, solid, nu=prm.nu, k=prm.k, alpha0=prm.alpha0,
+                       u_max=prm.u_max, ramp=prm.ramp)
+    mesh = Mesh(nx // 2, ny // 2, 1, 1, ellipse=ellipse)
+    return lvl, mesh, prm
+
+
+def test_geometry_matches_oracle_rules():
+    lvl, mesh, _ = pair()
+    assert lvl.solid.any()
+    assert (lvl.solid == mesh.solid_f).all()
+    assert (lvl.dirichlet == mesh.dirichlet.ravel()).all()
+    assert (lvl.inflow == mesh.inflow.ravel()).all()
+    assert (lvl.p_active == mesh.p_active.ravel()).all()
+    fine = solver.refine_mask(lvl.solid, 2)
+    assert fine.shape == (32, 64) and fine.sum() == 16 * lvl.solid.sum()
+
+
+@pytest.mark.parametrize("nu", [1e-3, 0.05])
+def test_operator_and_rhs_equal_oracle(nu):
+    lvl, mesh, prm = pair(nu=nu, k=0.02, alpha0=0.2)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((3, lvl.N))
+    # oracle residual with b = 0 is -A(x) on free rows
+    r = fem.residual(mesh, prm, x, np.zeros((2, lvl.N)))
+    A = lvl.operator(x)
+    free = [~lvl.dirichlet, ~lvl.dirichlet, lvl.p_active]
+    for c in range(3):
+        scale = np.abs(A[c][free[c]]).max()
+        np.testing.assert_allclose(-A[c][free[c]], r[c][free[c]], rtol=0, atol=1e-12 * scale)
+    b_or = fem.rhs(mesh, prm, x[:2])
+    np.testing.assert_allclose(lvl.rhs(x[:2]), b_or, rtol=0, atol=1e-12 * np.abs(b_or).max())
+
+
+def test_newton_matrix_is_exact_derivative():
+    # the defect is quadratic in x, so a central difference with any step is exact
+    lvl, _, _ = pair(nu=0.01)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((3, lvl.N))
+    e = rng.standard_normal((3, lvl.N))
+    b = rng.standard_normal((2, lvl.N))
+    Je = (lvl.jacobian(x) @ e.ravel()).reshape(3, lvl.N)
+    fd = 0.5 * (lvl.defect(x + e, b, 0.3) - lvl.defect(x - e, b, 0.3))
+    np.testing.assert_allclose(Je, fd, rtol=0, atol=1e-11 * np.abs(fd).max())
+
+
+def test_solution_zeroes_oracle_residual_and_carries_boundary_values():
+    lvl, mesh, prm = pair(ramp=True)
+    rng = np.random.default_rng(5)
+    prev = 0.3 * rng.standard_normal((3, lvl.N))
+    b = lvl.rhs(prev[:2])
+    hist = []
+    t = 0.25
+    x = lvl.solve(b, t, x0=prev, history=hist)
+    r = fem.residual(mesh, prm, x, b)
+    assert np.abs(r).max() <= 1e-10 * np.abs(b).max()
+    mask, uD, vD = transfer.dirichlet_velocity(mesh, prm, t)
+    assert np.array_equal(x[0, mask], uD[mask]) and np.array_equal(x[1, mask], vD[mask])
+    assert not x[2, ~lvl.p_active].any()
+    # quadratic convergence: a handful of iterations, each squaring the defect
+    assert len(hist) <= 7
+    tail = [h for h in hist if h > 1e-9 * hist[0]]
+    for a, c in zip(tail[1:], tail[2:]):
+        assert c <= 10 * a * a / hist[0] + 1e-13 * hist[0]
+
+
+def test_poiseuille_is_a_steady_state():
+    # without obstacle the nodal Poiseuille profile with its linear pressure drop
+    # solves the discrete system exactly (the S2 pin), so a step keeps it
+    lvl, _, prm = pair(nx=16, ny=8, ellipse=None)
+    X = (np.arange(lvl.N) % (lvl.nx + 1)) * lvl.hx
+    y = lvl.y
+    x = np.array([prm.u_max * 4 * y * (lvl.ly - y) / lvl.ly ** 2,
+                  np.zeros(lvl.N),
+                  8 * prm.u_max * prm.nu / lvl.ly ** 2 * (lvl.lx - X)])
+    x1 = lvl.advance(x, 0.01)
+    np.testing.assert_allclose(x1, x, rtol=0, atol=1e-11 * np.abs(x).max())
+
+
+def test_zero_network_run_is_the_plain_coarse_solve():
+    # Algorithm 2 with d = 0 hands the coarse solver the coarse level's own
+    # right-hand side (exact for zero boundary data), so the run equals plain
+    # time stepping on the coarse level; the correction is the oracle's step.
+    ell = (0.6, 0.2, 0.3, 0.12)
+    nxc, nyc, K = 16, 8, 1
+    prm = Params(u_max=0.0)
+    coarse = solver.Level(nxc, nyc, solver.ellipse_mask(nxc, nyc, ell), u_max=0.0)
+    m = Mesh(nxc, nyc, K, 1, ellipse=ell)
+    rng = np.random.default_rng(6)
+    x0 = np.zeros((3, coarse.N))
+    x0[:2] = rng.standard_normal((2, coarse.N))
+    x0[:2, coarse.dirichlet] = 0.0
+    H = 4
+    W = (0.1 * rng.standard_normal((3 * H, m.n_in)), 0.1 * rng.standard_normal((3 * H, H)),
+         np.zeros((m.n_out, H)))
+    state = {"h": np.zeros((m.P, H)), "bf": np.zeros((2, m.Nf))}
+
+    def correct(xc, t):
+        o = dnnmg_step(m, prm, W, xc, state["h"], state["bf"], t)
+        state["h"], state["bf"] = o["h"], o["bf"]
+        return o["bc"]
+
+    run = solver.dnnmg_run(coarse, correct, 4, x0=x0)
+    plain = solver.simulate(coarse, 4, x0=x0)
+    for a, b in zip(run, plain):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-10 * np.abs(b).max())
+    assert np.abs(plain[-1][:2]).max() > 0.1
+
+
+def test_level_rejects_odd_cells():
+    with pytest.raises(ValueError):
+        solver.Level(15, 8)
+
+
+def test_projection_term_on_partly_solid_patches():
+    # a coarse-level mask is not nested: some 2x2-cell patches are partly solid.
+    # Each patch then contributes its fluid cells' integrals, so the term stays
+    # symmetric, positive semidefinite and zero on linear pressures (pi
+    # reproduces them), and it equals the sum of the per-cell forms.
+    lvl = solver.Level(16, 8, solver.ellipse_mask(16, 8, ELL))
+    blk = lvl.solid.reshape(4, 2, 8, 2).transpose(0, 2, 1, 3).reshape(4, 8, 4)
+    assert (blk.any(axis=2) & ~blk.all(axis=2)).any()
+    L = lvl.L.toarray()
+    np.testing.assert_allclose(L, L.T, rtol=0, atol=1e-14 * np.abs(L).max())
+    X = (np.arange(lvl.N) % (lvl.nx + 1)) * lvl.hx
+    assert np.abs(L @ (0.3 + 2.0 * X - 5.0 * lvl.y)).max() <= 1e-12 * np.abs(L).max()
+    assert np.linalg.eigvalsh(L).min() >= -1e-12 * np.abs(L).max()
+    # a pressure living on the nodes of one fully solid patch costs nothing
+    n, m = np.argwhere(blk.all(axis=2))[0]
+    nodes = [(2 * n + b) * (lvl.nx + 1) + 2 * m + a for b in range(3) for a in range(3)]
+    centre = np.zeros(lvl.N)
+    centre[nodes[4]] = 1.0
+    assert centre @ L @ centre == 0.0
+    # a patch with fluid and solid cells: its centre node's energy is the
+    # fluid cells' share of the full patch's (each cell holds a quarter)
+    n, m = np.argwhere(blk.any(axis=2) & ~blk.all(axis=2))[0]
+    c = (2 * n + 1) * (lvl.nx + 1) + 2 * m + 1
+    e = np.zeros(lvl.N)
+    e[c] = 1.0
+    full = solver.Level(16, 8)
+    assert e @ L @ e == pytest.approx((~blk[n, m]).sum() / 4 * (e @ full.L @ e), rel=1e-13)

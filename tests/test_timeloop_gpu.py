@@ -1,0 +1,75 @@
+"""Algorithm 2 end to end on the GPU: host coarse solve, library correction step.
+
+The loop's correction (lines 6-9) goes through the C ABI, the coarse solve
+(line 5) is the host solver pinned in test_solver.py.  The whole trajectory
+must match the same loop driven by the oracle's step, and a network trained
+on solved flows must lower E_rel(v) on a held-out flow, both with the coarse
+solutions given and inside the loop.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.mesh import Mesh, Params
+from oracle.step import dnnmg_step
+from paper_2008_11520_gb300 import solver
+
+pytestmark = pytest.mark.gpu
+
+ELL = (0.6, 0.2, 0.3, 0.12)
+# A relative perturbation of 1e-14 in b_c grows to about 1e-11 in x_c over
+# six steps of this loop (measured with the oracle), and the FP64 kernels
+# differ from the oracle by rounding only: 1e-8 leaves a wide margin.
+TOL_LOOP = 1e-8
+
+
+@pytest.fixture(scope="module")
+def tl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_11520_gb300 import dnnmg, timeloop
+    return dnnmg, timeloop
+
+
+@pytest.mark.parametrize("keep_fine", [False, True])
+def test_loop_matches_oracle_loop(tl, keep_fine):
+    dn, timeloop = tl
+    desc = dn.make_desc(16, 8, 1, 1, ellipse=ELL, precision="f64", ramp=True)
+    mesh = dn.Mesh(desc)
+    I = mesh.info
+    coarse = timeloop.coarse_level(desc)
+    assert I.n_solid_coarse == coarse.solid.sum() > 0
+    H, steps = 8, 6
+    rng = np.random.default_rng(1)
+    W = (0.1 * rng.standard_normal((3 * H, I.n_in)), 0.1 * rng.standard_normal((3 * H, H)),
+         0.01 * rng.standard_normal((I.n_out, H)))
+    corr = timeloop.LibraryCorrection(mesh, dn.Net(*W, precision="f64"), keep_fine=keep_fine)
+    gpu = solver.dnnmg_run(coarse, corr, steps)
+
+    om, prm = Mesh(16, 8, 1, 1, ellipse=ELL), Params(ramp=True)
+    st = {"h": np.zeros((om.P, H)), "bf": np.zeros((2, om.Nf)), "v": None}
+
+    def correct(xc, t):
+        o = dnnmg_step(om, prm, W, xc, st["h"], st["bf"], t)
+        st["h"], st["bf"], st["v"] = o["h"], o["bf"], o["vcorr"]
+        return o["bc"]
+
+    ref = solver.dnnmg_run(coarse, correct, steps)
+    assert np.abs(ref[-1][:2]).max() > 0.1
+    for a, b in zip(gpu, ref):
+        assert np.abs(a - b).max() <= TOL_LOOP * np.abs(b).max()
+    if keep_fine:
+        v = corr.v_corr()
+        assert np.abs(v - st["v"]).max() <= TOL_LOOP * np.abs(st["v"]).max()
+
+
+def test_trained_network_lowers_error(tl):
+    # Measured on the CPU with the training oracle (FP64): E_rel 0.271 with
+    # d = 0; 0.132 for the trained net on the plain coarse solutions and 0.173
+    # inside the loop.  The bounds leave room for the FP32 training path.
+    _, timeloop = tl
+    out = timeloop.accuracy_experiment()
+    tr, zr = out["trained"], out["zero"]
+    assert tr["teacher"] < 0.75 * zr["teacher"], out
+    assert tr["loop"] < 0.85 * zr["loop"], out

@@ -1,4 +1,4 @@
-"""Training kernels of the patch network on the GPU (§8(f) NEXT-1).
+"""Training kernels of the patch network on the GPU.
 
 The GRU window's forward and backward (truncated BPTT), the loss of Sec. 6.5
 and Adam are compared with the FP64 training oracle (itself pinned by finite
