@@ -163,3 +163,33 @@ def test_projection_term_on_partly_solid_patches():
     e[c] = 1.0
     full = solver.Level(16, 8)
     assert e @ L @ e == pytest.approx((~blk[n, m]).sum() / 4 * (e @ full.L @ e), rel=1e-13)
+
+
+@pytest.fixture(scope="module")
+def tl():
+    import os
+    from paper_2008_11520_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2008_11520_gb300 import dnnmg, timeloop
+    return dnnmg, timeloop
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_levels_from_mesh_descriptor(tl, K):
+    # host-only: the Levels the time loop builds from a library mesh
+    # descriptor have the oracle's geometry on both levels and its parameters
+    dn, timeloop = tl
+    ell = (0.6, 0.2, 0.3, 0.12)
+    d = dn.make_desc(16, 8, K, 1, ellipse=ell, precision="f32", ramp=True, nu=0.01, u_max=1.2)
+    c, f = timeloop.coarse_level(d), timeloop.fine_level(d)
+    om = Mesh(16, 8, K, 1, ellipse=ell)
+    assert (c.solid == om.solid_coarse).all() and (f.solid == om.solid_f).all()
+    assert (f.dirichlet == om.dirichlet.ravel()).all() and (f.p_active == om.p_active.ravel()).all()
+    assert (c.dirichlet == om.dirichlet_c.ravel()).all()
+    assert (c.nu, c.k, c.alpha0, c.u_max, c.ramp) == (0.01, 0.01, 0.1, 1.2, True)
+    assert (f.nx, f.ny, f.u_max) == (16 * 2 ** K, 8 * 2 ** K, 1.2)
+    solid = np.zeros((8, 16), dtype=np.uint8)
+    solid[2:6, 6:8] = 1
+    c2 = timeloop.coarse_level(dn.make_desc(16, 8, K, 2, solid=solid))
+    assert (c2.solid == solid.astype(bool)).all()
