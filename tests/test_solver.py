@@ -193,3 +193,19 @@ def test_levels_from_mesh_descriptor(tl, K):
     solid[2:6, 6:8] = 1
     c2 = timeloop.coarse_level(dn.make_desc(16, 8, K, 2, solid=solid))
     assert (c2.solid == solid.astype(bool)).all()
+
+
+def test_chord_iterations_reach_the_newton_solution():
+    # reusing a factorisation changes the path, not the solution
+    lvl, mesh, prm = pair(ramp=True)
+    ref = solver.Level(lvl.nx, lvl.ny, lvl.solid, ramp=True)
+    xa = xb = np.zeros((3, lvl.N))
+    for n in range(1, 9):
+        t = n * lvl.k
+        b = lvl.rhs(xa[:2])
+        xa = lvl.solve(b, t, x0=xa, newton="chord")
+        xb = ref.solve(ref.rhs(xb[:2]), t, x0=xb, newton="exact")
+        np.testing.assert_allclose(xa, xb, rtol=0, atol=1e-10 * np.abs(xb).max())
+        scale = max(np.abs(b).max(), np.abs(lvl.operator(xa)).max())
+        assert np.abs(fem.residual(mesh, prm, xa, b)).max() <= 1e-10 * scale
+    assert lvl.factorisations < ref.factorisations / 2
