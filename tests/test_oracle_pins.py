@@ -390,6 +390,20 @@ def test_constant_correction_survives_averaging():
     assert np.array_equal(v[:, ~free], xf[:2, ~free])
 
 
+def test_general_constant_correction_within_one_ulp():
+    # a constant c that is not dyadic: the mean of m equal predictions
+    # (m = 1, 2 or 4) is c up to the rounding of the sum, one ulp at most
+    m = Mesh(8, 4, 2, 2, ellipse=(0.6, 0.2, 0.3, 0.12))
+    assert set(np.unique(m.multiplicity[m.multiplicity > 0])) == {1, 2, 4}
+    free = ~m.dirichlet.ravel()
+    for c in (0.1, -0.7, 1.0 / 3.0, 2.0 ** -30 * 3.1):
+        d = np.full((m.P, m.n_out), c)
+        v = average.scatter_average(m, d, np.zeros((3, m.Nf)))
+        err = np.abs(v[:, free] - c).max()
+        assert err <= np.spacing(abs(c)), (c, err)
+        assert not v[:, ~free].any()
+
+
 def test_averaging_of_two_patch_predictions():
     # a node shared by two patches gets the mean of the two predictions
     m = Mesh(4, 2, 1, 1)
