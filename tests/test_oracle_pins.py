@@ -188,6 +188,25 @@ def test_two_by_two_gauss_equals_three_by_three():
     assert np.abs(r2 - r3).max() <= 1e-12 * np.abs(r3).max()
 
 
+def _trapz(f, h):
+    return h * (f.sum() - 0.5 * (f[0] + f[-1]))
+
+
+def test_divergence_rows_sum_to_boundary_flux():
+    # Divergence theorem: the test functions sum to 1, so the divergence rows
+    # sum to the integral of div v, which is the outward flux through the four
+    # sides.  v.n is linear along each boundary edge of a bilinear field, so
+    # the trapezoidal rule on the nodal values gives the flux exactly.
+    m = Mesh(8, 4, 2, 1)
+    rng = np.random.default_rng(21)
+    u, v = rng.normal(size=(2, m.Nf))
+    div = fem.assemble_terms(m, u, v)["div"]
+    U, V = u.reshape(m.wyf + 1, m.wxf + 1), v.reshape(m.wyf + 1, m.wxf + 1)
+    flux = (_trapz(U[:, -1], m.hyf) - _trapz(U[:, 0], m.hyf)
+            + _trapz(V[-1, :], m.hxf) - _trapz(V[0, :], m.hxf))
+    assert abs(div.sum() - flux) <= 1e-13 * np.abs(div).sum()
+
+
 def test_constant_velocity_rhs_is_mass_times_velocity():
     # constant v: convection and diffusion vanish, b = (1/k) (v, phi_i);
     # (1, phi_i) = hx hy at interior nodes

@@ -209,3 +209,19 @@ def test_chord_iterations_reach_the_newton_solution():
         scale = max(np.abs(b).max(), np.abs(lvl.operator(xa)).max())
         assert np.abs(fem.residual(mesh, prm, xa, b)).max() <= 1e-10 * scale
     assert lvl.factorisations < ref.factorisations / 2
+
+
+def test_solution_conserves_mass():
+    # The pressure rows make (div v, xi_i) + projection term vanish; summed
+    # over all nodes the projection terms cancel (pi reproduces constants) and
+    # the divergence terms give the net flux out of the fluid, which is the
+    # outflow at x = lx minus the inflow at x = 0 (walls and obstacle are
+    # no-slip).  v.n is linear along boundary edges: the trapezoidal rule on
+    # nodal values is exact.
+    lvl, _, _ = pair(ramp=True)
+    x = solver.simulate(lvl, 12)[-1]
+    U = x[0].reshape(lvl.ny + 1, lvl.nx + 1)
+    trapz = lambda f: lvl.hy * (f.sum() - 0.5 * (f[0] + f[-1]))
+    q_in, q_out = trapz(U[:, 0]), trapz(U[:, -1])
+    assert q_in > 0.05
+    assert abs(q_out - q_in) <= 1e-10 * q_in
