@@ -225,3 +225,22 @@ def test_solution_conserves_mass():
     q_in, q_out = trapz(U[:, 0]), trapz(U[:, -1])
     assert q_in > 0.05
     assert abs(q_out - q_in) <= 1e-10 * q_in
+
+
+def test_generated_flows_are_the_level_solutions(tmp_path):
+    out = tmp_path / "flows.npz"
+    solver.main(["--nxc", "16", "--nyc", "8", "--K", "1", "--steps", "3", "--ratios", "0.6,1.0",
+                 "--out", str(out)])
+    z = np.load(out)
+    assert z["fine"].shape == (2, 4, 2, 33 * 17) and z["coarse"].shape == (2, 3, 3, 17 * 9)
+    assert not z["fine"][:, 0].any()
+    for i, q in enumerate((0.6, 1.0)):
+        ell = tuple(z["ellipses"][i])
+        assert ell == (0.2, 0.2, 0.05, 0.05 * q)
+        solid = solver.ellipse_mask(16, 8, ell)
+        c = solver.Level(16, 8, solid, ramp=True)
+        f = solver.Level(32, 16, solver.refine_mask(solid, 1), ramp=True)
+        for a, b in zip(z["coarse"][i], solver.simulate(c, 3)):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-10 * np.abs(b).max())
+        for a, b in zip(z["fine"][i][1:], solver.simulate(f, 3)):
+            np.testing.assert_allclose(a, b[:2], rtol=0, atol=1e-6 * np.abs(b[:2]).max())
