@@ -84,3 +84,43 @@ def test_mesh_query_rejects_oversize(lib):
     with pytest.raises(lib.DnnmgError) as e:
         lib.dnnmg_mesh_query(lib.make_desc(1024, 16384, 2, 1))
     assert e.value.code == 3
+
+
+def _run_isolated(code, pythonpath):
+    import subprocess
+    import sys
+    env = dict(os.environ, PYTHONPATH=pythonpath)
+    return subprocess.run([sys.executable, "-c", code], cwd=pythonpath, env=env,
+                          capture_output=True, text=True, timeout=300)
+
+
+def test_product_modules_never_load_the_oracle(lib):
+    # the oracle is test infrastructure: no module of the package may import it
+    mods = ["dnnmg", "synth", "solver", "timeloop", "train", "serve", "build"]
+    code = ("import sys\n"
+            + "".join(f"import paper_2008_11520_gb300.{m}\n" for m in mods)
+            + "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]\n"
+            + "assert not bad, bad\n")
+    r = _run_isolated(code, ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # a copy of the package without libdnnmg.so: importing the binding raises
+    # ImportError (no fallback), while host-only modules still import
+    import shutil
+    src = os.path.join(ROOT, "paper_2008_11520_gb300")
+    dst = tmp_path / "paper_2008_11520_gb300"
+    dst.mkdir()
+    for f in os.listdir(src):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(src, f), dst / f)
+    code = ("import paper_2008_11520_gb300.solver\n"
+            "try:\n"
+            "    import paper_2008_11520_gb300.dnnmg\n"
+            "except ImportError as e:\n"
+            "    assert 'libdnnmg.so is missing' in str(e) and 'no fallback' in str(e), e\n"
+            "else:\n"
+            "    raise SystemExit('imported without the library')\n")
+    r = _run_isolated(code, str(tmp_path))
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
