@@ -143,6 +143,40 @@ def test_restriction_is_transpose_of_prolongation(K):
     assert abs(transfer.restrict_raw(m, xf)[0].sum() - xf[0].sum()) <= 1e-12 * np.abs(xf).sum()
 
 
+def test_ramp_closed_form():
+    # omega(t) = 1/2 - cos(2 pi t) / 2 up to t = 1/2, then 1 (Sec. 6.1)
+    prm = Params(ramp=True)
+    assert [prm.omega(t) for t in (0.0, 0.25, 0.5, 0.75, 3.0)] == pytest.approx([0.0, 0.5, 1.0, 1.0, 1.0],
+                                                                                abs=1e-15)
+    assert Params().omega(0.0) == 1.0
+
+
+@pytest.mark.parametrize("t", [0.1, 0.25, 1.0])
+def test_dirichlet_overwrite_values(t):
+    # S1 overwrites fine Dirichlet velocity nodes: the parabolic inflow at
+    # x = 0 (peak u_max at y = H/2, times the ramp), zero on walls and
+    # obstacle; every other node keeps the raw prolongation.
+    m = Mesh(8, 4, 2, 1, ellipse=(0.6, 0.2, 0.3, 0.12))
+    prm = Params(ramp=True)
+    rng = np.random.default_rng(8)
+    xc = rng.normal(size=(3, m.Nc))
+    raw = transfer.prolongate_raw(m, xc)
+    xf = transfer.prolongate(m, prm, xc, t)
+    d = m.dirichlet.ravel()
+    assert np.array_equal(xf[:, ~d], raw[:, ~d]) and np.array_equal(xf[2], raw[2])
+    U = xf[0].reshape(m.wyf + 1, m.wxf + 1)
+    w = prm.omega(t)
+    assert U[m.nyf // 2, 0] == pytest.approx(prm.u_max * w, rel=1e-14)   # y = H/2
+    assert U[0, 0] == 0.0 and U[-1, 0] == 0.0
+    assert not xf[1, d].any()
+    assert not xf[0, d & ~m.inflow.ravel()].any()
+    # Simpson's rule is exact for the parabola: mean inflow (2/3) u_max w, so
+    # u_max = 1.5 gives a mean of 1 and Re = 100 for an obstacle of size 0.1
+    col = U[:, 0]
+    simpson = m.hyf / 3 * (col[0] + col[-1] + 4 * col[1:-1:2].sum() + 2 * col[2:-1:2].sum())
+    assert simpson / m.ly == pytest.approx(2.0 / 3.0 * prm.u_max * w, rel=1e-13)
+
+
 def test_restrict_zeroes_coarse_dirichlet_and_pressure():
     m = c1_mesh()
     rng = np.random.default_rng(2)
