@@ -134,12 +134,31 @@ def lps_alpha(mesh, prm):
     return prm.alpha0 * (mesh.hxf ** 2 + mesh.hyf ** 2) / prm.nu
 
 
+def lps_cell_stiffness(hx, hy, cells, nq=2):
+    """(grad f, grad g) over the listed cells (ca, cb) of a 2x2-cell patch, 9x9."""
+    pts, wts = gauss_1d(nq)
+    Ke = np.zeros((4, 4))
+    for xi, wx in zip(pts, wts):
+        for eta, wy in zip(pts, wts):
+            _, dxi, deta = q1_shape(xi, eta)
+            dx, dy = dxi / hx, deta / hy
+            Ke += wx * wy * hx * hy * (np.outer(dx, dx) + np.outer(dy, dy))
+    L = np.zeros((9, 9))
+    for ca, cb in cells:
+        idx = [3 * cb + ca, 3 * cb + ca + 1, 3 * (cb + 1) + ca, 3 * (cb + 1) + ca + 1]
+        L[np.ix_(idx, idx)] += Ke
+    return L
+
+
 def lps_term(mesh, prm, p, nq=2):
     """sum_T alpha_T (grad(p - pi p), grad(xi_i - pi xi_i)) per pressure node.
 
-    Loops over the 2x2-cell patches (aligned to even fine indices) whose cells
-    are fluid.  With f = (I - Pi) p_patch and g_i = (I - Pi) e_i the patch
-    contribution to row i is alpha g_i^T L f.
+    Loops over the 2x2-cell patches (aligned to even fine indices) that hold
+    a fluid cell.  With f = (I - Pi) p_patch and g_i = (I - Pi) e_i the patch
+    contribution to row i is alpha g_i^T L f, L the stiffness over the
+    patch's fluid cells T.  On nested masks (every level above a coarse one)
+    patches are all fluid or all solid; a single level's own mask can leave a
+    patch partly solid, and then only its fluid cells enter the sum over T.
     """
     nxn = mesh.wxf + 1
     Pi = lps_projection_matrix()
@@ -147,17 +166,23 @@ def lps_term(mesh, prm, p, nq=2):
     L = lps_patch_stiffness(mesh.hxf, mesh.hyf, nq)
     alpha = lps_alpha(mesh, prm)
     sol = mesh.solid_f
-    # LPS patches: fine cells (2m..2m+1, 2n..2n+1); nested masks make them all-fluid or all-solid
     blk = sol.reshape(mesh.wyf // 2, 2, mesh.wxf // 2, 2)
-    assert (blk.all(axis=(1, 3)) == blk.any(axis=(1, 3))).all()
-    n, m = np.nonzero(~blk.any(axis=(1, 3)))
-    base = (2 * n) * nxn + 2 * m
     offs = np.array([b * nxn + a for b in range(3) for a in range(3)])
-    nodes = base[:, None] + offs[None, :]
+    out = np.zeros(mesh.Nf)
+    # all-fluid patches: fine cells (2m..2m+1, 2n..2n+1)
+    n, m = np.nonzero(~blk.any(axis=(1, 3)))
+    nodes = ((2 * n) * nxn + 2 * m)[:, None] + offs[None, :]
     f = p[nodes] @ IminusPi.T
     contrib = alpha * (f @ L.T) @ IminusPi
-    out = np.zeros(mesh.Nf)
     np.add.at(out, nodes, contrib)
+    # partly solid patches: the stiffness of their fluid cells only
+    n, m = np.nonzero(blk.any(axis=(1, 3)) & ~blk.all(axis=(1, 3)))
+    for nn, mm in zip(n, m):
+        fluid = [(ca, cb) for cb in range(2) for ca in range(2) if not blk[nn, cb, mm, ca]]
+        Lp = lps_cell_stiffness(mesh.hxf, mesh.hyf, fluid, nq)
+        nd = (2 * nn) * nxn + 2 * mm + offs
+        fp = IminusPi @ p[nd]
+        out[nd] += alpha * IminusPi.T @ (Lp @ fp)
     return out
 
 

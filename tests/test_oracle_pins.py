@@ -336,6 +336,30 @@ def test_lps_orthogonal_to_patchwise_bilinear():
     assert abs(p @ lps) > 1e-3 * np.abs(p).max() * np.abs(lps).sum()
 
 
+def test_lps_on_partly_solid_patches():
+    # one level with its own mask (K = 0): some projection patches are partly
+    # solid and contribute their fluid cells only.  The term is then still a
+    # symmetric positive semidefinite form that vanishes on linear pressures,
+    # and a patch's centre node, whose fluctuation is symmetric, gets the
+    # fluid cells' share (a quarter each) of the all-fluid patch's energy.
+    ell = (0.6, 0.2, 0.3, 0.12)
+    m = Mesh(16, 8, 0, 1, ellipse=ell)
+    blk = m.solid_f.reshape(4, 2, 8, 2)
+    part = blk.any(axis=(1, 3)) & ~blk.all(axis=(1, 3))
+    assert part.any()
+    prm = Params()
+    L = np.array([fem.lps_term(m, prm, e) for e in np.eye(m.Nf)]).T
+    np.testing.assert_allclose(L, L.T, rtol=0, atol=1e-14 * np.abs(L).max())
+    assert np.linalg.eigvalsh(L).min() >= -1e-12 * np.abs(L).max()
+    xs, ys = m.fine_xy()
+    assert np.abs(L @ (0.3 + 2.0 * xs.ravel() - 5.0 * ys.ravel())).max() <= 1e-12 * np.abs(L).max()
+    full = np.array([fem.lps_term(Mesh(16, 8, 0, 1), prm, e) for e in np.eye(m.Nf)]).T
+    for n, mm in np.argwhere(part):
+        c = (2 * n + 1) * (m.wxf + 1) + 2 * mm + 1
+        share = (~blk[n, :, mm, :]).sum() / 4
+        assert L[c, c] == pytest.approx(share * full[c, c], rel=1e-13)
+
+
 def test_residual_zero_rows():
     m = c1_mesh()
     prm = Params()

@@ -244,3 +244,19 @@ def test_generated_flows_are_the_level_solutions(tmp_path):
             np.testing.assert_allclose(a, b, rtol=0, atol=1e-10 * np.abs(b).max())
         for a, b in zip(z["fine"][i][1:], solver.simulate(f, 3)):
             np.testing.assert_allclose(a, b[:2], rtol=0, atol=1e-6 * np.abs(b[:2]).max())
+
+
+def test_operator_equals_oracle_on_a_single_level_mask():
+    # the coarse level's own mask leaves projection patches partly solid:
+    # both the solver and the oracle then sum over the fluid cells only
+    ell = (0.6, 0.2, 0.3, 0.12)
+    lvl = solver.Level(16, 8, solver.ellipse_mask(16, 8, ell))
+    mesh, prm = Mesh(16, 8, 0, 1, ellipse=ell), Params()
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((3, lvl.N))
+    r = fem.residual(mesh, prm, x, np.zeros((2, lvl.N)))
+    A = lvl.operator(x)
+    free = [~lvl.dirichlet, ~lvl.dirichlet, lvl.p_active]
+    for c in range(3):
+        scale = np.abs(A[c][free[c]]).max()
+        np.testing.assert_allclose(-A[c][free[c]], r[c][free[c]], rtol=0, atol=1e-12 * scale)
