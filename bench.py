@@ -1,6 +1,6 @@
 """Benchmark of the DNN-MG fine-level correction step on GB300.
 
-One step = one full correction (Algorithm 2 lines 6-9: prolongation, residual
+One step = one full correction (Algorithm 2's correction step: prolongation, residual
 and patch features, GRU patch network, averaging, right-hand side,
 restriction) of the large single instance: 2048 x 512 coarse cells, K = 2
 (8192 x 2048 fine cells, 16.8 M fine nodes), 2 x 2-cell patches (262 144

@@ -3,8 +3,8 @@
  *
  * DNN-MG (Margenberg, Hartmann, Lessig, Richter, arXiv 2008.11520) corrects a
  * coarse multigrid solution on level L with a patch-wise recurrent network on
- * level L+K.  After the coarse Newton-Krylov solve of a time step, Algorithm 2
- * lines 6-9 do
+ * level L+K.  After the coarse Newton-Krylov solve of a time step, the
+ * correction step of Algorithm 2 does
  *     v~    <- P(v^L)                      prolongation            (dnnmg_prolongate)
  *     d     <- N(v~, Omega_L, Omega_L+K)   residual + features     (dnnmg_patch_features)
  *                                          GRU + output layer      (dnnmg_gru_step)
@@ -140,7 +140,7 @@ int dnnmg_net_create(int n_in, int hidden, int n_out, const double *Wx, const do
 int dnnmg_net_destroy(dnnmg_net_t net);
 
 /*
- * S1, Algorithm 2 line 6: xf = P xc on (u, v, p) by bilinear interpolation
+ * S1, the prolongation of Algorithm 2: xf = P xc on (u, v, p) by bilinear interpolation
  * from level L to L+K, then the fine velocity Dirichlet values at time t.
  *   xc [3][Nc] double (in), xf [3][plane] real (out).
  */
@@ -191,7 +191,7 @@ int dnnmg_scatter_avg(dnnmg_mesh_t mesh, const void *d, const void *xf, const do
                       void *vcorr, cudaStream_t stream);
 
 /*
- * S6 + S7, Algorithm 2 lines 8-9: bf = Rhs(vcorr) of Eq. 4cranknicholson3
+ * S6 + S7, right-hand side and restriction of Algorithm 2: bf = Rhs(vcorr) of Eq. 4cranknicholson3
  * (1/k (v,phi) - 1/2 (v.grad v,phi) - nu/2 (grad v,grad phi), no forcing),
  * zero on Dirichlet rows; then bc = R bf with R = P^T, coarse Dirichlet
  * velocity rows and all pressure rows zero.
@@ -202,14 +202,15 @@ int dnnmg_rhs_restrict(dnnmg_mesh_t mesh, const void *vcorr, void *bf, double *b
                        cudaStream_t stream);
 
 /*
- * S6 alone, Algorithm 2 line 8: bf = Rhs(vcorr) as in dnnmg_rhs_restrict,
+ * S6 alone, the right-hand side of Algorithm 2: bf = Rhs(vcorr) as in dnnmg_rhs_restrict,
  * without the restriction.
  *   vcorr [2][plane] real (in), bf [2][plane] real (out).
  */
 int dnnmg_rhs(dnnmg_mesh_t mesh, const void *vcorr, void *bf, cudaStream_t stream);
 
 /*
- * S5 + S6 fused, Algorithm 2 lines 7-8: bf = Rhs(v~ + averaged d) with
+ * S5 + S6 fused (Algorithm 2's averaged correction and right-hand side):
+ * bf = Rhs(v~ + averaged d) with
  * v~ = P xc at time t formed inside each tile (as dnnmg_scatter_avg with xc
  * followed by dnnmg_rhs, same arithmetic and bits); v_corr never reaches
  * memory.  Each tile copies the d rows of the patches around it to shared
@@ -221,7 +222,7 @@ int dnnmg_scatter_rhs(dnnmg_mesh_t mesh, const void *d, const double *xc, double
                       cudaStream_t stream);
 
 /*
- * S7 alone, Algorithm 2 line 9: bc = R bf with R = P^T (the transpose of the
+ * S7 alone, the restriction of Algorithm 2: bc = R bf with R = P^T (the transpose of the
  * bilinear prolongation across the K levels), coarse Dirichlet velocity rows
  * and all pressure rows zero.  Float input is accumulated with error-free
  * float-pair arithmetic (about 2^-44 relative to the sum of magnitudes) and
@@ -231,7 +232,7 @@ int dnnmg_scatter_rhs(dnnmg_mesh_t mesh, const void *d, const double *xc, double
 int dnnmg_restrict(dnnmg_mesh_t mesh, const void *bf, double *bc, cudaStream_t stream);
 
 /*
- * S1-S7 in order (Algorithm 2 lines 6-9) on one stream: S2+S3 and S5 with
+ * S1-S7 in order (the correction step of Algorithm 2) on one stream: S2+S3 and S5 with
  * S1 fused (x~ is formed inside their tiles from xc), then S4, S6, S7.
  *   xc [3][Nc] double (in), h [P][H] (in/out; may be NULL when P = 0, a mesh
  *   without fluid patches, whose step skips S4), bf [2][plane] (in: this step's
@@ -320,7 +321,7 @@ int dnnmg_step_timed(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
 /*
  * ---- Serving: batched steps of many instances ------------------------------
  *
- * A server runs Algorithm 2 lines 6-9 for several flow instances at once
+ * A server runs the correction step of Algorithm 2 for several flow instances at once
  * (meshes of any size, each with its own GRU state h, all using one net): the
  * stencil passes run per instance, the network (Eq. gru and the output
  * layer, Sec. 6.2) runs once over the patches of every instance in the batch

@@ -14,13 +14,13 @@ step by step, in float64, written for a reader checking it against the paper:
 * ``mesh``      -- structured channel mesh, obstacle mask, node classes, patches
                    (Sec. 5.2 "A patch-based neural network", Sec. 6.1 Fig. geom).
 * ``transfer``  -- prolongation P (interpolation) and restriction R = P^T
-                   (Sec. 3.4, mesh transfer; Algorithm 2 lines 6 and 9).
+                   (Sec. 3.4, mesh transfer; the first and last stages of Algorithm 2's correction).
 * ``fem``       -- Q1 Crank-Nicolson residual and right-hand side with local
                    projection stabilisation (Eq. nonlinearshort, Eq. 4cranknicholson3).
 * ``features``  -- per-patch network inputs (Sec. 5.2 "Neural network inputs").
 * ``gru``       -- GRU cell and fully connected output layer (Eq. gru, Sec. 6.2).
 * ``average``   -- averaging of duplicate predictions on shared nodes (Sec. 5.2).
-* ``step``      -- one DNN-MG correction step, Algorithm 2 lines 6-9.
+* ``step``      -- one DNN-MG correction step of Algorithm 2.
 
 Parity status: every function above is pinned by tests under ``tests/`` that
 check it against closed forms, invariants, hand-computed values and brute force

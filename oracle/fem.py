@@ -225,7 +225,8 @@ def residual(mesh, prm, xf, bf, nq=2):
 def rhs(mesh, prm, vel, nq=2):
     """S6: fine right-hand side b_f = Rhs(v) for the next step ([2][Nf]).
 
-    Algorithm 2 line 8 with v = v~ + d; Dirichlet velocity rows are 0.
+    The right-hand side of Algorithm 2's correction, with v = v~ + d;
+    Dirichlet velocity rows are 0.
     """
     u, v = (np.asarray(vel[c], dtype=np.float64) for c in range(2))
     terms = assemble_terms(mesh, u, v, None, nq)

@@ -2,13 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Algorithm 2 lines 6-9, in the paper's order:
-  v~     <- P(v^L)                      (line 6; S1)
-  d      <- N(v~, Omega_L, Omega_L+K)   (line 7; S2 residual, S3 features, S4 net)
-  b^L+K  <- Rhs(v~ + d)                 (line 8; S5 averaging, S6 right-hand side)
-  b^L    <- R(b^L+K)                    (line 9; S7)
+The correction step of Algorithm 2, in the paper's order:
+  v~     <- P(v^L)                      (prolongation; S1)
+  d      <- N(v~, Omega_L, Omega_L+K)   (network correction; S2 residual, S3 features, S4 net)
+  b^L+K  <- Rhs(v~ + d)                 (right-hand side; S5 averaging, S6)
+  b^L    <- R(b^L+K)                    (restriction; S7)
 The residual of S2 uses the fine right-hand side b_f of the current step,
-i.e. the one assembled by the previous step's line 8.
+i.e. the one assembled by the previous step's right-hand-side stage.
 
 Pins: with a zero network (d = 0) the step's coarse right-hand side equals
 the coarse level's own Crank-Nicolson right-hand side of x_c (a Galerkin

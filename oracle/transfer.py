@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 Sec. 3.4: prolongation is interpolation from the coarse to the fine space;
 restriction maps fine residual/right-hand-side vectors to the coarse level.
-Algorithm 2 line 6 prolongates the coarse solution from level L to L+K;
-line 9 restricts the fine right-hand side back to level L.
+Algorithm 2 prolongates the coarse solution from level L to L+K and, at the
+end of the correction, restricts the fine right-hand side back to level L.
 
 For right-hand-side (dual) vectors the restriction is the transpose of the
 prolongation, R = P^T.  Here P is written as direct bilinear interpolation
@@ -59,7 +59,7 @@ def dirichlet_velocity(mesh, prm, t):
 def prolongate(mesh, prm, xc, t):
     """S1: x~ = P x_c on (u, v, p), then the fine velocity Dirichlet values.
 
-    Algorithm 2 line 6.  xc: [3][Nc] float64; returns [3][Nf].
+    The prolongation of Algorithm 2.  xc: [3][Nc] float64; returns [3][Nf].
     """
     xf = prolongate_raw(mesh, xc)
     mask, uD, vD = dirichlet_velocity(mesh, prm, t)
@@ -98,7 +98,7 @@ def restrict_raw(mesh, bf):
 def restrict(mesh, bf):
     """S7: b_c = R b_f for the velocity rows, coarse Dirichlet rows zeroed.
 
-    Algorithm 2 line 9 (the right-hand side is restricted, not the velocity).
+    The restriction of Algorithm 2 (the right-hand side is restricted, not the velocity).
     bf: [2][Nf]; returns [3][Nc] with the pressure rows 0.
     """
     bc2 = restrict_raw(mesh, bf)

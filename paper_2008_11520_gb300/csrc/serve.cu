@@ -1,6 +1,6 @@
 // Batched correction steps of many flow instances (serving).
 //
-// Algorithm 2, lines 6-9, is per instance; its network (Eq. gru + output
+// The correction step of Algorithm 2 is per instance; its network (Eq. gru + output
 // layer) works patch by patch with weights shared by every instance that uses
 // the same net.  A server therefore runs one step of several instances as:
 //   per instance  S1+S2+S3 into that instance's rows of one feature matrix X,

@@ -1,5 +1,5 @@
-"""Serving: a continuous-batching request loop of DNN-MG steps (Algorithm 2,
-lines 6-9) over many flow instances with different meshes.
+"""Serving: a continuous-batching request loop of DNN-MG correction steps
+(Algorithm 2) over many flow instances with different meshes.
 
 Each request asks for one time step of one instance.  Instances are admitted
 by a device-memory budget into per-net servers (libdnnmg's dnnmg_server_*):

@@ -2,12 +2,12 @@
 
 Supporting code around the correction step, not part of it:
 
-* the coarse solve of Algorithm 2 line 5, which the correction step feeds with
+* the coarse solve of Algorithm 2, which the correction step feeds with
   its restricted right-hand side and which feeds the next step with x_c;
 * the plain fine-level time stepping whose velocities are the ground truth
   the network is trained towards (Sec. 5.3, "Training of DNN-MG").
 
-The correction step itself (Algorithm 2 lines 6-9) runs in the library's
+The correction step itself (the rest of Algorithm 2) runs in the library's
 kernels; nothing here stands in for one of them.  The paper solves this
 system by Newton's method with GMRES and a geometric multigrid
 preconditioner (Sec. 3.3); on the meshes that time loops and training data
@@ -361,8 +361,8 @@ def dnnmg_run(coarse, correct, steps, x0=None, t0=0.0, b0=None, newton="exact"):
     """Algorithm 2 over `steps` time steps: [x_c(t_1), ..., x_c(t_steps)].
 
     Each step solves the coarse system at t_n = t0 + n k with the right-hand
-    side b_c handed on by the previous step (line 5), then calls
-    correct(x_c, t_n) -> b_c for lines 6-9 (prolongation, network correction,
+    side b_c handed on by the previous step (the coarse solve), then calls
+    correct(x_c, t_n) -> b_c for the correction (prolongation, network correction,
     fine right-hand side, restriction), whose result the next solve uses.
     The first right-hand side is b0 ([2 or 3][N]), by default the coarse
     Rhs(x0) (x0 = 0: the fluid at rest).

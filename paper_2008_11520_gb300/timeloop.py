@@ -1,8 +1,8 @@
 """DNN-MG time stepping end to end (Algorithm 2): host coarse solve, library correction.
 
 Each time step solves the coarse level's Crank-Nicolson system on the host in
-FP64 (line 5, ``solver.Level.solve``), then runs the correction step
-(lines 6-9: prolongation, residual and features, GRU network, averaging,
+FP64 (the coarse solve, ``solver.Level.solve``), then runs the correction step
+(prolongation, residual and features, GRU network, averaging,
 fine right-hand side, restriction) in one ``dnnmg_step`` call on the GPU,
 whose restricted right-hand side the next coarse solve uses.  The GRU state
 and the fine right-hand side stay on the device between steps; only x_c goes

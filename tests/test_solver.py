@@ -1,4 +1,4 @@
-"""The host level solver (Algorithm 2 line 5 and the fine reference solve).
+"""The host level solver (the coarse solve of Algorithm 2 and the fine reference solve).
 
 The solver is supporting code outside the correction step; these tests pin
 it to the oracle's definition of the discrete system and to what the

@@ -1,7 +1,7 @@
 """Algorithm 2 end to end on the GPU: host coarse solve, library correction step.
 
-The loop's correction (lines 6-9) goes through the C ABI, the coarse solve
-(line 5) is the host solver pinned in test_solver.py.  The whole trajectory
+The loop's correction step goes through the C ABI; its coarse solve is the
+host solver pinned in test_solver.py.  The whole trajectory
 must match the same loop driven by the oracle's step, and a network trained
 on solved flows must lower E_rel(v) on a held-out flow, both with the coarse
 solutions given and inside the loop.
