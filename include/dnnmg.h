@@ -391,8 +391,8 @@ void dnnmg_pool_destroy(dnnmg_pool_t pool);
  *
  * Forward and backward of Eq. gru followed by the output layer (Sec. 6.2),
  * unrolled over a window of T steps of P patch rows, for truncated
- * backpropagation through time; the l2 loss of Sec. 6.5 and its gradient;
- * Adam with the Tikhonov term of Sec. 6.5.  FP32 throughout (CUDA cores);
+ * backpropagation through time; the l2 loss of Sec. 6.3 and its gradient;
+ * Adam with the Tikhonov term of Sec. 6.3.  FP32 throughout (CUDA cores);
  * weight-gradient sums are split over the T P rows in a fixed order, so
  * results repeat bit for bit.  All arrays are caller-owned device memory:
  *   X [T][P][ldx] (columns n_in..ldx-1 ignored), h0 / dh0 [P][H],
@@ -418,7 +418,7 @@ int dnnmg_gru_seq_state(dnnmg_trainer_t trainer, float **hT);
 int dnnmg_gru_seq_backward(dnnmg_trainer_t trainer, const float *dD, const float *X, const float *Uh, const float *Wfc,
                            float *gWx, float *gUh, float *gWfc, float *dh0, cudaStream_t stream);
 /*
- * Loss of Sec. 6.5 over n = T P n_out outputs: *loss (device double) =
+ * Loss of Sec. 6.3 over n = T P n_out outputs: *loss (device double) =
  * sum (D - Y)^2 / P, and dD = 2 (D - Y) / P if dD is not NULL.
  */
 int dnnmg_l2_loss(const float *D, const float *Y, long long n, int P, float *dD, double *loss, cudaStream_t stream);

@@ -7,7 +7,7 @@ residual on the fine patch nodes (3 components), the coarse velocities and
 Peclet numbers on the coarse patch nodes, and 12 geometry values of the patch
 (4 edge lengths, 4 aspect ratios, 4 angles).  For one-cell patches and K = 1
 that is 27 + 8 + 4 + 12 = 51 inputs, as the paper counts; for K = 2 it is 99
-(Sec. 6.5).
+(Sec. 6.6).
 
 Order of one feature row (a reading; the paper fixes the content, not the order):
   [ r_u(fine patch nodes), r_v(...), r_p(...),

@@ -1,5 +1,5 @@
 """Oracle for training the patch network: the GRU of Eq. gru
-unrolled over a window of time steps, the l2 training loss of Sec. 6.5 with
+unrolled over a window of time steps, the l2 training loss of Sec. 6.3 with
 Tikhonov regularisation, its gradient by backpropagation through time, and one
 Adam update.
 
@@ -13,7 +13,7 @@ Network (as ``oracle.gru``): per patch row and step t = 1..T,
     h_t  = z_t * h_{t-1} + (1 - z_t) * c_t
     d_t  = W_fc h_t
 
-Loss (Sec. 6.5, read as the squared l2 norm; the printed norm is unsquared):
+Loss (Sec. 6.3, read as the squared l2 norm; the printed norm is unsquared):
 the sum over the window's steps of the mean over patches of
 |d_t - y_t|^2, with the target y_t = v_bar - v~ on the patch's fine nodes (so
 that v~ + d - v_bar = d - y), plus alpha (|W_x|^2 + |U|^2 + |W_fc|^2).

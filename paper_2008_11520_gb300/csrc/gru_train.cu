@@ -1,4 +1,4 @@
-// Training the patch network (Eq. gru + output layer, Sec. 6.2 and 6.5):
+// Training the patch network (Eq. gru + output layer, Sec. 6.2 and 6.3):
 // the GRU unrolled over a window of T steps, and its gradient by truncated
 // backpropagation through time, in FP32 on the CUDA cores.
 //

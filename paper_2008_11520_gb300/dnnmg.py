@@ -596,7 +596,7 @@ class Trainer:
 
 
 def dnnmg_l2_loss(D, Y, P, dD=None, stream=None):
-    """Loss of Sec. 6.5 (device double tensor of one element) and, optionally, dD."""
+    """Loss of Sec. 6.3 (device double tensor of one element) and, optionally, dD."""
     _need(Y, torch.float32, D.numel(), "Y")
     if dD is not None:
         _need(dD, torch.float32, D.numel(), "dD")

@@ -5,7 +5,7 @@ Supporting code around the correction step, not part of it:
 * the coarse solve of Algorithm 2, which the correction step feeds with
   its restricted right-hand side and which feeds the next step with x_c;
 * the plain fine-level time stepping whose velocities are the ground truth
-  the network is trained towards (Sec. 5.3, "Training of DNN-MG").
+  the network is trained towards (Sec. 5.2, "Training of DNN-MG").
 
 The correction step itself (the rest of Algorithm 2) runs in the library's
 kernels; nothing here stands in for one of them.  The paper solves this
@@ -379,7 +379,7 @@ def dnnmg_run(coarse, correct, steps, x0=None, t0=0.0, b0=None, newton="exact"):
 
 
 def generate_flows(nxc, nyc, K, steps, ratios, a_x=0.05, centre=(0.2, 0.2), newton="chord", **params):
-    """Training flows of Sec. 5.3: for each axis ratio a_y / a_x of the elliptic
+    """Training flows of Sec. 5.2: for each axis ratio a_y / a_x of the elliptic
     obstacle, the fine-level (L+K) solution and the plain coarse-level solution
     of the start-up flow over `steps` steps.
 

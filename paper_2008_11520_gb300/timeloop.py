@@ -9,7 +9,7 @@ and the fine right-hand side stay on the device between steps; only x_c goes
 down and b_c comes back.
 
 ``python -m paper_2008_11520_gb300.timeloop`` trains the patch network on
-solved flows of a small channel and prints E_rel(v) (Sec. 6.6) of the method
+solved flows of a small channel and prints E_rel(v) (Sec. 6.4) of the method
 with the trained and with a zero network against the plain fine-level solve
 (``accuracy_experiment``).
 """
@@ -87,7 +87,7 @@ def fine_level(mesh_desc):
 
 
 def e_rel(v, ref):
-    """|v - v_bar| / |v_bar| over the fine velocity DOFs (Sec. 6.6)."""
+    """|v - v_bar| / |v_bar| over the fine velocity DOFs (Sec. 6.4)."""
     return float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
 
 
@@ -117,12 +117,12 @@ def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1
                         epochs=300, lr=1e-3, seed=0):
     """Train the patch network on solved flows and measure what it gains.
 
-    The paper's accuracy study (Sec. 6.5-6.6) in small: fine-level (L+K)
+    The paper's accuracy study (Sec. 6.3-6.4) in small: fine-level (L+K)
     solutions of the start-up flow at the inflow peaks u_train are the
     ground truth, plain coarse-level solutions the network's inputs
     (``train.solution_windows``); windows of T steps, Adam with the Tikhonov
     term, the state carried from one window to the next.  On a flow with the
-    held-out peak u_held it reports E_rel(v) (Sec. 6.6, fine velocity DOFs,
+    held-out peak u_held it reports E_rel(v) (Sec. 6.4, fine velocity DOFs,
     mean over the steps):
 
     * ``teacher``: v~ + d_bar on the plain coarse solutions, trained net vs d = 0;

@@ -3,9 +3,9 @@
 * ``GruWindow`` -- a ``torch.autograd.Function`` whose forward and backward are
   libdnnmg's GRU window kernels (Eq. gru + output layer unrolled over T steps,
   gradient by truncated backpropagation through time).
-* ``L2Loss`` -- the loss of Sec. 6.5 (sum over steps of the mean over patches
+* ``L2Loss`` -- the loss of Sec. 6.3 (sum over steps of the mean over patches
   of |d - y|^2) as an autograd function on the library's loss kernel.
-* ``PatchNetTrainer`` -- FP32 weights, Adam (Sec. 6.5) with the Tikhonov
+* ``PatchNetTrainer`` -- FP32 weights, Adam (Sec. 6.3) with the Tikhonov
   term alpha = 1e-4, one update per window.
 * ``flow_windows`` -- training windows from synthetic flows, built with the
   library's own S1 and S2+S3 kernels: features of x~ = P x_c(t_n) with the
@@ -19,7 +19,7 @@
   solution of ``solver`` as v_bar and a coarse solution (the fine one at the
   coarse nodes, ``coarse_nodes``, or a coarse-level simulation) as x_c, the
   paper's two-level training data.
-* ``e_rel`` -- E_rel(v) of Sec. 6.6 for a net, through the inference path
+* ``e_rel`` -- E_rel(v) of Sec. 6.4 for a net, through the inference path
   (dnnmg_gru_step, dnnmg_scatter_avg).
 
 Every arithmetic step of training runs in libdnnmg kernels; torch provides
@@ -54,7 +54,7 @@ class GruWindow(torch.autograd.Function):
 
 
 class L2Loss(torch.autograd.Function):
-    """sum over steps of the mean over the P patches of |D - Y|^2 (Sec. 6.5)."""
+    """sum over steps of the mean over the P patches of |D - Y|^2 (Sec. 6.3)."""
 
     @staticmethod
     def forward(ctx, D, Y, P):
@@ -172,7 +172,7 @@ def flow_windows(mesh, spec, nsteps, k=synth.DT, t0=0.0):
 def solution_windows(mesh, fine_states, coarse_states, k=synth.DT, t0=0.0):
     """Features X [T][P][ldx] and targets Y [T][P][n_out] from solved flows.
 
-    The training data of Sec. 5.3 ("Training of DNN-MG"): fine_states =
+    The training data of Sec. 5.2 ("Training of DNN-MG"): fine_states =
     [x_bar(t_0), ..., x_bar(t_T)], the fine-level solution (node-ordered
     [3][Nf] float64, e.g. ``solver.simulate`` on the fine level; entry 0 is
     the state before the window), and coarse_states = [x_c(t_1), ...,

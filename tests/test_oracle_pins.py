@@ -33,7 +33,7 @@ def test_c1_solid_cells_by_hand():
 
 def test_feature_and_output_lengths_match_paper():
     # Sec. 5.2: 51 inputs for one-cell patches on level L+1; Sec. 6.2: 18 outputs;
-    # Sec. 6.5: 99 inputs and 50 outputs across two levels.
+    # Sec. 6.6: 99 inputs and 50 outputs across two levels.
     m1 = Mesh(8, 4, 1, 1)
     assert (m1.n_in, m1.n_out) == (51, 18)
     m2 = Mesh(8, 4, 2, 1)
@@ -44,7 +44,7 @@ def test_param_counts_match_paper():
     # Sec. 6.2: 3(32*32 + 32*51) = 7968 GRU and 32*18 = 576 output weights.
     assert 3 * 32 * (32 + 51) == 7968
     assert gru.param_count(51, 32, 18) == 7968 + 576
-    # Sec. 6.5: N_GRU = 96 with 99 inputs and 50 outputs has 60 960 parameters.
+    # Sec. 6.6: N_GRU = 96 with 99 inputs and 50 outputs has 60 960 parameters.
     assert gru.param_count(99, 96, 50) == 60960
 
 

@@ -1,6 +1,6 @@
 """Training kernels of the patch network on the GPU.
 
-The GRU window's forward and backward (truncated BPTT), the loss of Sec. 6.5
+The GRU window's forward and backward (truncated BPTT), the loss of Sec. 6.3
 and Adam are compared with the FP64 training oracle (itself pinned by finite
 differences); the autograd function must give the kernels' gradients; and a
 net trained on synthetic flows must lower E_rel(v) on a held-out flow below
