@@ -1,0 +1,122 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Each case patches one plausible slip into an oracle function (on the CPU,
+for the duration of the test) and runs pins that should catch it: a pin set
+that passes a wrong oracle pins nothing.
+"""
+
+import numpy as np
+import pytest
+
+import test_oracle_assembly as assembly
+import test_oracle_pins as pins
+from oracle import fem, gru, transfer
+
+
+def _fails(checks):
+    for check in checks:
+        try:
+            check()
+        except AssertionError:
+            return True
+    return False
+
+
+def _assembly_pins():
+    return [lambda n=n: assembly.test_residual_equals_dense_assembly(n) for n in sorted(assembly.MESHES)] + \
+           [lambda n=n: assembly.test_rhs_equals_dense_assembly(n) for n in sorted(assembly.MESHES)]
+
+
+def _zero_step_pins():
+    return [lambda K=K, s=s: pins.test_zero_correction_step_gives_coarse_rhs(K, s)
+            for K in (1, 2) for s in (1, 2)]
+
+
+def _gru_pins():
+    return [pins.test_gru_hand_derived, pins.test_gru_recurrent_gates_and_zero_weights]
+
+
+def _lps_pins():
+    return [pins.test_lps_energy_closed_form, pins.test_lps_orthogonal_to_patchwise_bilinear] + _assembly_pins()
+
+
+def _mutants():
+    o_pi, o_vop, o_shape = fem.lps_projection_matrix, fem.velocity_operator, fem.q1_shape
+    o_rhs_raw, o_restrict_1d, o_pro = fem.rhs_raw, transfer._restrict_1d, transfer.prolongate_raw
+
+    def vop_pressure_sign(mesh, prm, t):
+        Au, Av = o_vop(mesh, prm, t)
+        return Au + 2 * t["pres_u"], Av + 2 * t["pres_v"]
+
+    def vop_full_convection(mesh, prm, t):
+        Au, Av = o_vop(mesh, prm, t)
+        return Au + 0.5 * t["conv_u"], Av + 0.5 * t["conv_v"]
+
+    def vop_full_viscosity(mesh, prm, t):
+        Au, Av = o_vop(mesh, prm, t)
+        return Au + 0.5 * prm.nu * t["diff_u"], Av + 0.5 * prm.nu * t["diff_v"]
+
+    def rhs_convection_sign(mesh, prm, t):
+        bu, bv = o_rhs_raw(mesh, prm, t)
+        return bu + t["conv_u"], bv + t["conv_v"]
+
+    def shape_swapped(xi, eta):
+        phi, dx, dy = o_shape(xi, eta)
+        return phi, dy, dx
+
+    def prolongate_shifted(mesh, xc):
+        x = o_pro(mesh, xc)
+        return x + 1e-3 * (np.arange(x.shape[1]) % 3 == 1)
+
+    def gru_reset_after_product(X, h, Wx, Uh, Wfc):
+        # the variant that applies the reset gate after the recurrent product
+        X, h = np.asarray(X, dtype=np.float64), np.asarray(h, dtype=np.float64)
+        H = h.shape[1]
+        z = gru.sigmoid(X @ Wx[0:H].T + h @ Uh[0:H].T)
+        r = gru.sigmoid(X @ Wx[H:2 * H].T + h @ Uh[H:2 * H].T)
+        cand = np.tanh(X @ Wx[2 * H:].T + r * (h @ Uh[2 * H:].T))
+        h_new = z * h + (1.0 - z) * cand
+        return h_new, h_new @ np.asarray(Wfc).T
+
+    def lps_without_test_projection(mesh, prm, p, nq=2):
+        # projects the pressure but not the test function
+        nxn = mesh.wxf + 1
+        F = np.eye(9) - fem.lps_projection_matrix()
+        L = fem.lps_patch_stiffness(mesh.hxf, mesh.hyf, nq)
+        blk = mesh.solid_f.reshape(mesh.wyf // 2, 2, mesh.wxf // 2, 2)
+        n, m = np.nonzero(~blk.any(axis=(1, 3)))
+        offs = np.array([b * nxn + a for b in range(3) for a in range(3)])
+        nodes = ((2 * n) * nxn + 2 * m)[:, None] + offs[None, :]
+        out = np.zeros(mesh.Nf)
+        np.add.at(out, nodes, fem.lps_alpha(mesh, prm) * (p[nodes] @ F.T) @ L.T)
+        return out
+
+    return {
+        "reset gate after the recurrent product": (gru, "gru_step", gru_reset_after_product, _gru_pins),
+        "projection of the test function dropped": (fem, "lps_term", lps_without_test_projection, _lps_pins),
+        "projection transposed": (fem, "lps_projection_matrix", lambda: o_pi().T, _assembly_pins),
+        "pressure term sign": (fem, "velocity_operator", vop_pressure_sign, _assembly_pins),
+        "convection weight 1 not 1/2": (fem, "velocity_operator", vop_full_convection, _assembly_pins),
+        "viscosity nu not nu/2": (fem, "velocity_operator", vop_full_viscosity, _assembly_pins),
+        "alpha from h_x alone": (fem, "lps_alpha", lambda m, p: p.alpha0 * m.hxf ** 2 / p.nu, _assembly_pins),
+        "x and y derivatives swapped": (fem, "q1_shape", shape_swapped, _assembly_pins),
+        "right-hand side convection sign": (fem, "rhs_raw", rhs_convection_sign, _assembly_pins),
+        "restriction weights scaled": (transfer, "_restrict_1d", lambda v, axis: 1.01 * o_restrict_1d(v, axis),
+                                       _zero_step_pins),
+        "prolongation perturbed": (transfer, "prolongate_raw", prolongate_shifted, _zero_step_pins),
+        "inexact quadrature": (fem, "gauss_1d", lambda nq: (np.array([0.25, 0.75]), np.array([0.5, 0.5])),
+                               _zero_step_pins),
+    }
+
+
+MUTANTS = _mutants()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(name, monkeypatch):
+    module, attr, wrong, checks = MUTANTS[name]
+    # the pins hold for the oracle as written ...
+    assert not _fails(checks())
+    # ... and fail with the mistake planted
+    monkeypatch.setattr(module, attr, wrong)
+    assert _fails(checks()), f"no pin caught: {name}"
