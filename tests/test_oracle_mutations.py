@@ -10,7 +10,9 @@ import pytest
 
 import test_oracle_assembly as assembly
 import test_oracle_pins as pins
+import test_train_oracle as tpins
 from oracle import fem, gru, transfer
+from oracle import train as otrain
 
 
 def _fails(checks):
@@ -38,6 +40,11 @@ def _gru_pins():
 
 def _lps_pins():
     return [pins.test_lps_energy_closed_form, pins.test_lps_orthogonal_to_patchwise_bilinear] + _assembly_pins()
+
+
+def _train_pins():
+    return [lambda a=a: tpins.test_bptt_gradient_matches_finite_differences(a) for a in (0.0, 1e-4)] + \
+           [tpins.test_gradient_of_a_single_step_by_hand, tpins.test_adam_closed_forms]
 
 
 def _mutants():
@@ -91,7 +98,26 @@ def _mutants():
         np.add.at(out, nodes, fem.lps_alpha(mesh, prm) * (p[nodes] @ F.T) @ L.T)
         return out
 
+    o_grad_D, o_backward, o_adam = otrain.loss_grad_D, otrain.seq_backward, otrain.adam_step
+
+    def backward_without_reset_recurrence(dD, cache, Wx, Uh, Wfc):
+        gWx, gUh, gWfc, dh0 = o_backward(dD, cache, Wx, Uh, Wfc)
+        H = Uh.shape[1]
+        gUh = gUh.copy()
+        gUh[H:2 * H] = 0.0
+        return gWx, gUh, gWfc, dh0
+
+    def adam_without_bias_correction(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + (1.0 - b1) * g
+        v = b2 * v + (1.0 - b2) * g * g
+        return p - lr * m / (np.sqrt(v) + eps), m, v
+
     return {
+        "loss gradient without its factor 2": (otrain, "loss_grad_D", lambda D, Y: 0.5 * o_grad_D(D, Y),
+                                               _train_pins),
+        "reset-gate recurrent gradient dropped": (otrain, "seq_backward", backward_without_reset_recurrence,
+                                                  _train_pins),
+        "Adam without bias correction": (otrain, "adam_step", adam_without_bias_correction, _train_pins),
         "reset gate after the recurrent product": (gru, "gru_step", gru_reset_after_product, _gru_pins),
         "projection of the test function dropped": (fem, "lps_term", lps_without_test_projection, _lps_pins),
         "projection transposed": (fem, "lps_projection_matrix", lambda: o_pi().T, _assembly_pins),
