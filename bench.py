@@ -72,7 +72,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -233,6 +233,55 @@ def run_ours(args, rank, world, local_rank):
                 e2e_ms=e2e_ms, wall=wall, launches=dnnmg.dnnmg_step_launches(mesh, net))
 
 
+def blas_threads():
+    """Threads of the BLAS library NumPy loaded, read from the library itself
+    (threadpoolctl when installed, else the OpenBLAS query symbol), or None."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i["num_threads"] for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except ImportError:
+        pass
+    import ctypes
+    try:
+        with open("/proc/self/maps") as f:
+            libs = sorted({ln.split()[-1] for ln in f if "openblas" in ln.lower() and ".so" in ln})
+    except OSError:
+        libs = []
+    for path in libs:
+        try:
+            so = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for sym in ("openblas_get_num_threads", "openblas_get_num_threads64_", "scipy_openblas_get_num_threads64_",
+                    "scipy_openblas_get_num_threads"):
+            fn = getattr(so, sym, None)
+            if fn is not None:
+                fn.restype = ctypes.c_int
+                return int(fn())
+    return None
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(seconds=12.0):
     """The oracle as it stands on a window of the large workload; fine DOF/s."""
     from oracle.mesh import Mesh as OMesh, Params
@@ -258,21 +307,55 @@ def cpu_baseline(seconds=12.0):
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    threads = blas_threads()
     return {"value": 2 * om.Nf * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} steps of a 64x64-coarse-cell window ({om.Nf} fine nodes) of the workload, "
-                      f"{el:.1f} s; NumPy FP64, BLAS threads up to {threads}",
-            "steps": n, "seconds": el}
+            "sample": f"{n} steps of a 64x64-coarse-cell window ({om.Nf} fine nodes, {2 * om.Nf} velocity DOF) of "
+                      f"the workload in {el:.1f} s; the rate is that window's DOF over its step time",
+            "steps": n, "seconds": el, "blas_threads": threads, "window_nodes": om.Nf}
+
+
+def cpu_baseline_runs(seconds=12.0):
+    """cpu_baseline at one thread and at every host core, each in a fresh
+    interpreter whose BLAS/OpenMP thread counts are set before NumPy loads."""
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    runs = {}
+    for threads in (1, ncores):
+        env = dict(os.environ)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[var] = str(threads)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", str(seconds)],
+                           env=env, capture_output=True, text=True, timeout=30 * seconds + 300)
+        if r.returncode:
+            raise RuntimeError(f"cpu baseline worker failed:\n{r.stderr[-2000:]}")
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        d["threads_requested"] = threads
+        runs[threads] = d
+    one, allc = runs[1], runs[ncores]
+    model = cpu_model()
+    used = allc["blas_threads"] if allc["blas_threads"] is not None else ncores
+    return {"value": allc["value"], "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": (f"{allc['sample']}; all {ncores} cores of a {model} host (BLAS threads in force: "
+                       f"{allc['blas_threads']}); at 1 thread (BLAS threads {one['blas_threads']}): "
+                       f"{one['value']:.4g} DOF/s over {one['steps']} steps"),
+            "cpu_model": model, "host_cores": ncores,
+            "one_thread": {"value": one["value"], "blas_threads": one["blas_threads"], "steps": one["steps"],
+                           "seconds": one["seconds"]},
+            "all_cores": {"value": allc["value"], "blas_threads": allc["blas_threads"], "steps": allc["steps"],
+                          "seconds": allc["seconds"]}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-worker", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_baseline_worker is not None:
+        print(json.dumps(cpu_baseline(seconds=args.cpu_baseline_worker)))
+        return
     args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -290,14 +373,18 @@ def main():
             steps.append(cpu_baseline(seconds=2.0))
         v = sum(s["value"] * s["seconds"] for s in steps) / sum(s["seconds"] for s in steps)
         base = steps[0]
+        ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * sum(s["seconds"] for s in steps) / sum(s["steps"] for s in steps),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": {"workload": WORKLOAD + ": " + describe(c),
                                                 "sample": "64x64-coarse-cell window per step, CPU oracle"},
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
-                                 "sample": base["sample"]},
+                "cpu_baseline": {"value": v, "unit": UNIT,
+                                 "cores": base["blas_threads"] if base["blas_threads"] is not None else ncores,
+                                 "kind": "oracle", "cpu_model": cpu_model(), "host_cores": ncores,
+                                 "sample": base["sample"] + f"; one such window per step, {ncores} host cores, "
+                                                            f"BLAS threads in force {base['blas_threads']}"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -356,8 +443,7 @@ def main():
         "roofline": roof, "stages": stages, "clocks": r["clocks"],
     }
     if world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline()
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = cpu_baseline_runs()
     print(json.dumps(line))
 
 

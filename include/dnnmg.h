@@ -286,11 +286,16 @@ int dnnmg_net_uses_tensor_cores(dnnmg_net_t net);
  * (features, predictions, corrected velocity) lives in a library-owned
  * static device array of dnnmg_static_scratch_bytes() bytes (64 MiB), which
  * every GPU that loads the library holds until the process exits.  The
- * call allocates nothing; meshes whose info.workspace_bytes exceed the array
- * are rejected with DNNMG_EINVAL and a message (use dnnmg_step then).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls on a device share the one array and it keeps
+ * call allocates nothing.  A mesh needs dnnmg_static_scratch_needed() bytes
+ * of it (its workspace without the host-call staging of x_c and b_c, which
+ * this call never uses); larger meshes are rejected with DNNMG_EINVAL and a
+ * message (use dnnmg_step then).
+ * The first call on a device, in a given CUDA context, looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it under that device and
+ * context; make that first call before any stream capture.  A cached
+ * address is checked before each use, so a context created after a
+ * cudaDeviceReset (or a second context on the device) gets its own lookup.
+ * All calls on a device share the one array and it keeps
  * the last call's contents: calls that can overlap on the GPU (different
  * streams, different host threads) race on it and must be serialised by
  * the caller.  Nothing in it needs clearing between calls.  Arguments and
@@ -301,6 +306,21 @@ int dnnmg_step_static(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void
 
 /* Size in bytes of the static scratch used by dnnmg_step_static. */
 size_t dnnmg_static_scratch_bytes(void);
+
+/* Bytes of the static scratch that dnnmg_step_static needs for this mesh
+ * (0 for a NULL mesh).  No counterpart in the paper. */
+size_t dnnmg_static_scratch_needed(dnnmg_mesh_t mesh);
+
+/*
+ * Byte offsets, inside a dnnmg_step workspace, of the arrays the step leaves
+ * there (valid once the stream has reached the end of the step): *x the
+ * features X [P][ldx] (S3), *d the network output [P][n_out] (S4), *vcorr
+ * the corrected fine velocity v~ + d_bar [2][plane] (S5), each in the mesh's
+ * real type (X in the feature type).  No counterpart in the paper: it lets a
+ * caller inspect the step's correction, as the parity tests do.  Host-only,
+ * synchronous; DNNMG_EINVAL on NULL arguments.
+ */
+int dnnmg_workspace_offsets(dnnmg_mesh_t mesh, long long *x, long long *d, long long *vcorr);
 
 /* Number of kernel launches one dnnmg_step enqueues for this mesh/net. */
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net);

@@ -663,8 +663,14 @@ int dnnmg_mesh_status(dnnmg_mesh_t mesh, int *status, int reset) {
     return DNNMG_OK;
 }
 
+// Bytes of the workspace that the device-buffer step uses: all of it but the
+// staging of x_c and b_c, which only dnnmg_step_host's pageable path needs.
+static size_t device_step_bytes(const dnnmg_mesh_info &I) {
+    return I.workspace_bytes - 2 * align256(3 * (size_t)I.Nc * sizeof(double));
+}
+
 static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, void *workspace,
-                       size_t workspace_bytes) {
+                       size_t workspace_bytes, bool device_only = false) {
     if (int e = check_mesh(mesh)) return e;
     if (!net) return fail(DNNMG_EINVAL, "net handle is NULL");
     const dnnmg_mesh_info &I = mesh->info;
@@ -677,8 +683,8 @@ static int step_checks(dnnmg_mesh_t mesh, dnnmg_net_t net, void *h, void *bf, vo
     // h has P rows: a mesh without fluid patches has no state
     if ((!h && I.P > 0) || !bf || !workspace) return fail(DNNMG_EINVAL, "NULL array");
     if (!aligned16(bf) || !aligned16(h)) return fail(DNNMG_EINVAL, "bf and h must be 16-byte aligned");
-    if (workspace_bytes < I.workspace_bytes)
-        return fail(DNNMG_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, I.workspace_bytes);
+    const size_t need = device_only ? device_step_bytes(I) : I.workspace_bytes;
+    if (workspace_bytes < need) return fail(DNNMG_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, need);
     if (reinterpret_cast<uintptr_t>(workspace) % 256)
         return fail(DNNMG_EINVAL, "workspace must be 256-byte aligned");
     return DNNMG_OK;
@@ -719,10 +725,13 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
 }  // extern "C"
 
 namespace dnnmg {
-// dnnmg_step with the checks done on the given workspace (used by step_static.cu).
+size_t step_scratch_bytes(const dnnmg_mesh_info &I) { return device_step_bytes(I); }
+
+// dnnmg_step with the checks done on the given scratch (used by step_static.cu):
+// the scratch needs only the device step's part of a workspace.
 int step_on_workspace(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
                       void *workspace, size_t workspace_bytes, double t, cudaStream_t stream) {
-    if (int e = step_checks(mesh, net, h, bf, workspace, workspace_bytes)) return e;
+    if (int e = step_checks(mesh, net, h, bf, workspace, workspace_bytes, true)) return e;
     if (!xc || !bc) return fail(DNNMG_EINVAL, "NULL array");
     return step_body(mesh, net, xc, h, bf, bc, carve(mesh->info, workspace), t, stream);
 }
@@ -775,6 +784,16 @@ int dnnmg_step_timed(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
     if (n_events != dnnmg_step_launches(mesh, net) + 1)
         return fail(DNNMG_EINVAL, "%d events given, the step needs %d", n_events, dnnmg_step_launches(mesh, net) + 1);
     return step_body(mesh, net, xc, h, bf, bc, carve(mesh->info, workspace), t, stream, events);
+}
+
+int dnnmg_workspace_offsets(dnnmg_mesh_t mesh, long long *x, long long *d, long long *vcorr) {
+    clear_error();
+    if (!mesh || !x || !d || !vcorr) return fail(DNNMG_EINVAL, "NULL argument");
+    const Workspace w = carve(mesh->info, nullptr);
+    *x = static_cast<long long>(reinterpret_cast<uintptr_t>(w.X));
+    *d = static_cast<long long>(reinterpret_cast<uintptr_t>(w.d));
+    *vcorr = static_cast<long long>(reinterpret_cast<uintptr_t>(w.vc));
+    return DNNMG_OK;
 }
 
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net) {

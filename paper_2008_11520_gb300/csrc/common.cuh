@@ -166,7 +166,9 @@ int feature_table_capacity();
 // within two cells of the tile exists and is fluid, bit 1 = the same within one.
 void tile_flags(const MeshGeom &g, const uint8_t *solid, uint8_t *flags);
 void tile_counts(const MeshGeom &g, int *ntx, int *nty);
-// dnnmg_step on a caller-chosen workspace (argument checks included).
+// Scratch bytes of the device-buffer step (the workspace minus the host-call staging).
+size_t step_scratch_bytes(const dnnmg_mesh_info &I);
+// dnnmg_step on a caller-chosen scratch of at least step_scratch_bytes (argument checks included).
 int step_on_workspace(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
                       void *workspace, size_t workspace_bytes, double t, cudaStream_t stream);
 

@@ -81,6 +81,8 @@ def _load():
         "dnnmg_rhs": [P, P, P, P],
         "dnnmg_scatter_rhs": [P, P, P, D, P, P],
         "dnnmg_step_static": [P, P, P, P, P, P, D, P],
+        "dnnmg_workspace_offsets": [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_longlong)],
         "dnnmg_net_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_mesh_status": [P, ctypes.POINTER(ctypes.c_int), I],
         "dnnmg_net_uses_tensor_cores": [P],
@@ -116,6 +118,8 @@ def _load():
     lib.dnnmg_pool_destroy.restype = None
     lib.dnnmg_static_scratch_bytes.argtypes = []
     lib.dnnmg_static_scratch_bytes.restype = ctypes.c_size_t
+    lib.dnnmg_static_scratch_needed.argtypes = [P]
+    lib.dnnmg_static_scratch_needed.restype = ctypes.c_size_t
     lib.dnnmg_last_error.argtypes = []
     lib.dnnmg_last_error.restype = ctypes.c_char_p
     return lib
@@ -230,6 +234,15 @@ class Mesh:
 
     def workspace(self, device="cuda"):
         return torch.empty(self.info.workspace_bytes, dtype=torch.uint8, device=device)
+
+    def step_outputs(self, workspace):
+        """Views of the network output d [P][n_out] and of v_corr [2][plane]
+        that dnnmg_step leaves in its workspace (read after the step)."""
+        _, od, ov = dnnmg_workspace_offsets(self)
+        I, nb = self.info, self.info.real_bytes
+        d = workspace[od:od + I.P * I.n_out * nb].view(self.real).view(I.P, I.n_out)
+        vc = workspace[ov:ov + 2 * I.plane * nb].view(self.real).view(2, I.plane)
+        return d, vc
 
 
 class Net:
@@ -417,6 +430,17 @@ def dnnmg_step_static(mesh, net, xc, h, bf, bc, t, stream=None):
 
 def dnnmg_static_scratch_bytes():
     return _lib.dnnmg_static_scratch_bytes()
+
+
+def dnnmg_static_scratch_needed(mesh):
+    return _lib.dnnmg_static_scratch_needed(mesh.handle)
+
+
+def dnnmg_workspace_offsets(mesh):
+    """Byte offsets (X, d, v_corr) of what dnnmg_step leaves in its workspace."""
+    x, d, v = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.dnnmg_workspace_offsets(mesh.handle, ctypes.byref(x), ctypes.byref(d), ctypes.byref(v)))
+    return x.value, d.value, v.value
 
 
 def dnnmg_step_host(mesh, net, xc_host, h, bf, bc_host, workspace, t, stream=None):

@@ -70,6 +70,57 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
+def node_classes(om):
+    """Masks [wyf+1][wxf+1] of non-Dirichlet fine nodes next to each kind of boundary.
+
+    Whole-field relative L2 can hide a few bad nodes beside a boundary, so the
+    parity tests also bound the error on these classes one by one: the column
+    after the inflow, the rows beside the walls, the do-nothing outflow
+    column, and the nodes beside the obstacle's no-slip nodes.  Indices are
+    global, so windows of a larger mesh get the classes of the full mesh.
+    """
+    gI, gJ = np.meshgrid(np.arange(om.fi0, om.fi0 + om.wxf + 1), np.arange(om.fj0, om.fj0 + om.wyf + 1))
+    free = ~om.dirichlet
+    obst = om.zero_bc & (gJ > 0) & (gJ < om.nyf)      # no-slip nodes of solid cells
+    near = np.zeros_like(obst)
+    pad = np.pad(obst, 1)
+    ny, nx = obst.shape
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            near |= pad[1 + dj:1 + dj + ny, 1 + di:1 + di + nx]
+    cls = {
+        "inflow-adjacent": free & (gI == 1),
+        "wall-adjacent": free & ((gJ == 1) | (gJ == om.nyf - 1)),
+        "outflow": free & (gI == om.nxf),
+        "obstacle-adjacent": free & near,
+    }
+    edge = np.zeros_like(free)
+    for m in cls.values():
+        edge |= m
+    cls["interior"] = free & ~edge
+    return cls
+
+
+def class_errors(got, ref, om, region=None):
+    """max |got - ref| over each node class, divided by the RMS of ref.
+
+    got, ref: fine fields [ncomp][wyf+1][wxf+1] (or flattened planes); region
+    (optional): mask of the nodes where the comparison is exact (windows).
+    Classes with no node in the region are left out.
+    """
+    shape = (om.wyf + 1, om.wxf + 1)
+    got = np.asarray(got, dtype=np.float64).reshape((-1,) + shape)
+    ref = np.asarray(ref, dtype=np.float64).reshape((-1,) + shape)
+    reg = np.ones(shape, dtype=bool) if region is None else region
+    rms = float(np.sqrt(np.mean(ref[:, reg] ** 2)))
+    out = {}
+    for name, m in node_classes(om).items():
+        m = m & reg
+        if m.any():
+            out[name] = float(np.abs(got[:, m] - ref[:, m]).max() / (rms if rms > 0 else 1.0))
+    return out
+
+
 def np_dtype(prec):
     return np.float64 if prec == "f64" else np.float32
 
@@ -102,4 +153,4 @@ def weights(case, n_in, n_out, seed=17):
 
 
 __all__ = ["CASES", "TOL", "Params", "oracle_mesh", "rel_l2", "np_dtype", "coarse_input",
-           "fine_velocity", "rhs_like", "weights", "mask_for", "spec_for"]
+           "fine_velocity", "rhs_like", "weights", "mask_for", "spec_for", "node_classes", "class_errors"]

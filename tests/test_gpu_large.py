@@ -1,8 +1,8 @@
 """Parity at the full workload sizes, in the launch configuration the
 benchmark times (dnnmg_step on the whole mesh).
 
-* 256 x 64 coarse cells, K = 2, H = 64 (FP32 and BF16 networks): the oracle
-  runs on the whole mesh.
+* 256 x 64 coarse cells, K = 2, H = 64 (FP32 and BF16 networks), over the
+  workload's 100 steps: the oracle runs on the whole mesh.
 * 2048 x 512 coarse cells, K = 2, 2 x 2-cell patches, H = 128, BF16: the
   oracle computes sampled outputs -- it runs on windows of the global mesh
   (obstacle, inflow, outflow corner, interior), and results are compared
@@ -13,10 +13,11 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import TOL, Params, rel_l2
+from helpers import TOL, Params, class_errors, rel_l2
 from oracle import fem, step as ostep
 from oracle.mesh import Mesh as OMesh
 from paper_2008_11520_gb300 import synth
+from parity import check, record
 
 pytestmark = pytest.mark.gpu
 PRM = Params()
@@ -49,25 +50,70 @@ def gpu_run(dn, c, prec, steps, xc_t, v0, h0):
     return mesh, W, out
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16"])
-def test_channel256_whole_mesh(dn, prec):
+class GpuSide:
+    """One network precision's run of the step on the whole mesh, as the benchmark launches it."""
+
+    def __init__(self, dn, c, prec, v0, h0):
+        self.dn = dn
+        self.mesh = dn.Mesh(dn.make_desc(c["nxc"], c["nyc"], c["K"], c["s"], c["ellipse"], precision=prec))
+        I = self.mesh.info
+        self.W = synth.net_weights(I.n_in, c["H"], I.n_out, seed=c["seed"])
+        self.net = dn.Net(*self.W, precision=prec)
+        self.bf = self.mesh.fine(2)
+        self.bc = self.mesh.coarse(3)
+        dn.dnnmg_rhs_restrict(self.mesh, self.mesh.pack(v0), self.bf, self.bc)
+        self.h = torch.as_tensor(h0).to(self.mesh.real).cuda().contiguous()
+        self.ws = self.mesh.workspace()
+
+    def step(self, xc, t):
+        self.dn.dnnmg_step(self.mesh, self.net, torch.as_tensor(xc).cuda().contiguous(), self.h, self.bf, self.bc,
+                           self.ws, t)
+        torch.cuda.synchronize()
+        d, vc = self.mesh.step_outputs(self.ws)
+        return {"h": self.h.double().cpu().numpy(), "bf": self.mesh.unpack(self.bf), "bc": self.bc.cpu().numpy(),
+                "d": d.double().cpu().numpy(), "vcorr": self.mesh.unpack(vc)}
+
+
+def test_channel256_hundred_steps(dn):
+    # 256 x 64 coarse cells, K = 2, H = 64, over the workload's 100 steps: the
+    # FP32 and the BF16 network run side by side against one FP64 oracle
+    # trajectory (each side keeps its own h and b_f, so errors can build up
+    # through the recurrence); x_c(t_n) is the synthetic coarse flow.  Every
+    # step's errors are recorded (the drift curve of h among them) and the
+    # bounds are asserted once all steps have run.
     c = synth.config("channel256")
     spec = synth.FlowSpec.from_seed(c["seed"], c["ellipse"])
     om = OMesh(c["nxc"], c["nyc"], c["K"], c["s"], ellipse=c["ellipse"])
-    steps = 2
-    xc_t = [synth.coarse_state(spec, c["nxc"], c["nyc"], n * PRM.k) for n in range(steps)]
+    steps = c["steps"]
     v0 = synth.fine_state(spec, om.nxf, om.nyf, 0.0, perturb_seed=3)[:2].astype(np.float32).astype(np.float64)
     h0 = synth.hidden_state(om.P, c["H"], seed=5).astype(np.float32).astype(np.float64)
-    mesh, W, got = gpu_run(dn, c, prec, steps, xc_t, v0, h0)
-    assert mesh.info.P == om.P
+    sides = {prec: GpuSide(dn, c, prec, v0, h0) for prec in ("f32", "bf16")}
+    assert all(sd.mesh.info.P == om.P for sd in sides.values())
+    W = sides["f32"].W
     h, bf = h0, fem.rhs(om, PRM, v0)
+    worst = []
     for n in range(steps):
-        out = ostep.dnnmg_step(om, PRM, W, xc_t[n], h, bf, n * PRM.k)
+        t = n * PRM.k
+        xc = synth.coarse_state(spec, c["nxc"], c["nyc"], t)
+        out = ostep.dnnmg_step(om, PRM, W, xc, h, bf, t)
         h, bf = out["h"], out["bf"]
-    tol = TOL[prec]
-    assert rel_l2(got["h"], out["h"]) <= tol
-    assert rel_l2(got["bf"].reshape(2, -1), out["bf"]) <= tol
-    assert rel_l2(got["bc"].reshape(3, -1), out["bc"]) <= tol
+        for prec, sd in sides.items():
+            got = sd.step(xc, t)
+            tol = TOL[prec]
+            errs = {"h": rel_l2(got["h"], out["h"]), "d": rel_l2(got["d"], out["d"]),
+                    "v_corr": rel_l2(got["vcorr"], out["vcorr"]), "bf": rel_l2(got["bf"], out["bf"]),
+                    "bc": rel_l2(got["bc"].reshape(3, -1), out["bc"])}
+            for k, v in errs.items():
+                record("100 steps " + k, v, tol, prec, step=n)
+                worst.append((v / tol, prec, n, k))
+            if n % 10 == 9 or n == 0:
+                for cname, v in class_errors(got["bf"], out["bf"], om).items():
+                    record("100 steps bf max/RMS " + cname, v, tol, prec, step=n)
+                    worst.append((v / tol, prec, n, "bf " + cname))
+    for prec, sd in sides.items():
+        assert dn.dnnmg_net_status(sd.net) == 0
+    over = [w for w in worst if w[0] > 1.0]
+    assert not over, sorted(over)[-5:]
 
 
 WINDOWS = {  # coarse-cell windows of the 2048 x 512 mesh (multiples of the patch size)
@@ -110,14 +156,20 @@ def test_large_sampled_windows(dn):
         hi_j = (cj1 - cj0) + 1 - (0 if cj1 == c["nyc"] else margin_c)
         ref = out["bc"].reshape(3, cj1 - cj0 + 1, ci1 - ci0 + 1)[:2, lo_j:hi_j, lo_i:hi_i]
         gbc = bc_g[:2, cj0 + lo_j:cj0 + hi_j, ci0 + lo_i:ci0 + hi_i]
-        assert rel_l2(gbc, ref) <= TOL["bf16"], name
+        check("window bc", rel_l2(gbc, ref), TOL["bf16"], "bf16", window=name)
         fref = out["bf"].reshape(2, om.wyf + 1, om.wxf + 1)[:, lo_j * r:(hi_j - 1) * r + 1, lo_i * r:(hi_i - 1) * r + 1]
         gbf = bf_g[:, cj0 * r + lo_j * r:cj0 * r + (hi_j - 1) * r + 1, ci0 * r + lo_i * r:ci0 * r + (hi_i - 1) * r + 1]
-        assert rel_l2(gbf, fref) <= TOL["bf16"], name
+        check("window bf", rel_l2(gbf, fref), TOL["bf16"], "bf16", window=name)
+        # per node class, over the exact region of the window
+        region = np.zeros((om.wyf + 1, om.wxf + 1), dtype=bool)
+        region[lo_j * r:(hi_j - 1) * r + 1, lo_i * r:(hi_i - 1) * r + 1] = True
+        gwin = bf_g[:, cj0 * r:cj1 * r + 1, ci0 * r:ci1 * r + 1]
+        for cname, v in class_errors(gwin, out["bf"], om, region).items():
+            check("window bf max/RMS " + cname, v, TOL["bf16"], "bf16", window=name)
         # hidden state of patches whose dependence stays inside the window
         pi, pj = om.patches[:, 0], om.patches[:, 1]
         s = c["s"]
         inner = ((pi * s >= ci0 + lo_i) & ((pi + 1) * s <= ci0 + hi_i - 1)
                  & (pj * s >= cj0 + lo_j) & ((pj + 1) * s <= cj0 + hi_j - 1))
         assert inner.sum() > 0
-        assert rel_l2(got["h"][gidx[inner]], out["h"][inner]) <= TOL["bf16"], name
+        check("window h", rel_l2(got["h"][gidx[inner]], out["h"][inner]), TOL["bf16"], "bf16", window=name)
