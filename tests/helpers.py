@@ -101,6 +101,14 @@ def node_classes(om):
     return cls
 
 
+# The classes whose max/RMS error the tests bound.  The interior class is
+# recorded only: a maximum over the whole interior (about 10^5 nodes at the
+# 256 x 64 workload) sits several standard deviations above the RMS error, so
+# bounding it would be a stricter test than the whole-field norm, not a check
+# of boundary rows.
+BOUNDARY_CLASSES = ("inflow-adjacent", "wall-adjacent", "outflow", "obstacle-adjacent")
+
+
 def class_errors(got, ref, om, region=None):
     """max |got - ref| over each node class, divided by the RMS of ref.
 
@@ -153,4 +161,5 @@ def weights(case, n_in, n_out, seed=17):
 
 
 __all__ = ["CASES", "TOL", "Params", "oracle_mesh", "rel_l2", "np_dtype", "coarse_input",
-           "fine_velocity", "rhs_like", "weights", "mask_for", "spec_for", "node_classes", "class_errors"]
+           "fine_velocity", "rhs_like", "weights", "mask_for", "spec_for", "node_classes", "class_errors",
+           "BOUNDARY_CLASSES"]
