@@ -331,8 +331,9 @@ int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net);
  * step (cudaEventElapsedTime).  No counterpart in the paper: an
  * instrumentation form of dnnmg_step.
  *   events: n_events = dnnmg_step_launches() + 1 caller-created events.
- * The kernels, in order: coarse padding (S1 staging), S2+S3, S4 (when the
- * mesh has fluid patches), S5, S6, S7.
+ * The kernels, in order: coarse padding (S1 staging), S2+S3 on the
+ * all-fluid tiles in closed form (FP32 fields with K = 1 or 2 only), S2+S3
+ * on the other tiles, S4 (when the mesh has fluid patches), S5, S6, S7.
  */
 int dnnmg_step_timed(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void *h, void *bf, double *bc,
                      void *workspace, size_t workspace_bytes, double t, cudaEvent_t *events, int n_events,

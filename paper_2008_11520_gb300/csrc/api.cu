@@ -416,19 +416,48 @@ int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out) {
         return fail(DNNMG_ENOMEM, "device allocation of the tile flags failed");
     }
     g.tile_flags = m->d_tile_flags;
-    m->d_status = nullptr;
-    if (cudaMalloc(&m->d_status, sizeof(int)) != cudaSuccess || cudaMemset(m->d_status, 0, sizeof(int)) != cudaSuccess) {
+    auto undo = [&](const char *what) {
+        if (m->side) cudaStreamDestroy(m->side);
+        if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+        if (m->ev_join) cudaEventDestroy(m->ev_join);
         cudaFree(m->d_solid);
         cudaFree(m->d_patch_id);
         cudaFree(m->d_patch_cell);
         cudaFree(m->d_feat_tab);
         cudaFree(m->d_tile_flags);
+        cudaFree(m->d_slow_tiles);
+        cudaFree(m->d_cf_tab);
         cudaFree(m->d_status);
         delete m;
         cudaGetLastError();
-        return fail(DNNMG_ENOMEM, "device allocation of the mesh status failed");
-    }
+        return fail(DNNMG_ENOMEM, "device allocation of the %s failed", what);
+    };
+    // tiles the general S2+S3 kernel does when the all-fluid ones run in closed form
+    std::vector<int> slow;
+    for (size_t i = 0; i < tflags.size(); ++i)
+        if (!(tflags[i] & 1)) slow.push_back((int)i);
+    g.n_slow_tiles = (int)slow.size();
+    m->d_slow_tiles = nullptr;
+    if (cudaMalloc(&m->d_slow_tiles, (slow.size() ? slow.size() : 1) * sizeof(int)) != cudaSuccess ||
+        (slow.size() && cudaMemcpy(m->d_slow_tiles, slow.data(), slow.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice) != cudaSuccess))
+        return undo("boundary tile list");
+    g.slow_tiles = m->d_slow_tiles;
+    std::vector<uint16_t> ctab((size_t)I.ldx);
+    residual_cf_table(g, ctab.data());
+    m->d_cf_tab = nullptr;
+    if (cudaMalloc(&m->d_cf_tab, ctab.size() * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMemcpy(m->d_cf_tab, ctab.data(), ctab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return undo("closed-form column table");
+    g.cf_tab = m->d_cf_tab;
+    m->d_status = nullptr;
+    if (cudaMalloc(&m->d_status, sizeof(int)) != cudaSuccess || cudaMemset(m->d_status, 0, sizeof(int)) != cudaSuccess)
+        return undo("mesh status");
     g.status = m->d_status;
+    if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return undo("side stream and its events");
     fem_coefficients(*desc, &m->fem64);
     to_float(m->fem64, &m->fem32);
     *out = m;
@@ -443,7 +472,12 @@ int dnnmg_mesh_destroy(dnnmg_mesh_t mesh) {
     cudaFree(mesh->d_patch_cell);
     cudaFree(mesh->d_feat_tab);
     cudaFree(mesh->d_tile_flags);
+    cudaFree(mesh->d_slow_tiles);
+    cudaFree(mesh->d_cf_tab);
     cudaFree(mesh->d_status);
+    if (mesh->side) cudaStreamDestroy(mesh->side);
+    if (mesh->ev_fork) cudaEventDestroy(mesh->ev_fork);
+    if (mesh->ev_join) cudaEventDestroy(mesh->ev_join);
     delete mesh;
     return DNNMG_OK;
 }
@@ -707,8 +741,27 @@ static int step_body(dnnmg_mesh_t mesh, dnnmg_net_t net, const double *xc, void 
     // round trip.  See dnnmg_scatter_rhs.)
     DNNMG_CUDA_TRY(launch_coarse_pad(g, prec, xc, w.xcp, s));
     DNNMG_CUDA_TRY(mark());
-    DNNMG_CUDA_TRY(launch_residual_step(g, prec, mesh->fem64, mesh->fem32, w.xcp, t, bf, w.X, s));
-    DNNMG_CUDA_TRY(mark());
+    // S2 + S3: all-fluid tiles in closed form (x~ = P x_c is bilinear per
+    // coarse cell there), the other tiles by the general element kernel
+    const bool cf = residual_cf_supported(g, prec);
+    if (cf && !ev && g.n_slow_tiles > 0) {
+        // the two S2+S3 kernels write disjoint rows of X: the boundary tiles
+        // (few, slow CTAs) run on the side stream while the closed form runs
+        DNNMG_CUDA_TRY(cudaEventRecord(mesh->ev_fork, s));
+        DNNMG_CUDA_TRY(cudaStreamWaitEvent(mesh->side, mesh->ev_fork, 0));
+        DNNMG_CUDA_TRY(launch_residual_step(g, prec, mesh->fem64, mesh->fem32, w.xcp, t, bf, w.X, mesh->side, true));
+        DNNMG_CUDA_TRY(launch_residual_cf(g, prec, mesh->fem32, w.xcp, bf, w.X, s));
+        DNNMG_CUDA_TRY(cudaEventRecord(mesh->ev_join, mesh->side));
+        DNNMG_CUDA_TRY(cudaStreamWaitEvent(s, mesh->ev_join, 0));
+    } else {
+        // (the timed form runs them one after the other, to time each)
+        if (cf) {
+            DNNMG_CUDA_TRY(launch_residual_cf(g, prec, mesh->fem32, w.xcp, bf, w.X, s));
+            DNNMG_CUDA_TRY(mark());
+        }
+        DNNMG_CUDA_TRY(launch_residual_step(g, prec, mesh->fem64, mesh->fem32, w.xcp, t, bf, w.X, s, cf));
+        DNNMG_CUDA_TRY(mark());
+    }
     if (mesh->info.P) {
         DNNMG_CUDA_TRY(launch_gru(*net, w.X, h, w.d, mesh->info.P, s));
         DNNMG_CUDA_TRY(mark());
@@ -798,7 +851,8 @@ int dnnmg_workspace_offsets(dnnmg_mesh_t mesh, long long *x, long long *d, long 
 
 int dnnmg_step_launches(dnnmg_mesh_t mesh, dnnmg_net_t net) {
     if (!mesh || !net) return -1;
-    return 5 + (mesh->info.P ? gru_launch_count(*net) : 0);
+    return 5 + (residual_cf_supported(mesh->g, mesh->info.precision) ? 1 : 0) +
+           (mesh->info.P ? gru_launch_count(*net) : 0);
 }
 
 }  // extern "C"

@@ -51,6 +51,9 @@ struct MeshGeom {
     const int *feat_tab;          // device [ldx], source of each feature column (stencil.cu)
     const uint8_t *tile_flags;    // device [nty][ntx], all-fluid bits of each 32 x 16-cell tile
     int ntx, nty;
+    const int *slow_tiles;        // device [n_slow_tiles]: tiles without the all-fluid bit (ty ntx + tx)
+    int n_slow_tiles;
+    const uint16_t *cf_tab;       // device [ldx]: feature column sources of the closed-form tiles
     int *status;                  // device status word of the mesh (DNNMG_DEVERR_* bits)
 };
 
@@ -96,7 +99,13 @@ struct Mesh {
     int *d_patch_cell;
     int *d_feat_tab;
     uint8_t *d_tile_flags;
+    int *d_slow_tiles;
+    uint16_t *d_cf_tab;
     int *d_status;
+    // the boundary tiles of S2+S3 run on this stream beside the closed-form
+    // kernel (forked from and joined back to the caller's stream)
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
 };
 
 struct Net {
@@ -143,7 +152,16 @@ cudaError_t launch_coarse_pad(const MeshGeom &g, int prec, const double *xc, voi
 // CTAs, TMA-fed and double-buffered tiles (same arithmetic as
 // launch_residual_features with xc; rf is not written).
 cudaError_t launch_residual_step(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
-                                 const void *xcp, double t, const void *bf, void *X, cudaStream_t st);
+                                 const void *xcp, double t, const void *bf, void *X, cudaStream_t st,
+                                 bool skip_fast = false);
+// S2 + S3 of the step on the all-fluid tiles in closed form (residual_cf.cu):
+// FP32 fields, K = 1 or 2.  launch_residual_step(..., skip_fast = true) then
+// does the other tiles.
+bool residual_cf_supported(const MeshGeom &g, int prec);
+// Column table of the closed-form tiles' feature gather ([ldx] entries).
+void residual_cf_table(const MeshGeom &g, uint16_t *tab);
+cudaError_t launch_residual_cf(const MeshGeom &g, int prec, const FemCoef<float> &f32, const void *xcp, const void *bf,
+                               void *X, cudaStream_t st);
 // S5 + S6 fused: b_f = Rhs(P x_c + mean of d) without writing v_corr.
 cudaError_t launch_avg_rhs(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
                            const void *d, const double *xc, double t, void *bf, cudaStream_t st);

@@ -397,8 +397,11 @@ int dnnmg_server_step(dnnmg_server_t s, int n, const int *slots, const double *c
         cudaStream_t st = s->lane[i % kLanes];
         void *xcp = static_cast<char *>(s->scratch[i % kLanes]) + align256(2 * (size_t)I.plane * I.real_bytes);
         DNNMG_CUDA_TRY(launch_coarse_pad(m.g, I.precision, xc[i], xcp, st));
-        DNNMG_CUDA_TRY(launch_residual_step(m.g, I.precision, m.fem64, m.fem32, xcp, t[i], bf[i],
-                                            X + (size_t)row0[i] * net.ldx, st));
+        // the same two S2+S3 kernels as dnnmg_step, so an instance gets the same bits
+        void *Xi = X + (size_t)row0[i] * net.ldx;
+        const bool cf = residual_cf_supported(m.g, I.precision);
+        if (cf) DNNMG_CUDA_TRY(launch_residual_cf(m.g, I.precision, m.fem32, xcp, bf[i], Xi, st));
+        DNNMG_CUDA_TRY(launch_residual_step(m.g, I.precision, m.fem64, m.fem32, xcp, t[i], bf[i], Xi, st, cf));
     }
     if (int e = join()) return e;
     // S4 once over every instance's rows

@@ -1043,11 +1043,20 @@ struct StepLayout {
 template <typename T, typename TX, int R>
 __global__ void __launch_bounds__(RES_THREADS)
 k_residual_step(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap tmB,
-                const __grid_constant__ CUtensorMap tmC, double inflow_peak, TX *__restrict__ X) {
+                const __grid_constant__ CUtensorMap tmC, double inflow_peak, TX *__restrict__ X,
+                const int *__restrict__ tile_list) {
     using L = ResLayout;
     using SL = StepLayout<T, R>;
     using CWin = typename SL::CWin;
     constexpr int K = Log2<R>::v;
+    // tile_list (when the closed-form kernel does the all-fluid tiles): the
+    // other tiles, one per CTA; otherwise the grid covers every tile
+    int tx = blockIdx.x, ty = blockIdx.y;
+    if (tile_list) {
+        const int tile = __ldg(tile_list + blockIdx.x);
+        ty = tile / g.ntx;
+        tx = tile - ty * g.ntx;
+    }
     extern __shared__ unsigned char smem_raw[];
     __shared__ T geo_s[12];
     // aligned by an offset from the shared-memory symbol itself, so that every
@@ -1062,7 +1071,7 @@ k_residual_step(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap t
     uint64_t *mb = reinterpret_cast<uint64_t *>(base + SL::MB);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(mb + 1);
     const uint32_t mb_u = ptx::smem_u32(mb);
-    const int I0 = blockIdx.x * TXC, J0 = blockIdx.y * TYC;
+    const int I0 = tx * TXC, J0 = ty * TYC;
     CWin cw;
     cw.cs = reinterpret_cast<T *>(base + SL::CSB);
     cw.ci0 = ((I0 - L::XO) >> K) & ~3;
@@ -1083,7 +1092,7 @@ k_residual_step(MeshGeom g, FemCoef<T> fc, const __grid_constant__ CUtensorMap t
         pid[e] = (pi < g.npx && pj < g.npy) ? __ldg(g.patch_id + pj * g.npx + pi) : -1;
     }
     if (threadIdx.x < 12) geo_s[threadIdx.x] = fc.geo[threadIdx.x];
-    const bool fast = tile_fluid(g, blockIdx.x, blockIdx.y, 1);
+    const bool fast = tile_fluid(g, tx, ty, 1);
     __syncthreads();   // the barrier is initialised; pid and geo_s are visible
     const bool ok = ptx::mbar_test(mb_u, 0) || ptx::mbar_wait(mb_u, 0, abort_flag);
     if (__syncthreads_or(!ok)) {
@@ -1966,7 +1975,7 @@ cudaError_t launch_coarse_pad(const MeshGeom &g, int prec, const double *xc, voi
 
 template <typename T, typename TX, int R>
 cudaError_t run_residual_step(const MeshGeom &g, const FemCoef<T> &fc, const T *xcp, double up, const T *bf, TX *X,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool skip_fast) {
     using L = ResLayout;
     using SL = StepLayout<T, R>;
     const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -1987,27 +1996,32 @@ cudaError_t run_residual_step(const MeshGeom &g, const FemCoef<T> &fc, const T *
     const size_t sm = SL::BYTES;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k<<<tile_grid(g), RES_THREADS, sm, st>>>(g, fc, tmB, tmC, up, X);
+    if (skip_fast) {
+        if (g.n_slow_tiles == 0) return cudaSuccess;
+        k<<<g.n_slow_tiles, RES_THREADS, sm, st>>>(g, fc, tmB, tmC, up, X, g.slow_tiles);
+    } else {
+        k<<<tile_grid(g), RES_THREADS, sm, st>>>(g, fc, tmB, tmC, up, X, nullptr);
+    }
     return cudaGetLastError();
 }
 
 template <typename T, typename TX>
 cudaError_t run_residual_step_r(const MeshGeom &g, const FemCoef<T> &fc, const void *xcp, double up, const void *bf,
-                                void *X, cudaStream_t st) {
+                                void *X, cudaStream_t st, bool sf) {
     switch (g.r) {
-        case 2: return run_residual_step<T, TX, 2>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st);
-        case 4: return run_residual_step<T, TX, 4>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st);
-        case 8: return run_residual_step<T, TX, 8>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st);
+        case 2: return run_residual_step<T, TX, 2>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st, sf);
+        case 4: return run_residual_step<T, TX, 4>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st, sf);
+        case 8: return run_residual_step<T, TX, 8>(g, fc, (const T *)xcp, up, (const T *)bf, (TX *)X, st, sf);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_residual_step(const MeshGeom &g, int prec, const FemCoef<double> &f64, const FemCoef<float> &f32,
-                                 const void *xcp, double t, const void *bf, void *X, cudaStream_t st) {
+                                 const void *xcp, double t, const void *bf, void *X, cudaStream_t st, bool skip_fast) {
     const double up = inflow_peak(g, t);
-    if (prec == DNNMG_F64) return run_residual_step_r<double, double>(g, f64, xcp, up, bf, X, st);
-    if (prec == DNNMG_F32) return run_residual_step_r<float, float>(g, f32, xcp, up, bf, X, st);
-    return run_residual_step_r<float, __nv_bfloat16>(g, f32, xcp, up, bf, X, st);
+    if (prec == DNNMG_F64) return run_residual_step_r<double, double>(g, f64, xcp, up, bf, X, st, skip_fast);
+    if (prec == DNNMG_F32) return run_residual_step_r<float, float>(g, f32, xcp, up, bf, X, st, skip_fast);
+    return run_residual_step_r<float, __nv_bfloat16>(g, f32, xcp, up, bf, X, st, skip_fast);
 }
 
 template <typename T>

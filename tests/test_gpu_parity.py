@@ -522,7 +522,8 @@ def test_mesh_without_fluid_patches(dn):
     assert m.info.P == 0 and om.P == 0
     Wx, Uh, Wfc = weights(case, om.n_in, om.n_out)
     net = dn.Net(Wx, Uh, Wfc, "bf16")
-    assert dn.dnnmg_step_launches(m, net) == 5
+    # no GRU launch: the stencil kernels only (two S2+S3 kernels on FP32 fields with K <= 2)
+    assert dn.dnnmg_step_launches(m, net) == 6
     xc = coarse_input(case, t=0.0)
     v0 = fine_velocity(case)[:2].astype(np.float32).astype(np.float64)
     bf = m.fine(2)
