@@ -434,8 +434,7 @@ int dnnmg_mesh_create(const dnnmg_mesh_desc *desc, dnnmg_mesh_t *out) {
     };
     // tiles the general S2+S3 kernel does when the all-fluid ones run in closed form
     std::vector<int> slow;
-    for (size_t i = 0; i < tflags.size(); ++i)
-        if (!(tflags[i] & 1)) slow.push_back((int)i);
+    residual_cf_slow_tiles(g, tflags.data(), &slow);
     g.n_slow_tiles = (int)slow.size();
     m->d_slow_tiles = nullptr;
     if (cudaMalloc(&m->d_slow_tiles, (slow.size() ? slow.size() : 1) * sizeof(int)) != cudaSuccess ||

@@ -8,6 +8,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "dnnmg.h"
 
@@ -160,6 +161,8 @@ cudaError_t launch_residual_step(const MeshGeom &g, int prec, const FemCoef<doub
 bool residual_cf_supported(const MeshGeom &g, int prec);
 // Column table of the closed-form tiles' feature gather ([ldx] entries).
 void residual_cf_table(const MeshGeom &g, uint16_t *tab);
+// The general S2+S3 tiles (ty ntx + tx) that the closed form leaves, from the tile flags.
+void residual_cf_slow_tiles(const MeshGeom &g, const uint8_t *flags, std::vector<int> *slow);
 cudaError_t launch_residual_cf(const MeshGeom &g, int prec, const FemCoef<float> &f32, const void *xcp, const void *bf,
                                void *X, cudaStream_t st);
 // S5 + S6 fused: b_f = Rhs(P x_c + mean of d) without writing v_corr.

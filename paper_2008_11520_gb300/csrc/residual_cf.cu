@@ -25,16 +25,18 @@
 // two or four one-sided parts.  The tile layout matches the general kernel
 // (32 x 16 fine cells); tiles without the all-fluid flag are left to it.
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 
 namespace dnnmg {
 namespace {
 
-constexpr int CF_TXC = 32, CF_TYC = 16;               // fine cells per tile
-constexpr int CF_NYN = CF_TYC + 1;                    // node rows of a tile
-constexpr int CF_THREADS = 160;                       // 136 runs of 4 nodes + 17 edge nodes
-constexpr int CF_RXP = 36;                            // residual row pitch (elements)
+// A CTA takes two horizontally adjacent 32 x 16-cell tiles of the general
+// kernel (64 x 16 fine cells), so the column the two share is computed once.
+constexpr int CF_TXC = 64, CF_TYC = 16;               // fine cells per block
+constexpr int CF_NYN = CF_TYC + 1;                    // node rows of a block
+constexpr int CF_RXP = 68;                            // residual row pitch (elements)
 constexpr int CF_RPL = CF_NYN * CF_RXP;               // residual plane (elements)
 
 // Moment products of one kind of support (full in both directions, half in
@@ -166,16 +168,121 @@ template <typename TX> __device__ __forceinline__ TX to_feat(float v);
 template <> __device__ __forceinline__ float to_feat<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_feat<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// Four consecutive residuals of a run as one aligned shared-memory store.
-__device__ __forceinline__ void put4(float *p, const float (&r)[4]) {
-    *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+// EPC consecutive 16-bit table entries (16- or 8-byte aligned) from shared memory.
+template <int EPC> __device__ __forceinline__ void load_entries(const uint16_t *p, uint16_t (&e)[EPC]) {
+    if constexpr (EPC == 8) {
+        const uint4 tv = *reinterpret_cast<const uint4 *>(p);
+        const uint32_t w[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            e[2 * k] = (uint16_t)(w[k] & 0xFFFFu);
+            e[2 * k + 1] = (uint16_t)(w[k] >> 16);
+        }
+    } else {
+        const uint2 tv = *reinterpret_cast<const uint2 *>(p);
+        e[0] = (uint16_t)(tv.x & 0xFFFFu);
+        e[1] = (uint16_t)(tv.x >> 16);
+        e[2] = (uint16_t)(tv.y & 0xFFFFu);
+        e[3] = (uint16_t)(tv.y >> 16);
+    }
 }
-__device__ __forceinline__ void put4(__nv_bfloat16 *p, const float (&r)[4]) {
-    const __nv_bfloat162 a = __floats2bfloat162_rn(r[0], r[1]), b = __floats2bfloat162_rn(r[2], r[3]);
-    uint2 v;
-    v.x = *reinterpret_cast<const uint32_t *>(&a);
-    v.y = *reinterpret_cast<const uint32_t *>(&b);
-    *reinterpret_cast<uint2 *>(p) = v;
+
+// Block (bx, by) of the closed form: general tiles (2 bx, by) and (2 bx + 1,
+// by), both of which must have the all-fluid flag (every cell within two of
+// the tile exists and is fluid).
+__host__ __device__ __forceinline__ bool block_fast_flags(const uint8_t *flags, int ntx, int nty, int bx, int by) {
+    const int t0 = 2 * bx;
+    if (t0 + 1 >= ntx || by >= nty) return false;
+    return (flags[(size_t)by * ntx + t0] & 1) && (flags[(size_t)by * ntx + t0 + 1] & 1);
+}
+__device__ __forceinline__ bool block_fast(const MeshGeom &g, int bx, int by) {
+    const int t0 = 2 * bx;
+    if (t0 + 1 >= g.ntx || by >= g.nty) return false;
+    return (__ldg(g.tile_flags + (size_t)by * g.ntx + t0) & 1) && (__ldg(g.tile_flags + (size_t)by * g.ntx + t0 + 1) & 1);
+}
+
+// R consecutive residuals of one row as one aligned shared-memory store.
+template <int R> __device__ __forceinline__ void put_row(float *p, const float *r) {
+    if constexpr (R == 4) *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+    else *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
+}
+template <int R> __device__ __forceinline__ void put_row(__nv_bfloat16 *p, const float *r) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(r[0], r[1]);
+    if constexpr (R == 4) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(r[2], r[3]);
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t *>(&a);
+        v.y = *reinterpret_cast<const uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = v;
+    } else {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = a;
+    }
+}
+template <int R> __device__ __forceinline__ void load_row(const float *p, float *v) {
+    if constexpr (R == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = q.x; v[1] = q.y;
+    }
+}
+
+// The fine nodes of coarse cell (ci, cj) of the block (block-local coarse
+// indices; the block's first staged coarse node is window node (1, 1) minus
+// one): rows b = 0 .. R-1 when FY (else row 0 only), columns a = 0 .. R-1
+// when FX (else column 0 only).  Node (a, b) lies on a vertical coarse edge
+// when a = 0 and on a horizontal one when b = 0.  Residuals r = b_f - A(x~)
+// go to the block's residual array in the feature type.
+template <typename TX, int R, bool FX, bool FY>
+__device__ __forceinline__ void cell_task(const CfCoef &c, const float *cs, int cw, int ch, int ci, int cj,
+                                          const MeshGeom &g, const float *__restrict__ bf, int I0, int J0, TX *rres) {
+    Cell own, left, low, lowleft;
+    const int o = (cj + 1) * cw + ci + 1;   // own cell's SW node in the window
+    own.load(c, cs, cw, ch, o);
+    left.load(c, cs, cw, ch, o - 1);
+    low.load(c, cs, cw, ch, o - cw);
+    lowleft.load(c, cs, cw, ch, o - cw - 1);
+    constexpr int NA = FX ? R : 1, NB = FY ? R : 1;
+    const int Il = ci * R, Jl = cj * R;     // block-local fine node of the cell's SW corner
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const float Y = (float)b * c.hy;
+        const size_t node = (size_t)(J0 + Jl + b) * g.pitch + I0 + Il;
+        float bu[R], bv[R], ru[R], rv[R], rp[R];
+        if constexpr (FX) {
+            load_row<R>(bf + node, bu);
+            load_row<R>(bf + g.plane + node, bv);
+        } else {
+            bu[0] = __ldg(bf + node);
+            bv[0] = __ldg(bf + g.plane + node);
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            float Au, Av, Ap;
+            const float X = (float)a * c.hx;
+            if (b == 0) {
+                if (a == 0) node_A<true, true>(c, own, left, low, lowleft, X, Y, Au, Av, Ap);
+                else node_A<false, true>(c, own, left, low, lowleft, X, Y, Au, Av, Ap);
+            } else {
+                if (a == 0) node_A<true, false>(c, own, left, low, lowleft, X, Y, Au, Av, Ap);
+                else node_A<false, false>(c, own, left, low, lowleft, X, Y, Au, Av, Ap);
+            }
+            ru[a] = bu[a] - Au;
+            rv[a] = bv[a] - Av;
+            rp[a] = -Ap;
+        }
+        TX *dst = rres + (Jl + b) * CF_RXP + Il;
+        if constexpr (FX) {
+            put_row<R>(dst, ru);
+            put_row<R>(dst + CF_RPL, rv);
+            put_row<R>(dst + 2 * CF_RPL, rp);
+        } else {
+            dst[0] = to_feat<TX>(ru[0]);
+            dst[CF_RPL] = to_feat<TX>(rv[0]);
+            dst[2 * CF_RPL] = to_feat<TX>(rp[0]);
+        }
+    }
 }
 
 // Sizes of one (K, s) configuration: R = 2^K fine cells per coarse cell,
@@ -189,6 +296,9 @@ struct CfShape {
     static constexpr int TPX = CF_TXC / S, TPY = CF_TYC / S, NP = TPX * TPY;
     static constexpr int EPC = 16 / sizeof(TX), NCH = LDX / EPC;      // columns per 16-byte piece
     static constexpr int CW = CF_TXC / R + 3, CH = CF_TYC / R + 3;    // coarse window nodes
+    static constexpr int NCX = CF_TXC / R, NCY = CF_TYC / R, NFULL = NCX * NCY;   // coarse cells of the block
+    static constexpr int NTASK = NFULL + NCX + NCY + 1;               // plus the partial cells above and right
+    static constexpr int THREADS = (NTASK + 31) / 32 * 32;
     // shared memory (bytes)
     static constexpr size_t CS = 0;                                               // [3][CH][CW] float
     static constexpr size_t RR = (CS + 3 * CW * CH * 4 + 15) / 16 * 16;           // [3][NYN][RXP] TX
@@ -205,37 +315,42 @@ struct CfShape {
 // tile's last node column.  Then the feature rows of the tile's patches are
 // gathered from shared memory in 16-byte pieces.
 template <typename TX, int R, int SP>
-__global__ void __launch_bounds__(CF_THREADS, R == 4 ? 6 : 4)
+__global__ void __launch_bounds__(CfShape<TX, R, SP>::THREADS, R == 4 ? 8 : 3)
 k_residual_cf(MeshGeom g, CfCoef c, const float *__restrict__ xcp, int pc, const float *__restrict__ bf,
               TX *__restrict__ X) {
     using SH = CfShape<TX, R, SP>;
     constexpr int K = SH::K, S = SH::S, LS = K + SP - 1;
     const int tx = blockIdx.x, ty = blockIdx.y;
-    if (!(tx < g.ntx && ty < g.nty && (__ldg(g.tile_flags + (size_t)ty * g.ntx + tx) & 1))) return;
+    if (!block_fast(g, tx, ty)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     float *cs = reinterpret_cast<float *>(smem + SH::CS);
     TX *rres = reinterpret_cast<TX *>(smem + SH::RR);
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem + SH::TAB);
     int *pid = reinterpret_cast<int *>(smem + SH::PID);
     TX *ex = reinterpret_cast<TX *>(smem + SH::EX);
+    __shared__ float geo_s[12];
     const int I0 = tx * CF_TXC, J0 = ty * CF_TYC;
     const int cx0 = (I0 >> K) - 1, cy0 = (J0 >> K) - 1;   // first staged coarse node
     // ---- staging: coarse window, patch numbers, column table
     const size_t cplane = (size_t)pc * (g.nyc + 1);
-    for (int e = threadIdx.x; e < 3 * SH::CW * SH::CH; e += CF_THREADS) {
+    for (int e = threadIdx.x; e < 3 * SH::CW * SH::CH; e += SH::THREADS) {
         const int f = e / (SH::CW * SH::CH), rem = e - f * (SH::CW * SH::CH);
         const int b = rem / SH::CW, a = rem - b * SH::CW;
         cs[e] = __ldg(xcp + f * cplane + (size_t)(cy0 + b) * pc + cx0 + a);   // inside: the tile is interior
     }
-    for (int e = threadIdx.x; e < SH::NP; e += CF_THREADS) {
+    for (int e = threadIdx.x; e < SH::NP; e += SH::THREADS) {
         const int py = e / SH::TPX, px = e - py * SH::TPX;
         pid[e] = __ldg(g.patch_id + ((J0 >> LS) + py) * g.npx + (I0 >> LS) + px);
     }
-    for (int col = threadIdx.x; col < SH::LDX / 2; col += CF_THREADS)
+    for (int col = threadIdx.x; col < SH::LDX / 2; col += SH::THREADS)
         reinterpret_cast<uint32_t *>(tab)[col] = __ldg(reinterpret_cast<const uint32_t *>(g.cf_tab) + col);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) geo_s[i] = c.geo[i];
+    }
     __syncthreads();
     // ---- extra columns of each patch: coarse-node u, v, Peclet, geometry, zero padding
-    for (int e = threadIdx.x; e < SH::NP * SH::EXW; e += CF_THREADS) {
+    for (int e = threadIdx.x; e < SH::NP * SH::EXW; e += SH::THREADS) {
         const int q = e / SH::EXW, k = e - q * SH::EXW;
         const int py = q / SH::TPX, px = q - py * SH::TPX;
         float val = 0.0f;
@@ -243,116 +358,57 @@ k_residual_cf(MeshGeom g, CfCoef c, const float *__restrict__ xcp, int pc, const
             const int which = k / SH::NC, n = k - which * SH::NC, lb = n / (SP + 1), la = n - lb * (SP + 1);
             const int o = (py * SP + 1 + lb) * SH::CW + px * SP + 1 + la;   // patch origin at window node (1, 1)
             const float a = cs[o], b = cs[SH::CW * SH::CH + o];
-            val = which == 0 ? a : (which == 1 ? b : c.q_over_nu * sqrtf(a * a + b * b));
+            if (which == 2)
+                val = c.q_over_nu * sqrtf(a * a + b * b);
+            else
+                val = which ? b : a;
         } else if (k < 3 * SH::NC + 12) {
-            val = c.geo[k - 3 * SH::NC];
+            val = geo_s[k - 3 * SH::NC];
         }
         ex[e] = to_feat<TX>(val);
     }
-    // ---- node pass
+    // ---- node pass: one thread per coarse cell of the block, taking every
+    // fine node of the cell (its rows 0 .. R-1, columns 0 .. R-1), so that
+    // every thread has the same mix of corner, edge and interior nodes; the
+    // block's last node row and column come from the partial cells above and
+    // to the right of it
     const int t = threadIdx.x;
-    constexpr int NNZ = CF_TYC - CF_TYC / R;          // rows off horizontal coarse edges (b != 0)
-    constexpr int NZ = CF_TYC / R + 1;                // rows on them (b == 0), including row 16
-    if (t < 8 * (NNZ + NZ)) {
-        const int r = t & 7;
-        const int idx = t >> 3;
-        const bool on_edge = idx >= NNZ;
-        const int J = on_edge ? (idx - NNZ) * R : (idx + idx / (R - 1) + 1);
-        const int Ia = 4 * r;                          // first node of the run (tile-local)
-        const float Y = (float)(J & (R - 1)) * c.hy;
-        const int cyl = ((J0 + J) >> K) - cy0;         // the run's own coarse cell row in the window
-        float bu[4], bv[4];
-        {
-            const size_t node = (size_t)(J0 + J) * g.pitch + I0 + Ia;
-            const float4 q0 = __ldg(reinterpret_cast<const float4 *>(bf + node));
-            const float4 q1 = __ldg(reinterpret_cast<const float4 *>(bf + g.plane + node));
-            bu[0] = q0.x; bu[1] = q0.y; bu[2] = q0.z; bu[3] = q0.w;
-            bv[0] = q1.x; bv[1] = q1.y; bv[2] = q1.z; bv[3] = q1.w;
-        }
-        float ru[4], rv[4], rp[4];
-        auto run_nodes = [&](auto yedge) {
-            constexpr bool YE = decltype(yedge)::value;
-            // a run spans one coarse cell (R = 4) or two (R = 2)
-#pragma unroll
-            for (int cg = 0; cg < 4 / R; ++cg) {
-                const int cxl = ((I0 + Ia + cg * R) >> K) - cx0;   // own cell column in the window
-                Cell own, left, low, lowleft;
-                own.load(c, cs, SH::CW, SH::CH, cyl * SH::CW + cxl);
-                left.load(c, cs, SH::CW, SH::CH, cyl * SH::CW + cxl - 1);
-                if constexpr (YE) {
-                    low.load(c, cs, SH::CW, SH::CH, (cyl - 1) * SH::CW + cxl);
-                    lowleft.load(c, cs, SH::CW, SH::CH, (cyl - 1) * SH::CW + cxl - 1);
-                }
-#pragma unroll
-                for (int a = 0; a < R; ++a) {
-                    const int n = cg * R + a;
-                    float Au, Av, Ap;
-                    if (a == 0)
-                        node_A<true, YE>(c, own, left, low, lowleft, 0.0f, Y, Au, Av, Ap);
-                    else
-                        node_A<false, YE>(c, own, left, low, lowleft, (float)a * c.hx, Y, Au, Av, Ap);
-                    ru[n] = bu[n] - Au;
-                    rv[n] = bv[n] - Av;
-                    rp[n] = -Ap;
-                }
-            }
-        };
-        if (on_edge)
-            run_nodes(std::true_type{});
-        else
-            run_nodes(std::false_type{});
-        TX *dst = rres + J * CF_RXP + Ia;
-        put4(dst, ru);
-        put4(dst + CF_RPL, rv);
-        put4(dst + 2 * CF_RPL, rp);
-    } else if (t < 8 * (NNZ + NZ) + CF_NYN) {
-        // the tile's last node column (the next tile's first): one node
-        const int J = t - 8 * (NNZ + NZ);
-        const int b = J & (R - 1);
-        const int cyl = ((J0 + J) >> K) - cy0, cxl = ((I0 + CF_TXC) >> K) - cx0;
-        Cell own, left, low, lowleft;
-        own.load(c, cs, SH::CW, SH::CH, cyl * SH::CW + cxl);
-        left.load(c, cs, SH::CW, SH::CH, cyl * SH::CW + cxl - 1);
-        float Au, Av, Ap;
-        const float Y = (float)b * c.hy;
-        if (b == 0) {
-            low.load(c, cs, SH::CW, SH::CH, (cyl - 1) * SH::CW + cxl);
-            lowleft.load(c, cs, SH::CW, SH::CH, (cyl - 1) * SH::CW + cxl - 1);
-            node_A<true, true>(c, own, left, low, lowleft, 0.0f, Y, Au, Av, Ap);
-        } else {
-            node_A<true, false>(c, own, left, low, lowleft, 0.0f, Y, Au, Av, Ap);
-        }
-        const size_t node = (size_t)(J0 + J) * g.pitch + I0 + CF_TXC;
-        TX *dst = rres + J * CF_RXP + CF_TXC;
-        dst[0] = to_feat<TX>(__ldg(bf + node) - Au);
-        dst[CF_RPL] = to_feat<TX>(__ldg(bf + g.plane + node) - Av);
-        dst[2 * CF_RPL] = to_feat<TX>(-Ap);
+    if (t < SH::NFULL) {
+        const int cj = t / SH::NCX, ci = t - cj * SH::NCX;
+        cell_task<TX, R, true, true>(c, cs, SH::CW, SH::CH, ci, cj, g, bf, I0, J0, rres);
+    } else if (t < SH::NFULL + SH::NCX) {
+        cell_task<TX, R, true, false>(c, cs, SH::CW, SH::CH, t - SH::NFULL, SH::NCY, g, bf, I0, J0, rres);
+    } else if (t < SH::NFULL + SH::NCX + SH::NCY) {
+        cell_task<TX, R, false, true>(c, cs, SH::CW, SH::CH, SH::NCX, t - SH::NFULL - SH::NCX, g, bf, I0, J0, rres);
+    } else if (t == SH::NFULL + SH::NCX + SH::NCY) {
+        cell_task<TX, R, false, false>(c, cs, SH::CW, SH::CH, SH::NCX, SH::NCY, g, bf, I0, J0, rres);
     }
     __syncthreads();
-    // ---- feature rows: 16-byte pieces of each patch row, columns from the table
-    for (int q = threadIdx.x; q < SH::NP * SH::NCH; q += CF_THREADS) {
-        const int pp = q / SH::NCH, ch = q - pp * SH::NCH;
+    // ---- feature rows: 16-byte pieces of each patch row, columns from the table;
+    // pieces made of residual columns only, then the rest (mixed and extra columns)
+    constexpr int NRCH = SH::NRES / SH::EPC, NTCH = SH::NCH - NRCH;
+    for (int q = threadIdx.x; q < SH::NP * NRCH; q += SH::THREADS) {
+        const int pp = q / NRCH, ch = q - pp * NRCH;
+        const int id = pid[pp];
+        if (id < 0) continue;
+        const int py = pp / SH::TPX, px = pp - py * SH::TPX;
+        const TX *rb = rres + py * S * CF_RXP + px * S;
+        uint16_t e[SH::EPC];
+        load_entries<SH::EPC>(tab + ch * SH::EPC, e);
+        __align__(16) TX v[SH::EPC];
+#pragma unroll
+        for (int k = 0; k < SH::EPC; ++k) v[k] = rb[e[k]];
+        *reinterpret_cast<uint4 *>(X + (size_t)id * SH::LDX + ch * SH::EPC) = *reinterpret_cast<const uint4 *>(v);
+    }
+    for (int q = threadIdx.x; q < SH::NP * NTCH; q += SH::THREADS) {
+        const int pp = q / NTCH, ch = NRCH + (q - pp * NTCH);
         const int id = pid[pp];
         if (id < 0) continue;
         const int py = pp / SH::TPX, px = pp - py * SH::TPX;
         const TX *rb = rres + py * S * CF_RXP + px * S;
         const TX *eb = ex + pp * SH::EXW;
         uint16_t e[SH::EPC];
-        if constexpr (SH::EPC == 8) {
-            const uint4 tv = *reinterpret_cast<const uint4 *>(tab + ch * 8);
-            const uint32_t w[4] = {tv.x, tv.y, tv.z, tv.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                e[2 * k] = (uint16_t)(w[k] & 0xFFFFu);
-                e[2 * k + 1] = (uint16_t)(w[k] >> 16);
-            }
-        } else {
-            const uint2 tv = *reinterpret_cast<const uint2 *>(tab + ch * 4);
-            e[0] = (uint16_t)(tv.x & 0xFFFFu);
-            e[1] = (uint16_t)(tv.x >> 16);
-            e[2] = (uint16_t)(tv.y & 0xFFFFu);
-            e[3] = (uint16_t)(tv.y >> 16);
-        }
+        load_entries<SH::EPC>(tab + ch * SH::EPC, e);
         __align__(16) TX v[SH::EPC];
 #pragma unroll
         for (int k = 0; k < SH::EPC; ++k) v[k] = (e[k] & 0x8000u) ? eb[e[k] & 0x7FFFu] : rb[e[k]];
@@ -368,7 +424,7 @@ cudaError_t run_cf(const MeshGeom &g, const CfCoef &c, const float *xcp, const f
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::BYTES);
     if (e != cudaSuccess) return e;
     const dim3 grid((g.nxf + CF_TXC - 1) / CF_TXC, (g.nyf + CF_TYC - 1) / CF_TYC);
-    k<<<grid, CF_THREADS, SH::BYTES, st>>>(g, c, xcp, coarse_pitch(g), bf, X);
+    k<<<grid, SH::THREADS, SH::BYTES, st>>>(g, c, xcp, coarse_pitch(g), bf, X);
     return cudaGetLastError();
 }
 
@@ -396,6 +452,13 @@ void residual_cf_table(const MeshGeom &g, uint16_t *tab) {
             tab[col] = (uint16_t)(0x8000u | (col - nres));
         }
     }
+}
+
+void residual_cf_slow_tiles(const MeshGeom &g, const uint8_t *flags, std::vector<int> *slow) {
+    slow->clear();
+    for (int ty = 0; ty < g.nty; ++ty)
+        for (int tx = 0; tx < g.ntx; ++tx)
+            if (!block_fast_flags(flags, g.ntx, g.nty, tx / 2, ty)) slow->push_back(ty * g.ntx + tx);
 }
 
 bool residual_cf_supported(const MeshGeom &g, int prec) {
