@@ -111,26 +111,40 @@ __device__ __forceinline__ void cell_part(const CfCoef &c, float uw, float vw, f
     }
 }
 
-// One coarse cell's bilinear fields (u, v, p) from its corner values:
-// w = c00 + bx X + by Y + d X Y at offset (X, Y) from its SW corner.
+// One coarse cell's bilinear fields (u, v, p): w = c00 + bx X + by Y + d X Y
+// at offset (X, Y) from its SW corner.  The coefficients are formed once per
+// block from the corner values (cell_coefficients) and read from shared
+// memory where they are used, which keeps few of them in registers at a time.
+constexpr int CELL_COEF = 12;   // [c00, bx, by, d] x (u, v, p)
 struct Cell {
-    float c00[3], bx[3], by[3], d[3];
-    __device__ __forceinline__ void load(const CfCoef &c, const float *cs, int cw, int ch, int o) {
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const float *q = cs + f * cw * ch + o;
-            const float w00 = q[0], w10 = q[1], w01 = q[cw], w11 = q[cw + 1];
-            c00[f] = w00;
-            bx[f] = (w10 - w00) * c.iHx;
-            by[f] = (w01 - w00) * c.iHy;
-            d[f] = ((w11 - w10) - (w01 - w00)) * c.iHxy;
-        }
+    const float *q;             // the cell's coefficients in shared memory
+    __device__ __forceinline__ D3 der(int f, float X, float Y) const {
+        const float bx = q[4 * f + 1], by = q[4 * f + 2], d = q[4 * f + 3];
+        return D3{bx + d * Y, by + d * X, d};
     }
-    __device__ __forceinline__ D3 der(int f, float X, float Y) const { return D3{bx[f] + d[f] * Y, by[f] + d[f] * X, d[f]}; }
     __device__ __forceinline__ float value(int f, float X, float Y) const {
-        return c00[f] + bx[f] * X + Y * (by[f] + d[f] * X);
+        const float c00 = q[4 * f], bx = q[4 * f + 1], by = q[4 * f + 2], d = q[4 * f + 3];
+        return c00 + bx * X + Y * (by + d * X);
     }
 };
+
+// Coefficients of every coarse cell of the staged window: cells (a, b) with
+// SW node (a, b) of the window, a < cw - 1, b < ch - 1, into cc[(b (cw - 1) + a) 12 ..].
+__device__ __forceinline__ void cell_coefficients(const CfCoef &c, const float *cs, int cw, int ch, float *cc,
+                                                  int nthreads) {
+    const int ncx = cw - 1, n = ncx * (ch - 1);
+    for (int e = threadIdx.x; e < 3 * n; e += nthreads) {
+        const int f = e / n, cell = e - f * n;
+        const int b = cell / ncx, a = cell - b * ncx;
+        const float *q = cs + f * cw * ch + b * cw + a;
+        const float w00 = q[0], w10 = q[1], w01 = q[cw], w11 = q[cw + 1];
+        float *o = cc + cell * CELL_COEF + 4 * f;
+        o[0] = w00;
+        o[1] = (w10 - w00) * c.iHx;
+        o[2] = (w01 - w00) * c.iHy;
+        o[3] = ((w11 - w10) - (w01 - w00)) * c.iHxy;
+    }
+}
 
 // A(x~) at a node at offset (X, Y) in its own cell (the cell above and to
 // the right): XE / YE say whether the node lies on a vertical / horizontal
@@ -230,23 +244,20 @@ template <int R> __device__ __forceinline__ void load_row(const float *p, float 
 
 // The fine nodes of coarse cell (ci, cj) of the block (block-local coarse
 // indices; the block's first staged coarse node is window node (1, 1) minus
-// one): rows b = 0 .. R-1 when FY (else row 0 only), columns a = 0 .. R-1
-// when FX (else column 0 only).  Node (a, b) lies on a vertical coarse edge
+// one): rows b = B0 .. B1-1, columns a = 0 .. R-1 when FX (else column 0
+// only).  Node (a, b) lies on a vertical coarse edge
 // when a = 0 and on a horizontal one when b = 0.  Residuals r = b_f - A(x~)
 // go to the block's residual array in the feature type.
-template <typename TX, int R, bool FX, bool FY>
-__device__ __forceinline__ void cell_task(const CfCoef &c, const float *cs, int cw, int ch, int ci, int cj,
+template <typename TX, int R, bool FX, int B0, int B1>
+__device__ __forceinline__ void cell_task(const CfCoef &c, const float *cc, int ncx, int ci, int cj,
                                           const MeshGeom &g, const float *__restrict__ bf, int I0, int J0, TX *rres) {
-    Cell own, left, low, lowleft;
-    const int o = (cj + 1) * cw + ci + 1;   // own cell's SW node in the window
-    own.load(c, cs, cw, ch, o);
-    left.load(c, cs, cw, ch, o - 1);
-    low.load(c, cs, cw, ch, o - cw);
-    lowleft.load(c, cs, cw, ch, o - cw - 1);
-    constexpr int NA = FX ? R : 1, NB = FY ? R : 1;
+    const int o = (cj + 1) * ncx + ci + 1;   // own cell in the window's cell array
+    const Cell own{cc + o * CELL_COEF}, left{cc + (o - 1) * CELL_COEF}, low{cc + (o - ncx) * CELL_COEF},
+        lowleft{cc + (o - ncx - 1) * CELL_COEF};
+    constexpr int NA = FX ? R : 1;
     const int Il = ci * R, Jl = cj * R;     // block-local fine node of the cell's SW corner
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
+    for (int b = B0; b < B1; ++b) {
         const float Y = (float)b * c.hy;
         const size_t node = (size_t)(J0 + Jl + b) * g.pitch + I0 + Il;
         float bu[R], bv[R], ru[R], rv[R], rp[R];
@@ -301,7 +312,8 @@ struct CfShape {
     static constexpr int THREADS = (NTASK + 31) / 32 * 32;
     // shared memory (bytes)
     static constexpr size_t CS = 0;                                               // [3][CH][CW] float
-    static constexpr size_t RR = (CS + 3 * CW * CH * 4 + 15) / 16 * 16;           // [3][NYN][RXP] TX
+    static constexpr size_t CC = (CS + 3 * CW * CH * 4 + 15) / 16 * 16;           // [cells][12] float
+    static constexpr size_t RR = (CC + (CW - 1) * (CH - 1) * CELL_COEF * 4 + 15) / 16 * 16;   // [3][NYN][RXP] TX
     static constexpr size_t TAB = (RR + 3 * CF_RPL * sizeof(TX) + 15) / 16 * 16;  // [LDX] uint16
     static constexpr size_t PID = (TAB + LDX * 2 + 15) / 16 * 16;                 // [NP] int
     static constexpr size_t EX = (PID + NP * 4 + 15) / 16 * 16;                   // [NP][EXW] TX
@@ -315,7 +327,7 @@ struct CfShape {
 // tile's last node column.  Then the feature rows of the tile's patches are
 // gathered from shared memory in 16-byte pieces.
 template <typename TX, int R, int SP>
-__global__ void __launch_bounds__(CfShape<TX, R, SP>::THREADS, R == 4 ? 8 : 3)
+__global__ void __launch_bounds__(CfShape<TX, R, SP>::THREADS, R == 4 ? 10 : 3)
 k_residual_cf(MeshGeom g, CfCoef c, const float *__restrict__ xcp, int pc, const float *__restrict__ bf,
               TX *__restrict__ X) {
     using SH = CfShape<TX, R, SP>;
@@ -324,6 +336,7 @@ k_residual_cf(MeshGeom g, CfCoef c, const float *__restrict__ xcp, int pc, const
     if (!block_fast(g, tx, ty)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     float *cs = reinterpret_cast<float *>(smem + SH::CS);
+    float *cc = reinterpret_cast<float *>(smem + SH::CC);
     TX *rres = reinterpret_cast<TX *>(smem + SH::RR);
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem + SH::TAB);
     int *pid = reinterpret_cast<int *>(smem + SH::PID);
@@ -367,6 +380,8 @@ k_residual_cf(MeshGeom g, CfCoef c, const float *__restrict__ xcp, int pc, const
         }
         ex[e] = to_feat<TX>(val);
     }
+    cell_coefficients(c, cs, SH::CW, SH::CH, cc, SH::THREADS);
+    __syncthreads();
     // ---- node pass: one thread per coarse cell of the block, taking every
     // fine node of the cell (its rows 0 .. R-1, columns 0 .. R-1), so that
     // every thread has the same mix of corner, edge and interior nodes; the
@@ -375,13 +390,13 @@ k_residual_cf(MeshGeom g, CfCoef c, const float *__restrict__ xcp, int pc, const
     const int t = threadIdx.x;
     if (t < SH::NFULL) {
         const int cj = t / SH::NCX, ci = t - cj * SH::NCX;
-        cell_task<TX, R, true, true>(c, cs, SH::CW, SH::CH, ci, cj, g, bf, I0, J0, rres);
+        cell_task<TX, R, true, 0, R>(c, cc, SH::CW - 1, ci, cj, g, bf, I0, J0, rres);
     } else if (t < SH::NFULL + SH::NCX) {
-        cell_task<TX, R, true, false>(c, cs, SH::CW, SH::CH, t - SH::NFULL, SH::NCY, g, bf, I0, J0, rres);
+        cell_task<TX, R, true, 0, 1>(c, cc, SH::CW - 1, t - SH::NFULL, SH::NCY, g, bf, I0, J0, rres);
     } else if (t < SH::NFULL + SH::NCX + SH::NCY) {
-        cell_task<TX, R, false, true>(c, cs, SH::CW, SH::CH, SH::NCX, t - SH::NFULL - SH::NCX, g, bf, I0, J0, rres);
+        cell_task<TX, R, false, 0, R>(c, cc, SH::CW - 1, SH::NCX, t - SH::NFULL - SH::NCX, g, bf, I0, J0, rres);
     } else if (t == SH::NFULL + SH::NCX + SH::NCY) {
-        cell_task<TX, R, false, false>(c, cs, SH::CW, SH::CH, SH::NCX, SH::NCY, g, bf, I0, J0, rres);
+        cell_task<TX, R, false, 0, 1>(c, cc, SH::CW - 1, SH::NCX, SH::NCY, g, bf, I0, J0, rres);
     }
     __syncthreads();
     // ---- feature rows: 16-byte pieces of each patch row, columns from the table;
