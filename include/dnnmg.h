@@ -463,6 +463,70 @@ int dnnmg_adam_step(float *p, const float *g, float *m, float *v, long long n, i
  */
 int dnnmg_selftest_wait_timeout(long long limit_ns, int *status, long long *waited_ns);
 
+/*
+ * ---- Plain multigrid fine solve (the method DNN-MG is compared with) --------
+ *
+ * Sec. 3.3 solves each time step's system (Eq. nonlinearshort) by Newton's
+ * method, each Newton system by GMRES with a geometric multigrid
+ * preconditioner (Sec. 3.4, Algorithm 1) smoothed by the Vanka method; Sec.
+ * 6.4 times DNN-MG against it.  These calls are the GPU pieces of that
+ * solver on a hierarchy of uniform levels; the iterations are driven from the
+ * host (paper_2008_11520_gb300/mg.py).  Level 0 is the finest (nx x ny
+ * cells); level l has nx / 2^l x ny / 2^l cells.  Node fields are [3][N]
+ * (u, v, p), N = (nx_l + 1)(ny_l + 1), x fastest, without padding, in the
+ * handle's precision (double for DNNMG_F64, float for DNNMG_F32), in device
+ * memory owned by the caller.  The discretisation is the correction step's
+ * (Q1/Q1, Crank-Nicolson, local projection stabilisation, 2 x 2 Gauss).
+ * Any finest mask is accepted (a partly solid projection patch contributes
+ * the integrals of its fluid cells); a coarser level's patch is solid iff all
+ * 16 cells under it on the finer level are.  All calls
+ * except create/destroy/level are asynchronous on `stream`.
+ */
+typedef struct dnnmg_mg_desc {
+    int nx, ny;                 /* cells of the finest level, multiples of 2^levels */
+    int levels;                 /* 1 .. 12 */
+    double lx, ly;              /* channel size */
+    const unsigned char *solid; /* [ny][nx] cell mask of the finest level (host, may be NULL) */
+    double nu, k, alpha0, u_max;
+    int ramp;                   /* start-up ramp of the inflow (Sec. 6.1) */
+    int precision;              /* DNNMG_F64 or DNNMG_F32 */
+} dnnmg_mg_desc;
+typedef struct dnnmg_mg_s *dnnmg_mg_t;
+
+int dnnmg_mg_create(const dnnmg_mg_desc *desc, dnnmg_mg_t *out);
+int dnnmg_mg_destroy(dnnmg_mg_t mg);
+/* Cells of a level and (when solid is not NULL) its cell mask [ny][nx] (host). */
+int dnnmg_mg_level(dnnmg_mg_t mg, int level, int *nx, int *ny, unsigned char *solid);
+/* Newton defect F(x) (Sec. 3.3): A(x) - b on free rows, x - g(t) on velocity
+ * Dirichlet rows (g: parabolic inflow at t, else 0) and p on inactive pressure
+ * rows.  b: [3][N] (pressure rows normally 0). */
+int dnnmg_mg_defect(dnnmg_mg_t mg, int level, const void *x, const void *b, double t, void *F, cudaStream_t stream);
+/* Right-hand side b = Rhs(x) of Eq. 4cranknicholson3 (f = 0) from the
+ * velocity of x: [3][N], Dirichlet and pressure rows 0; x, b must not alias. */
+int dnnmg_mg_rhs(dnnmg_mg_t mg, int level, const void *x, void *b, cudaStream_t stream);
+/* y = J(x) dx, J the Newton matrix of the defect (fixed rows: identity). */
+int dnnmg_mg_jvp(dnnmg_mg_t mg, int level, const void *x, const void *dx, void *y, cudaStream_t stream);
+/* One Vanka sweep (Sec. 3.4) for J(x) d = r, d = dx updated in place: for
+ * each of 16 cell colours (ci mod 4, cj mod 4) in turn, every fluid cell of
+ * the colour solves the 12 x 12 block of J(x) on the unknowns of its 4 nodes
+ * against the current defect r - J(x) d there (fixed unknowns: correction 0)
+ * and adds omega times the solution to d (block Gauss-Seidel; cells of one
+ * colour are independent, so the sweep is deterministic).  dx must not
+ * alias x or r. */
+int dnnmg_mg_vanka(dnnmg_mg_t mg, int level, const void *x, const void *r, void *dx, double omega,
+                   cudaStream_t stream);
+/* rc = P^T rf from level to level + 1 (fixed rows of level + 1 zeroed). */
+int dnnmg_mg_restrict(dnnmg_mg_t mg, int level, const void *rf, void *rc, cudaStream_t stream);
+/* df += P dc from level + 1 to level (fixed rows of level unchanged). */
+int dnnmg_mg_prolong_add(dnnmg_mg_t mg, int level, const void *dc, void *df, cudaStream_t stream);
+/* xc = xf at the nodes of level + 1 (linearisation point of the coarser level). */
+int dnnmg_mg_inject(dnnmg_mg_t mg, int level, const void *xf, void *xc, cudaStream_t stream);
+/* *out (device double) = sum a_i b_i over n elements (FP64 accumulation). */
+int dnnmg_mg_dot(dnnmg_mg_t mg, long long n, const void *a, const void *b, double *out, cudaStream_t stream);
+/* y = alpha x + beta y over n elements (beta = 0: y = alpha x). */
+int dnnmg_mg_axpby(dnnmg_mg_t mg, long long n, double alpha, const void *x, double beta, void *y,
+                   cudaStream_t stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char *dnnmg_last_error(void);
 

@@ -313,6 +313,27 @@ int check_mesh(dnnmg_mesh_t m) {
 }  // namespace
 }  // namespace dnnmg
 
+namespace dnnmg {
+// Element constants of a single uniform level of nx x ny cells (the
+// multigrid levels): the same construction as a mesh's fine level.
+void level_coefficients(double lx, double ly, int nx, int ny, double nu, double k, double alpha0,
+                        FemCoef<double> *f64, FemCoef<float> *f32) {
+    dnnmg_mesh_desc d;
+    memset(&d, 0, sizeof d);
+    d.nxc = nx;
+    d.nyc = ny;
+    d.K = 0;
+    d.s = 1;
+    d.lx = lx;
+    d.ly = ly;
+    d.nu = nu;
+    d.k = k;
+    d.alpha0 = alpha0;
+    fem_coefficients(d, f64);
+    to_float(*f64, f32);
+}
+}  // namespace dnnmg
+
 using namespace dnnmg;
 
 extern "C" {

@@ -54,6 +54,14 @@ class MeshInfo(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class MgDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("levels", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("solid", ctypes.POINTER(ctypes.c_ubyte)),
+                ("nu", ctypes.c_double), ("k", ctypes.c_double), ("alpha0", ctypes.c_double),
+                ("u_max", ctypes.c_double), ("ramp", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2008_11520_gb300.build.build() "
@@ -107,6 +115,18 @@ def _load():
         "dnnmg_selftest_wait_timeout": [ctypes.c_longlong, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)],
         "dnnmg_adam_step": [P, P, P, P, ctypes.c_longlong, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             ctypes.c_float, ctypes.c_float, P],
+        "dnnmg_mg_create": [ctypes.POINTER(MgDesc), ctypes.POINTER(P)],
+        "dnnmg_mg_destroy": [P],
+        "dnnmg_mg_level": [P, I, ctypes.POINTER(I), ctypes.POINTER(I), P],
+        "dnnmg_mg_defect": [P, I, P, P, D, P, P],
+        "dnnmg_mg_rhs": [P, I, P, P, P],
+        "dnnmg_mg_jvp": [P, I, P, P, P, P],
+        "dnnmg_mg_vanka": [P, I, P, P, P, D, P],
+        "dnnmg_mg_restrict": [P, I, P, P, P],
+        "dnnmg_mg_prolong_add": [P, I, P, P, P],
+        "dnnmg_mg_inject": [P, I, P, P, P],
+        "dnnmg_mg_dot": [P, ctypes.c_longlong, P, P, P, P],
+        "dnnmg_mg_axpby": [P, ctypes.c_longlong, D, P, D, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -649,3 +669,101 @@ def dnnmg_selftest_wait_timeout(limit_ns):
     _check(_lib.dnnmg_selftest_wait_timeout(int(limit_ns), ctypes.byref(st), w))
     return st.value, [w[0], w[1]]
 
+
+
+# ---------------------------------------------------------------- plain multigrid
+class MG:
+    """Owning wrapper of a dnnmg_mg_t: the level hierarchy of the plain
+    multigrid fine solve (dnnmg_mg_* calls; iterations in mg.py)."""
+
+    def __init__(self, nx, ny, levels, solid=None, precision="f64", lx=2.2, ly=0.41, nu=1e-3, k=0.01,
+                 alpha0=0.1, u_max=1.5, ramp=False):
+        d = MgDesc()
+        d.nx, d.ny, d.levels = nx, ny, levels
+        d.lx, d.ly, d.nu, d.k, d.alpha0, d.u_max, d.ramp = lx, ly, nu, k, alpha0, u_max, int(ramp)
+        d.precision = PRECISIONS[precision]
+        if d.precision == BF16NET:
+            raise ValueError("the multigrid solve runs in f64 or f32")
+        keep = None
+        if solid is not None:
+            keep = np.ascontiguousarray(np.asarray(solid, dtype=np.uint8))
+            if keep.shape != (ny, nx):
+                raise ValueError("solid must be [ny][nx]")
+            d.solid = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        h = ctypes.c_void_p()
+        _check(_lib.dnnmg_mg_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.levels = levels
+        self.precision = precision
+        self.real = _REAL[d.precision]
+        self.params = dict(lx=lx, ly=ly, nu=nu, k=k, alpha0=alpha0, u_max=u_max, ramp=ramp)
+
+    def close(self):
+        if self.handle:
+            _lib.dnnmg_mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level(self, l):
+        """(nx, ny, solid [ny][nx] bool) of level l."""
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.dnnmg_mg_level(self.handle, l, ctypes.byref(nx), ctypes.byref(ny), None))
+        m = np.zeros((ny.value, nx.value), dtype=np.uint8)
+        _check(_lib.dnnmg_mg_level(self.handle, l, None, None, m.ctypes.data_as(ctypes.c_void_p)))
+        return nx.value, ny.value, m.astype(bool)
+
+    def nodes(self, l):
+        nx, ny, _ = self.level(l)
+        return (nx + 1) * (ny + 1)
+
+    def field(self, l, device="cuda"):
+        return torch.zeros(3, self.nodes(l), dtype=self.real, device=device)
+
+    def _f(self, l, t, name):
+        _need(t, self.real, 3 * self.nodes(l), name)
+        return _ptr(t)
+
+    def defect(self, l, x, b, t, F, stream=None):
+        _check(_lib.dnnmg_mg_defect(self.handle, l, self._f(l, x, "x"), self._f(l, b, "b"), float(t),
+                                    self._f(l, F, "F"), _stream(stream)))
+
+    def rhs(self, l, x, b, stream=None):
+        _check(_lib.dnnmg_mg_rhs(self.handle, l, self._f(l, x, "x"), self._f(l, b, "b"), _stream(stream)))
+
+    def jvp(self, l, x, dx, y, stream=None):
+        _check(_lib.dnnmg_mg_jvp(self.handle, l, self._f(l, x, "x"), self._f(l, dx, "dx"), self._f(l, y, "y"),
+                                 _stream(stream)))
+
+    def vanka(self, l, x, r, dx, omega, stream=None):
+        _check(_lib.dnnmg_mg_vanka(self.handle, l, self._f(l, x, "x"), self._f(l, r, "r"), self._f(l, dx, "dx"),
+                                   float(omega), _stream(stream)))
+
+    def restrict(self, l, rf, rc, stream=None):
+        _check(_lib.dnnmg_mg_restrict(self.handle, l, self._f(l, rf, "rf"), self._f(l + 1, rc, "rc"),
+                                      _stream(stream)))
+
+    def prolong_add(self, l, dc, df, stream=None):
+        _check(_lib.dnnmg_mg_prolong_add(self.handle, l, self._f(l + 1, dc, "dc"), self._f(l, df, "df"),
+                                         _stream(stream)))
+
+    def inject(self, l, xf, xc, stream=None):
+        _check(_lib.dnnmg_mg_inject(self.handle, l, self._f(l, xf, "xf"), self._f(l + 1, xc, "xc"),
+                                    _stream(stream)))
+
+    def dot(self, a, b, out, stream=None):
+        """out: a CUDA float64 tensor of one element (written on the stream)."""
+        if a.dtype != self.real or b.dtype != self.real or a.numel() != b.numel():
+            raise TypeError("dot: operands of the handle's precision and equal size")
+        _need(out, torch.float64, 1, "out")
+        _check(_lib.dnnmg_mg_dot(self.handle, a.numel(), _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+
+    def axpby(self, alpha, x, beta, y, stream=None):
+        if x.dtype != self.real or y.dtype != self.real or x.numel() != y.numel():
+            raise TypeError("axpby: operands of the handle's precision and equal size")
+        _check(_lib.dnnmg_mg_axpby(self.handle, x.numel(), float(alpha), _ptr(x), float(beta), _ptr(y),
+                                   _stream(stream)))
