@@ -479,7 +479,8 @@ int dnnmg_selftest_wait_timeout(long long limit_ns, int *status, long long *wait
  * (Q1/Q1, Crank-Nicolson, local projection stabilisation, 2 x 2 Gauss).
  * Any finest mask is accepted (a partly solid projection patch contributes
  * the integrals of its fluid cells); a coarser level's patch is solid iff all
- * 16 cells under it on the finer level are.  All calls
+ * 16 cells under it on the finer level are, and every level uses the finest
+ * level's projection coefficient (alpha0 scaled by 4^-level).  All calls
  * except create/destroy/level are asynchronous on `stream`.
  */
 typedef struct dnnmg_mg_desc {
@@ -509,10 +510,11 @@ int dnnmg_mg_jvp(dnnmg_mg_t mg, int level, const void *x, const void *dx, void *
 /* One Vanka sweep (Sec. 3.4) for J(x) d = r, d = dx updated in place: for
  * each of 16 cell colours (ci mod 4, cj mod 4) in turn, every fluid cell of
  * the colour solves the 12 x 12 block of J(x) on the unknowns of its 4 nodes
- * against the current defect r - J(x) d there (fixed unknowns: correction 0)
- * and adds omega times the solution to d (block Gauss-Seidel; cells of one
- * colour are independent, so the sweep is deterministic).  dx must not
- * alias x or r. */
+ * against the current defect r - J(x) d there (rows of fixed unknowns:
+ * identity) and adds omega times the solution to d (block Gauss-Seidel; cells of one
+ * colour are independent, so the sweep is deterministic); then every fixed
+ * unknown takes d = r (its exact correction; this reaches nodes inside an
+ * obstacle that no cell block holds).  dx must not alias x or r. */
 int dnnmg_mg_vanka(dnnmg_mg_t mg, int level, const void *x, const void *r, void *dx, double omega,
                    cudaStream_t stream);
 /* rc = P^T rf from level to level + 1 (fixed rows of level + 1 zeroed). */

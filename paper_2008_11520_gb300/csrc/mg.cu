@@ -20,7 +20,12 @@
 // the integrals of its fluid cells, as on the coarse level of the host
 // solver); level l+1 has half the cells of level l in each direction, and a
 // patch of level l+1 is solid iff all 16 cells of level l under it are.
-// (Coarse levels only precondition: their geometry approximates the fine one.)
+// Every level uses the finest level's projection coefficient alpha (alpha0
+// scaled by 4^-l): the fine projection term vanishes on a prolongated
+// pressure, and alpha = alpha0 h^2 / nu evaluated with a coarse h would
+// outweigh the pressure coupling of the time step there and make the coarse
+// pressure corrections far too small.  (Coarse levels only precondition:
+// their geometry and stabilisation approximate the fine ones.)
 //
 // The smoother is multiplicative (block Gauss-Seidel over cells) in 16
 // colours.  A cell's local defect reads the correction up to two nodes beyond
@@ -253,8 +258,8 @@ __global__ void __launch_bounds__(MG_THREADS) k_mg_jvp(MgLev<T> L, const T *__re
 // One colour pass of the Vanka smoother for J(x) d = rhs: every fluid cell
 // (ci, cj) with ci = cx (mod 4), cj = cy (mod 4) solves the 12 x 12 block of
 // J(x) on the unknowns of its four nodes against the current defect
-// rhs - J(x) d on those unknowns (rows of fixed unknowns: identity, right-
-// hand side 0) and adds omega times the solution to d.  Cells of one colour
+// rhs - J(x) d on those unknowns (rows of fixed unknowns: identity) and adds
+// omega times the solution to d.  Cells of one colour
 // are four cells apart: none reads a node another one writes, so the pass is
 // a block Gauss-Seidel step in any order.
 template <typename T>
@@ -331,7 +336,9 @@ __global__ void __launch_bounds__(128) k_mg_vanka(MgLev<T> L, const T *__restric
                 }
             }
         }
-    // right-hand side: the defect rhs - J(x) d on the cell's unknowns; fixed unknowns keep their value
+    // right-hand side: the defect rhs - J(x) d on the cell's unknowns.  Rows of
+    // fixed unknowns are identity rows of J, so their correction is exactly
+    // their defect (the first cell that holds one sets it, later ones add 0).
     T z[12];
     for (int a = 0; a < 4; ++a) {
         const uint8_t fl = L.flags[gn[a]];
@@ -340,14 +347,21 @@ __global__ void __launch_bounds__(128) k_mg_vanka(MgLev<T> L, const T *__restric
         for (int c = 0; c < 3; ++c) {
             const int i = 3 * a + c;
             const bool fixed = c < 2 ? (fl & 1) : !(fl & 4);
-            z[i] = fixed ? T(0) : rhs[c * L.N + gn[a]] - jd[c];
+            z[i] = rhs[c * L.N + gn[a]] - jd[c];
             if (fixed) {
                 for (int j = 0; j < 12; ++j) A[i][j] = T(0);
                 A[i][i] = T(1);
             }
         }
     }
-    // Gaussian elimination with partial pivoting
+    // Gaussian elimination with partial pivoting.  A block can be singular: a
+    // cell whose 4 nodes all hold Dirichlet velocities couples its pressures
+    // only through the projection term, which vanishes on linear functions.
+    // A pivot below a relative threshold leaves that unknown's correction 0.
+    T scale = T(0);
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j) scale = fmax(scale, fabs(A[i][j]));
+    const T tiny = scale * (sizeof(T) == 8 ? T(1e-12) : T(1e-6));
     for (int k = 0; k < 12; ++k) {
         int piv = k;
         T best = fabs(A[k][k]);
@@ -366,7 +380,13 @@ __global__ void __launch_bounds__(128) k_mg_vanka(MgLev<T> L, const T *__restric
             z[k] = z[piv];
             z[piv] = tz;
         }
-        const T inv = A[k][k] != T(0) ? T(1) / A[k][k] : T(0);
+        if (best <= tiny) {
+            A[k][k] = T(1);
+            for (int j = k + 1; j < 12; ++j) A[k][j] = T(0);
+            z[k] = T(0);
+            continue;
+        }
+        const T inv = T(1) / A[k][k];
         for (int i = k + 1; i < 12; ++i) {
             const T f = A[i][k] * inv;
             if (f == T(0)) continue;
@@ -377,10 +397,25 @@ __global__ void __launch_bounds__(128) k_mg_vanka(MgLev<T> L, const T *__restric
     for (int k = 11; k >= 0; --k) {
         T s = z[k];
         for (int j = k + 1; j < 12; ++j) s -= A[k][j] * z[j];
-        z[k] = A[k][k] != T(0) ? s / A[k][k] : T(0);
+        z[k] = s / A[k][k];
     }
     for (int a = 0; a < 4; ++a)
         for (int c = 0; c < 3; ++c) dx[c * L.N + gn[a]] += omega * z[3 * a + c];
+}
+
+// End of a Vanka sweep: every fixed unknown (an identity row of J) takes its
+// exact correction, its defect: d = rhs there.  This also reaches the nodes
+// that no fluid cell holds (inside an obstacle), which no cell block visits.
+template <typename T>
+__global__ void __launch_bounds__(MG_THREADS) k_mg_fixed(MgLev<T> L, const T *__restrict__ rhs, T *__restrict__ dx) {
+    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= L.N) return;
+    const uint8_t fl = L.flags[node];
+    if (fl & 1) {
+        dx[node] = rhs[node];
+        dx[L.N + node] = rhs[L.N + node];
+    }
+    if (!(fl & 4)) dx[2 * L.N + node] = rhs[2 * L.N + node];
 }
 
 // Restriction rc = P^T rf from level l (fine) to l+1 (coarse): full weighting
@@ -640,9 +675,13 @@ int dnnmg_mg_create(const dnnmg_mg_desc *d, dnnmg_mg_t *out) {
                 }
         }
         node_classes(h);
-        level_coefficients(d->lx, d->ly, h.nx, h.ny, d->nu, d->k, d->alpha0, &h.f64, &h.f32);
+        // every level keeps the finest level's projection coefficient alpha:
+        // the fine term vanishes on prolongated pressures, and a coefficient
+        // growing with h^2 would swamp the coarse pressure corrections
+        const double alpha0_l = d->alpha0 / (double)(1LL << (2 * l));
+        level_coefficients(d->lx, d->ly, h.nx, h.ny, d->nu, d->k, alpha0_l, &h.f64, &h.f32);
         std::vector<double> lps;
-        lps_tables(h.f64, d->lx / h.nx, d->ly / h.ny, d->alpha0, d->nu, &lps);
+        lps_tables(h.f64, d->lx / h.nx, d->ly / h.ny, alpha0_l, d->nu, &lps);
         std::vector<float> lps32(lps.begin(), lps.end());
         if (cudaMalloc(&h.d_lps64, lps.size() * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h.d_lps32, lps32.size() * sizeof(float)) != cudaSuccess ||
@@ -757,6 +796,10 @@ int dnnmg_mg_vanka(dnnmg_mg_t m, int level, const void *x, const void *r, void *
                         (k_mg_vanka<float><<<blocks(nc, 128), 128, 0, s>>>(
                             dev_level<float>(*m, level), (const float *)x, (const float *)r, (float *)dx, (float)omega,
                             cx, cy)));
+    MG_DISPATCH((k_mg_fixed<double><<<blocks(h.N, MG_THREADS), MG_THREADS, 0, s>>>(
+                    dev_level<double>(*m, level), (const double *)r, (double *)dx)),
+                (k_mg_fixed<float><<<blocks(h.N, MG_THREADS), MG_THREADS, 0, s>>>(
+                    dev_level<float>(*m, level), (const float *)r, (float *)dx)));
     return DNNMG_OK;
 }
 

@@ -171,11 +171,12 @@ def vanka_reference(lev, x, r, d0, omega):
                     A = J[dofs][:, dofs].toarray()
                     z_rhs = res[dofs].copy()
                     for k, q in enumerate(dofs):
-                        if fixed[q]:
+                        if fixed[q]:                      # identity row of the Newton matrix
                             A[k, :] = 0.0
                             A[k, k] = 1.0
-                            z_rhs[k] = 0.0
                     d[dofs] += omega * np.linalg.solve(A, z_rhs)
+    # fixed unknowns (identity rows), also those in no fluid cell: correction = their defect
+    d[fixed] = r.ravel()[fixed]
     return d.reshape(3, N)
 
 
@@ -202,9 +203,7 @@ def test_vcycle_contracts(dn):
     x = dev(flow(lev))
     pm.linearize(x)
     rng = np.random.default_rng(11)
-    r = rng.standard_normal((3, lev.N))
-    r[:2, lev.dirichlet] = 0.0
-    r[2, ~lev.p_active] = 0.0
+    r = rng.standard_normal((3, lev.N))          # fixed rows included: the cycle must set them
     b = dev(r)
     d = pm.mg.field(0)
     res = b.clone()
@@ -222,7 +221,7 @@ def test_vcycle_contracts(dn):
     # every fine patch), while a coarse level keeps its own, so pressure
     # corrections on coarse scales are damped: the cycle contracts, but not
     # by the textbook factor.  GMRES takes up the rest.
-    check("mg V-cycle contraction (worst of 6)", max(rates), 0.8, "f64")
+    check("mg V-cycle contraction (worst of 6)", max(rates), 0.75, "f64")
 
 
 # FP32: the defect of a converged iterate is the rounding of its O(hx hy / k)
@@ -237,6 +236,7 @@ def test_newton_mg_step_matches_host(dn, prec, tol, single):
     pm = PlainMG(nx, ny, LEVELS, solid, prec)
     lev = host_level(nx, ny, solid)
     x0 = flow(lev)
+    x0[:2, lev.dirichlet] *= 0.9                   # the step must restore the boundary values
     t1 = 0.01
     ref = lev.solve(lev.rhs(x0[:2]), t1, x0=x0)
     x = dev(x0, pm.mg.real)
