@@ -282,11 +282,12 @@ def compare(workload="large", steps=2, precision="f32", newton_tol=1e-4, lin_rto
     _, corr_ms, _ = _timed(lambda: [dnnmg.dnnmg_step(mesh, net, xc, h, bf, bc, ws, 0.05 + 0.01 * i)
                                     for i in range(20)])
     out["dnnmg_correction_ms"] = corr_ms / 20
-    coarse = out["dnnmg_coarse"]["steps"][-1]["device_ms"]
-    fine = out["plain_fine"]["steps"][-1]["device_ms"]
-    out["dnnmg_step_ms"] = coarse + out["dnnmg_correction_ms"]
-    out["plain_step_ms"] = fine
-    out["speedup"] = fine / out["dnnmg_step_ms"]
+    if steps > 0:
+        coarse = out["dnnmg_coarse"]["steps"][-1]["device_ms"]
+        fine = out["plain_fine"]["steps"][-1]["device_ms"]
+        out["dnnmg_step_ms"] = coarse + out["dnnmg_correction_ms"]
+        out["plain_step_ms"] = fine
+        out["speedup"] = fine / out["dnnmg_step_ms"]
     return out
 
 
@@ -295,4 +296,6 @@ if __name__ == "__main__":
     import sys
     wl = sys.argv[1] if len(sys.argv) > 1 else "large"
     prec = sys.argv[2] if len(sys.argv) > 2 else "f32"
-    print(json.dumps(compare(wl, precision=prec, deadline_s=float(sys.argv[3]) if len(sys.argv) > 3 else 120.0)))
+    steps = int(sys.argv[4]) if len(sys.argv) > 4 else 2
+    print(json.dumps(compare(wl, steps=steps, precision=prec,
+                             deadline_s=float(sys.argv[3]) if len(sys.argv) > 3 else 120.0)))
