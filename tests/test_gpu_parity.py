@@ -407,11 +407,13 @@ def test_restrict_fp64_class_accuracy(dn, name):
     check("R b_f (FP64 class)", rel_l2(host(bc).reshape(3, -1), ref), 1e-13, case["prec"], case=name)
 
 
-GRU_SHAPES = [(51, 32, 18), (99, 64, 50), (99, 96, 50), (282, 128, 162), (60, 32, 40)]
+# (282, 64, 162): an output layer wider than 2H (two MMA pieces);
+# P = 40000: more tiles than SMs, so each persistent CTA walks several
+GRU_SHAPES = [(51, 32, 18), (99, 64, 50), (99, 96, 50), (282, 128, 162), (60, 32, 40), (282, 64, 162)]
 
 
 @pytest.mark.parametrize("shape", GRU_SHAPES)
-@pytest.mark.parametrize("P", [1, 127, 128, 300, 1000])
+@pytest.mark.parametrize("P", [1, 127, 128, 300, 1000, 40000])
 def test_gru_tensor_cores_match_cuda_cores(dn, shape, P, monkeypatch):
     # same BF16-operand arithmetic on the tcgen05 kernel and on CUDA cores;
     # only the FP32 summation order differs
