@@ -413,7 +413,8 @@ void dnnmg_pool_destroy(dnnmg_pool_t pool);
  * Forward and backward of Eq. gru followed by the output layer (Sec. 6.2),
  * unrolled over a window of T steps of P patch rows, for truncated
  * backpropagation through time; the l2 loss of Sec. 6.3 and its gradient;
- * Adam with the Tikhonov term of Sec. 6.3.  FP32 throughout (CUDA cores);
+ * Adam with the Tikhonov term of Sec. 6.3.  FP32 products on the CUDA cores,
+ * or BF16 products on the tensor cores (dnnmg_trainer_set_precision);
  * weight-gradient sums are split over the T P rows in a fixed order, so
  * results repeat bit for bit.  All arrays are caller-owned device memory:
  *   X [T][P][ldx] (columns n_in..ldx-1 ignored), h0 / dh0 [P][H],
@@ -426,6 +427,34 @@ typedef struct dnnmg_trainer_s *dnnmg_trainer_t;
 int dnnmg_trainer_create(int n_in, int ldx, int H, int n_out, int T, int P, dnnmg_trainer_t *out);
 /* Wait for the device, then free the trainer (NULL is allowed). */
 int dnnmg_trainer_destroy(dnnmg_trainer_t trainer);
+/*
+ * Arithmetic of the trainer's matrix products (the pointwise steps, the
+ * reductions and every array stay FP32; the training workload of Sec. 6.3
+ * asks for BF16 products with FP32 master weights):
+ *   DNNMG_F32      FP32 products on the CUDA cores (the default);
+ *   DNNMG_BF16NET  BF16 operands, FP32 accumulation, on the tensor cores
+ *                  (tcgen05): each product's operands are rounded to BF16
+ *                  (transposed where the product needs it) into scratch the
+ *                  trainer allocates here (about T P (3H + max(n_in, H))
+ *                  BF16 values).
+ * DNNMG_EINVAL for another value, DNNMG_ENOMEM if the scratch cannot be had.
+ */
+int dnnmg_trainer_set_precision(dnnmg_trainer_t trainer, int precision);
+/*
+ * Device status bits of the trainer's tensor-core products (DNNMG_DEVERR_*,
+ * e.g. a bounded wait that timed out); reset clears them.  Synchronous.
+ */
+int dnnmg_trainer_status(dnnmg_trainer_t trainer, int *status, int reset);
+/*
+ * C[M][N] (row stride ldc, FP32) = A[M][K] B[N][K]^T, or C += A B^T when
+ * accumulate is nonzero, on the tensor cores (tcgen05, FP32 accumulation);
+ * the training products' kernel, exported for testing.  A and B: BF16 device
+ * arrays, K contiguous, row strides lda, ldb elements (multiples of 8, at
+ * least K; 16-byte aligned).  *status (device int) receives DNNMG_DEVERR_*
+ * bits.  Asynchronous on stream.
+ */
+int dnnmg_gemm_bf16_nt(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                       int accumulate, int *status, cudaStream_t stream);
 /* D = outputs of the T steps from state h0 (NULL: h0 = 0); keeps the activations for the backward. */
 int dnnmg_gru_seq_forward(dnnmg_trainer_t trainer, const float *X, const float *h0, const float *Wx, const float *Uh,
                           const float *Wfc, float *D, cudaStream_t stream);

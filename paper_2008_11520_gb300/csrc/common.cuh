@@ -179,6 +179,12 @@ cudaError_t launch_gru_tc(const Net &n, const void *X, void *h, void *d, int P, 
 cudaError_t launch_gru_tc_rows(const Net &n, const void *X, void *h, void *d, int P, const int *hrow, int h_rows,
                                cudaStream_t st);
 bool tc_prepare(Net &n, const double *Wx, const double *Uh, const double *Wfc);
+// C (+)= A B^T with BF16 A [M][K] (lda), B [N][K] (ldb) on the tensor cores
+// (gemm_tc.cu); splits > 1: K-range partials to part (reduced by the caller),
+// gemm_tc_splits_used of them.
+cudaError_t launch_gemm_tc(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                           bool accumulate, int splits, float *part, int *status, cudaStream_t st);
+int gemm_tc_splits_used(int K, int splits);
 void tc_release(Net &n);
 // Per feature column: (kind << 24) | offset into the residual / node tiles of stencil.cu.
 void feature_table(const MeshGeom &g, int *tab);

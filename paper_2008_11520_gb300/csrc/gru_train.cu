@@ -163,6 +163,36 @@ cudaError_t gemm_splitk(int M, int N, int K, const float *A, int lda, const floa
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- BF16 products
+// K of a BF16 operand rounded up to whole 16-byte rows
+inline int kpad(int K) { return (K + 7) / 8 * 8; }
+
+// dst[i][k] (row stride ldd) = bf16(op(src)) for i < rows, k < K, where op(src)
+// is src [rows][K] (row stride ld), or with TR its transpose, src [K][rows];
+// 32 x 32 tiles through shared memory, so both sides move along rows.
+template <bool TR>
+__global__ void k_to_bf16(int rows, int K, const float *__restrict__ src, int ld, __nv_bfloat16 *__restrict__ dst,
+                          int ldd) {
+    __shared__ float tile[32][33];
+    const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    if (TR) {
+        for (int y = threadIdx.y; y < 32; y += 8) {
+            const int k = k0 + y, i = i0 + threadIdx.x;
+            tile[y][threadIdx.x] = (k < K && i < rows) ? src[(size_t)k * ld + i] : 0.f;
+        }
+        __syncthreads();
+        for (int y = threadIdx.y; y < 32; y += 8) {
+            const int i = i0 + y, k = k0 + threadIdx.x;
+            if (i < rows && k < K) dst[(size_t)i * ldd + k] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+        }
+    } else {
+        for (int y = threadIdx.y; y < 32; y += 8) {
+            const int i = i0 + y, k = k0 + threadIdx.x;
+            if (i < rows && k < K) dst[(size_t)i * ldd + k] = __float2bfloat16_rn(src[(size_t)i * ld + k]);
+        }
+    }
+}
+
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 // ---------------------------------------------------------------- pointwise
@@ -312,10 +342,44 @@ struct dnnmg_trainer_s {
     size_t part_floats;
     double *red;    // reduction partials [kRedBlocks]
     int splits;
+    // BF16 products (dnnmg_trainer_set_precision): operand scratch, K contiguous
+    int bf16;
+    __nv_bfloat16 *opA, *opB;
+    size_t opA_elems, opB_elems;
+    int *d_status;
 };
 
 namespace dnnmg {
 namespace {
+
+// One product of the trainer, C (+)= op(A) op(B) in the layouts of gemm():
+// FP32 on the CUDA cores, or (BF16 mode) its operands rounded to BF16 with K
+// contiguous and multiplied on the tensor cores.  split: K split over
+// t->splits ranges, reduced in a fixed order.
+template <bool TA, bool TB>
+cudaError_t prod(dnnmg_trainer_s *t, int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C,
+                 int ldc, bool accumulate, bool split, cudaStream_t st) {
+    if (!t->bf16)
+        return split ? gemm_splitk<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, t->splits, t->part, st)
+                     : gemm<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, accumulate, st);
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int kp = kpad(K);
+    if ((size_t)M * kp > t->opA_elems || (size_t)N * kp > t->opB_elems) return cudaErrorInvalidValue;
+    const dim3 blk(32, 8);
+    k_to_bf16<TA><<<dim3((K + 31) / 32, (M + 31) / 32), blk, 0, st>>>(M, K, A, lda, t->opA, kp);
+    k_to_bf16<!TB><<<dim3((K + 31) / 32, (N + 31) / 32), blk, 0, st>>>(N, K, B, ldb, t->opB, kp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (!split || t->splits <= 1)
+        return launch_gemm_tc(M, N, K, t->opA, kp, t->opB, kp, C, ldc, !split && accumulate, 1, nullptr, t->d_status,
+                              st);
+    e = launch_gemm_tc(M, N, K, t->opA, kp, t->opB, kp, C, ldc, false, t->splits, t->part, t->d_status, st);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)M * N;
+    k_reduce_splits<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, N, gemm_tc_splits_used(K, t->splits), t->part, C,
+                                                                  ldc, 0);
+    return cudaGetLastError();
+}
 
 void trainer_free(dnnmg_trainer_s *t) {
     if (!t) return;
@@ -323,6 +387,9 @@ void trainer_free(dnnmg_trainer_s *t) {
                      t->part};
     for (float *b : bufs) cudaFree(b);
     cudaFree(t->red);
+    cudaFree(t->opA);
+    cudaFree(t->opB);
+    cudaFree(t->d_status);
     delete t;
 }
 
@@ -383,6 +450,67 @@ int dnnmg_trainer_destroy(dnnmg_trainer_t t) {
     return DNNMG_OK;
 }
 
+int dnnmg_trainer_set_precision(dnnmg_trainer_t t, int precision) {
+    clear_error();
+    if (int e = check_trainer(t)) return e;
+    if (precision != DNNMG_F32 && precision != DNNMG_BF16NET)
+        return fail(DNNMG_EINVAL, "trainer precision must be DNNMG_F32 or DNNMG_BF16NET, got %d", precision);
+    t->bf16 = 0;
+    if (precision == DNNMG_F32) return DNNMG_OK;
+    // the largest operands of the window's products: activations with K up to
+    // max(n_in, 2H, n_out), and the weight gradients' with K = T P
+    const size_t TP = (size_t)t->T * t->P;
+    const size_t kmax = (size_t)kpad(std::max({t->n_in, 2 * t->H, t->n_out}));
+    const size_t ktp = (size_t)kpad((int)TP);
+    const size_t a = std::max({TP * kmax, (size_t)t->P * kmax, (size_t)std::max(3 * t->H, t->n_out) * ktp});
+    const size_t b = std::max({(size_t)std::max({t->n_in, 3 * t->H, t->n_out}) * kmax,
+                               (size_t)std::max(t->n_in, t->H) * ktp});
+    if (a > t->opA_elems || b > t->opB_elems || !t->d_status) {
+        cudaFree(t->opA);
+        cudaFree(t->opB);
+        t->opA = t->opB = nullptr;
+        t->opA_elems = t->opB_elems = 0;
+        if (cudaMalloc(&t->opA, a * sizeof(__nv_bfloat16)) != cudaSuccess ||
+            cudaMalloc(&t->opB, b * sizeof(__nv_bfloat16)) != cudaSuccess ||
+            (!t->d_status && cudaMalloc(&t->d_status, sizeof(int)) != cudaSuccess)) {
+            cudaFree(t->opA);
+            cudaFree(t->opB);
+            t->opA = t->opB = nullptr;
+            cudaGetLastError();
+            return fail(DNNMG_ENOMEM, "BF16 operand scratch (%zu + %zu values) could not be allocated", a, b);
+        }
+        DNNMG_CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
+        t->opA_elems = a;
+        t->opB_elems = b;
+    }
+    t->bf16 = 1;
+    return DNNMG_OK;
+}
+
+int dnnmg_trainer_status(dnnmg_trainer_t t, int *status, int reset) {
+    clear_error();
+    if (int e = check_trainer(t)) return e;
+    if (!status) return fail(DNNMG_EINVAL, "status is NULL");
+    *status = 0;
+    if (!t->d_status) return DNNMG_OK;
+    DNNMG_CUDA_TRY(cudaMemcpy(status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (reset) DNNMG_CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
+    return DNNMG_OK;
+}
+
+int dnnmg_gemm_bf16_nt(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                       int accumulate, int *status, cudaStream_t st) {
+    clear_error();
+    if (M < 0 || N < 0 || K < 0 || (M > 0 && N > 0 && (!A || !B || !C || !status)) || ldc < N)
+        return fail(DNNMG_EINVAL, "bad argument (M %d, N %d, K %d, ldc %d)", M, N, K, ldc);
+    cudaError_t e = launch_gemm_tc(M, N, K, A, lda, B, ldb, C, ldc, accumulate != 0, 1, nullptr, status, st);
+    if (e == cudaErrorInvalidValue)
+        return fail(DNNMG_EINVAL, "operands not taken: lda %d, ldb %d must be multiples of 8 and >= K %d, 16-byte aligned",
+                    lda, ldb, K);
+    DNNMG_CUDA_TRY(e);
+    return DNNMG_OK;
+}
+
 int dnnmg_gru_seq_forward(dnnmg_trainer_t t, const float *X, const float *h0, const float *Wx, const float *Uh,
                           const float *Wfc, float *D, cudaStream_t st) {
     clear_error();
@@ -395,21 +523,21 @@ int dnnmg_gru_seq_forward(dnnmg_trainer_t t, const float *X, const float *h0, co
     if (h0) DNNMG_CUDA_TRY(cudaMemcpyAsync(t->hs, h0, PH * sizeof(float), cudaMemcpyDeviceToDevice, st));
     else DNNMG_CUDA_TRY(cudaMemsetAsync(t->hs, 0, PH * sizeof(float), st));
     // input parts of every gate, all steps: GX = X W_x^T
-    DNNMG_CUDA_TRY((gemm<false, true>(TP, 3 * H, t->n_in, X, t->ldx, Wx, t->n_in, t->GX, 3 * H, false, st)));
+    DNNMG_CUDA_TRY((prod<false, true>(t, TP, 3 * H, t->n_in, X, t->ldx, Wx, t->n_in, t->GX, 3 * H, false, false, st)));
     for (int s = 0; s < T; ++s) {
         const float *hp = t->hs + (size_t)s * PH;
         const float *GX = t->GX + (size_t)s * P * 3 * H;
         float *z = t->z + (size_t)s * PH, *r = t->r + (size_t)s * PH, *rh = t->rh + (size_t)s * PH;
         float *c = t->c + (size_t)s * PH, *h = t->hs + (size_t)(s + 1) * PH;
-        DNNMG_CUDA_TRY((gemm<false, true>(P, 2 * H, H, hp, H, Uh, H, t->GH, 2 * H, false, st)));
+        DNNMG_CUDA_TRY((prod<false, true>(t, P, 2 * H, H, hp, H, Uh, H, t->GH, 2 * H, false, false, st)));
         k_gates_fwd<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, GX, t->GH, hp, z, r, rh);
         DNNMG_CUDA_TRY(cudaGetLastError());
-        DNNMG_CUDA_TRY((gemm<false, true>(P, H, H, rh, H, Uh + (size_t)2 * H * H, H, t->AH, H, false, st)));
+        DNNMG_CUDA_TRY((prod<false, true>(t, P, H, H, rh, H, Uh + (size_t)2 * H * H, H, t->AH, H, false, false, st)));
         k_cand_fwd<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, GX, t->AH, z, hp, c, h);
         DNNMG_CUDA_TRY(cudaGetLastError());
     }
     // outputs of every step: D = [h_1 .. h_T] W_fc^T
-    DNNMG_CUDA_TRY((gemm<false, true>(TP, t->n_out, H, t->hs + PH, H, Wfc, H, D, t->n_out, false, st)));
+    DNNMG_CUDA_TRY((prod<false, true>(t, TP, t->n_out, H, t->hs + PH, H, Wfc, H, D, t->n_out, false, false, st)));
     return DNNMG_OK;
 }
 
@@ -429,7 +557,7 @@ int dnnmg_gru_seq_backward(dnnmg_trainer_t t, const float *dD, const float *X, c
     const size_t PH = (size_t)P * H;
     const int TP = T * P;
     // gradient reaching each h_t from its own output: dD W_fc, all steps
-    DNNMG_CUDA_TRY((gemm<false, false>(TP, H, n_out, dD, n_out, Wfc, H, t->dHfc, H, false, st)));
+    DNNMG_CUDA_TRY((prod<false, false>(t, TP, H, n_out, dD, n_out, Wfc, H, t->dHfc, H, false, false, st)));
     DNNMG_CUDA_TRY(cudaMemsetAsync(t->carry, 0, PH * sizeof(float), st));
     for (int s = T - 1; s >= 0; --s) {
         const float *hp = t->hs + (size_t)s * PH;
@@ -439,23 +567,20 @@ int dnnmg_gru_seq_backward(dnnmg_trainer_t t, const float *dD, const float *X, c
                                                                 dG, t->dh);
         DNNMG_CUDA_TRY(cudaGetLastError());
         // d(r h_{t-1}) = dA_c U_h
-        DNNMG_CUDA_TRY((gemm<false, false>(P, H, H, dG + 2 * H, 3 * H, Uh + (size_t)2 * H * H, H, t->drh, H, false,
-                                           st)));
+        DNNMG_CUDA_TRY((prod<false, false>(t, P, H, H, dG + 2 * H, 3 * H, Uh + (size_t)2 * H * H, H, t->drh, H,
+                                           false, false, st)));
         k_bwd_reset<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, t->drh, hp, r, z, t->dh, dG, t->carry);
         DNNMG_CUDA_TRY(cudaGetLastError());
         // carry += [dA_z, dA_r] [U_z; U_r]
-        DNNMG_CUDA_TRY((gemm<false, false>(P, H, 2 * H, dG, 3 * H, Uh, H, t->carry, H, true, st)));
+        DNNMG_CUDA_TRY((prod<false, false>(t, P, H, 2 * H, dG, 3 * H, Uh, H, t->carry, H, true, false, st)));
     }
     if (dh0) DNNMG_CUDA_TRY(cudaMemcpyAsync(dh0, t->carry, PH * sizeof(float), cudaMemcpyDeviceToDevice, st));
     // weight gradients: products over all steps and patches
-    DNNMG_CUDA_TRY((gemm_splitk<true, false>(3 * H, n_in, TP, t->dG, 3 * H, X, t->ldx, gWx, n_in, t->splits,
-                                              t->part, st)));
-    DNNMG_CUDA_TRY((gemm_splitk<true, false>(2 * H, H, TP, t->dG, 3 * H, t->hs, H, gUh, H, t->splits, t->part,
-                                              st)));
-    DNNMG_CUDA_TRY((gemm_splitk<true, false>(H, H, TP, t->dG + 2 * H, 3 * H, t->rh, H, gUh + (size_t)2 * H * H, H,
-                                              t->splits, t->part, st)));
-    DNNMG_CUDA_TRY((gemm_splitk<true, false>(n_out, H, TP, dD, n_out, t->hs + PH, H, gWfc, H, t->splits, t->part,
-                                              st)));
+    DNNMG_CUDA_TRY((prod<true, false>(t, 3 * H, n_in, TP, t->dG, 3 * H, X, t->ldx, gWx, n_in, false, true, st)));
+    DNNMG_CUDA_TRY((prod<true, false>(t, 2 * H, H, TP, t->dG, 3 * H, t->hs, H, gUh, H, false, true, st)));
+    DNNMG_CUDA_TRY((prod<true, false>(t, H, H, TP, t->dG + 2 * H, 3 * H, t->rh, H, gUh + (size_t)2 * H * H, H, false,
+                                      true, st)));
+    DNNMG_CUDA_TRY((prod<true, false>(t, n_out, H, TP, dD, n_out, t->hs + PH, H, gWfc, H, false, true, st)));
     return DNNMG_OK;
 }
 

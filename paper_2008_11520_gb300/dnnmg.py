@@ -107,6 +107,9 @@ def _load():
         "dnnmg_pool_stats": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
         "dnnmg_trainer_create": [I, I, I, I, I, I, ctypes.POINTER(P)],
         "dnnmg_trainer_destroy": [P],
+        "dnnmg_trainer_set_precision": [P, I],
+        "dnnmg_trainer_status": [P, ctypes.POINTER(I), I],
+        "dnnmg_gemm_bf16_nt": [I, I, I, P, I, P, I, P, I, I, P, P],
         "dnnmg_gru_seq_forward": [P, P, P, P, P, P, P, P],
         "dnnmg_gru_seq_state": [P, ctypes.POINTER(P)],
         "dnnmg_gru_seq_backward": [P, P, P, P, P, P, P, P, P, P],
@@ -586,15 +589,43 @@ def _view_f32(addr, numel):
 
 
 # ---------------------------------------------------------------- training
+def gemm_bf16_nt(A, B, C, accumulate=False, status=None, stream=None):
+    """C (+)= A B^T on the tensor cores: A [M][K], B [N][K] BF16 (K contiguous,
+    row strides multiples of 8), C [M][N] FP32 (dnnmg_gemm_bf16_nt)."""
+    M, K = A.shape
+    N = B.shape[0]
+    for name, t in (("A", A), ("B", B)):
+        if t.dtype != torch.bfloat16 or not t.is_cuda or t.stride(1) != 1:
+            raise DnnmgError(1, f"{name} must be a CUDA bfloat16 matrix with K contiguous")
+    if C.dtype != torch.float32 or not C.is_cuda or C.stride(1) != 1 or tuple(C.shape) != (M, N):
+        raise DnnmgError(1, "C must be a CUDA float32 [M][N] matrix")
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=C.device)
+    _check(_lib.dnnmg_gemm_bf16_nt(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), C.stride(0),
+                                   1 if accumulate else 0, _ptr(st), _stream(stream)))
+    return st
+
+
 class Trainer:
     """Owning wrapper of a dnnmg_trainer_t: the activations of one window of
-    T steps of P patch rows (FP32), for dnnmg_gru_seq_forward / _backward."""
+    T steps of P patch rows (FP32), for dnnmg_gru_seq_forward / _backward.
+    precision "f32" multiplies in FP32 on the CUDA cores, "bf16" rounds each
+    product's operands to BF16 and multiplies on the tensor cores (FP32
+    accumulation; the FP32 master weights are the caller's)."""
 
-    def __init__(self, n_in, ldx, H, n_out, T, P):
+    def __init__(self, n_in, ldx, H, n_out, T, P, precision="f32"):
         h = ctypes.c_void_p()
         _check(_lib.dnnmg_trainer_create(n_in, ldx, H, n_out, T, P, ctypes.byref(h)))
         self.handle = h
         self.n_in, self.ldx, self.H, self.n_out, self.T, self.P = n_in, ldx, H, n_out, T, P
+        self.precision = precision
+        if precision != "f32":
+            _check(_lib.dnnmg_trainer_set_precision(h, PRECISIONS[precision]))
+
+    def status(self, reset=False):
+        """Device status bits (DNNMG_DEVERR_*) of the tensor-core products."""
+        st = ctypes.c_int(0)
+        _check(_lib.dnnmg_trainer_status(self.handle, ctypes.byref(st), 1 if reset else 0))
+        return st.value
 
     def close(self):
         if self.handle:

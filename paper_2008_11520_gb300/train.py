@@ -73,9 +73,11 @@ class PatchNetTrainer:
     """Weights of the patch network and Adam state; one update per window."""
 
     def __init__(self, n_in, ldx, H, n_out, T, P, seed=0, std=0.1, out_std=None, lr=1e-3, alpha=1e-4,
-                 device="cuda"):
+                 device="cuda", precision="f32"):
         """Initial weights N(0, std^2); the output layer N(0, out_std^2) if given
-        (0: zero, so that the untrained net predicts d = 0)."""
+        (0: zero, so that the untrained net predicts d = 0).  precision: "f32"
+        products on the CUDA cores, or "bf16" products on the tensor cores
+        (FP32 master weights and Adam state either way)."""
         Wx, Uh, Wfc = synth.net_weights(n_in, H, n_out, seed=seed, std=std)
         if out_std is not None:
             Wfc = Wfc * (out_std / std)
@@ -86,7 +88,7 @@ class PatchNetTrainer:
         self.v = [torch.zeros_like(p) for p in self.params]
         self.step_no = 0
         self.lr, self.alpha = lr, alpha
-        self.trainer = dnnmg.Trainer(n_in, ldx, H, n_out, T, P)
+        self.trainer = dnnmg.Trainer(n_in, ldx, H, n_out, T, P, precision=precision)
         self.P = P
 
     def weights(self):
@@ -240,7 +242,7 @@ def e_rel(mesh, weights, spec, steps, H, k=synth.DT, t0=0.0):
     return float(np.mean(with_net)), float(np.mean(without))
 
 
-def bench(P=65536, T=10, n_in=51, H=64, n_out=18, iters=10, warmup=3):
+def bench(P=65536, T=10, n_in=51, H=64, n_out=18, iters=10, warmup=3, precision="f32"):
     """Time one training update (window forward, backward, Adam) at the
     training workload's batch (65 536 patches, T = 10, H = 64, K = 1 net) on
     random inputs (the cost does not depend on the values)."""
@@ -249,7 +251,7 @@ def bench(P=65536, T=10, n_in=51, H=64, n_out=18, iters=10, warmup=3):
     g = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn(T, P, ldx, device="cuda", generator=g)
     Y = 0.1 * torch.randn(T, P, n_out, device="cuda", generator=g)
-    tn = PatchNetTrainer(n_in, ldx, H, n_out, T, P, seed=0, std=0.05, out_std=0.05)
+    tn = PatchNetTrainer(n_in, ldx, H, n_out, T, P, seed=0, std=0.05, out_std=0.05, precision=precision)
     for _ in range(warmup):
         tn.train_window(X, Y)
     torch.cuda.synchronize()
@@ -264,11 +266,12 @@ def bench(P=65536, T=10, n_in=51, H=64, n_out=18, iters=10, warmup=3):
     flops = 3.0 * fwd                                          # + state and weight gradients
     line = {"metric": "training update time", "unit": "ms", "value": ms, "patches": P, "T": T, "H": H,
             "n_in": n_in, "n_out": n_out, "gflop_per_update": flops / 1e9,
-            "tflops": flops / (ms / 1e3) / 1e12, "dtype": "f32", "data": "synthetic"}
+            "tflops": flops / (ms / 1e3) / 1e12, "dtype": precision, "data": "synthetic"}
     print(json.dumps(line))
     return line
 
 
 if __name__ == "__main__":
-    bench()
+    import sys
+    bench(precision=sys.argv[1] if len(sys.argv) > 1 else "f32")
 

@@ -145,3 +145,55 @@ def test_training_lowers_relative_error(dn):
     held = synth.FlowSpec.from_seed(9, ell)
     e_net, e_zero = train.e_rel(mesh, tn.weights(), held, 2 * T, H)
     assert e_net < 0.6 * e_zero, (e_net, e_zero)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (127, 51, 64), (300, 192, 51), (129, 300, 130), (1000, 256, 200),
+                                   (257, 18, 640)])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_gemm_bf16_nt_matches_exact_product(dn, M, N, K, accumulate):
+    # the training products' tensor-core kernel: BF16 operands, FP32
+    # accumulation, against the exact product of the same BF16 values
+    rng = np.random.default_rng(M + N + K)
+    kp = (K + 7) // 8 * 8
+    A = torch.zeros(M, kp, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(N, kp, dtype=torch.bfloat16, device="cuda")
+    A[:, :K] = torch.as_tensor(rng.normal(0, 1, (M, K)), dtype=torch.float32).to(torch.bfloat16).cuda()
+    B[:, :K] = torch.as_tensor(rng.normal(0, 1, (N, K)), dtype=torch.float32).to(torch.bfloat16).cuda()
+    A[:, K:] = float("nan")                    # past K: never read
+    C0 = rng.normal(0, 1, (M, N))
+    C = cu(C0)
+    st = dn.gemm_bf16_nt(A[:, :K], B[:, :K], C, accumulate=accumulate)
+    ref = A[:, :K].double().cpu().numpy() @ B[:, :K].double().cpu().numpy().T
+    if accumulate:
+        ref = ref + C0.astype(np.float32)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert rel_l2(C.cpu().numpy(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("T,P,H", [(1, 70, 32), (3, 129, 64), (2, 5000, 32)])
+def test_window_bf16_products_match_oracle(dn, T, P, H):
+    # the same window with every product's operands rounded to BF16 (tensor
+    # cores, FP32 accumulation): within the BF16 bound of the FP64 oracle, and
+    # repeatable bit for bit; (2, 5000) splits the weight-gradient sums
+    n_in, ldx, n_out = 51, 64, 18
+    (X, h0, Y), (Wx, Uh, Wfc) = problem(T, P, n_in, ldx, H, n_out, seed=11)
+    tr = dn.Trainer(n_in, ldx, H, n_out, T, P, precision="bf16")
+    Xg, h0g, Wg = cu(X), cu(h0), [cu(w) for w in (Wx, Uh, Wfc)]
+    D = torch.empty(T, P, n_out, device="cuda")
+    tr.forward(Xg, h0g, *Wg, D)
+    Do, cache = otrain.seq_forward(X[:, :, :n_in], h0, Wx, Uh, Wfc)
+    dD = otrain.loss_grad_D(Do, Y)
+    g = [torch.empty_like(w) for w in Wg]
+    dh0 = torch.empty(P, H, device="cuda")
+    tr.backward(cu(dD), Xg, Wg[1], Wg[2], *g, dh0=dh0)
+    go = otrain.seq_backward(dD, cache, Wx, Uh, Wfc)
+    g2 = [torch.empty_like(w) for w in Wg]
+    tr.backward(cu(dD), Xg, Wg[1], Wg[2], *g2)
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    assert rel_l2(D.cpu().numpy(), Do) <= 2e-2
+    for a, b, name in zip(g + [dh0], go, ("Wx", "Uh", "Wfc", "h0")):
+        assert rel_l2(a.cpu().numpy(), b) <= 2e-2, name
+    for a, b in zip(g, g2):
+        assert torch.equal(a, b)
