@@ -173,10 +173,104 @@ def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1
     return out
 
 
+def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision="bf16", seed=0, halves=2,
+                     loop_steps=None):
+    """Train the patch network on solved training flows and measure what it gains.
+
+    The training workload of Sec. 5.2 / 6.3: ``paths`` are .npz files written
+    by ``solver.main`` (one channel flow each: the fine-level (L+1) solution
+    as ground truth and the plain coarse-level solution as the network's
+    input, every step of the start-up flow); the flow ``held_out`` (an index
+    into ``paths``) is left out of training.  The other flows' windows
+    (``train.solution_windows``) are laid side by side along the patch axis,
+    their time series cut into ``halves`` consecutive parts that run side by
+    side as well, so one update sees every training flow; truncated BPTT over
+    windows of T steps with the state carried from window to window; Adam
+    with the Tikhonov term; products in ``precision`` ("bf16": the tensor
+    cores, FP32 master weights).  On the held-out flow it reports E_rel(v)
+    (Sec. 6.4, fine velocity DOFs, mean over steps) of v~ + d_bar on the plain
+    coarse solutions (``teacher``) and, over the first ``loop_steps`` steps,
+    of Algorithm 2 end to end (``loop``), each for the trained net and for
+    d = 0 (the plain coarse solution).
+    """
+    from . import train
+
+    flows = [np.load(p) for p in paths]
+
+    def setup(f):
+        nxc, nyc, K = int(f["nxc"]), int(f["nyc"]), int(f["K"])
+        ell = tuple(float(x) for x in f["ellipses"][0])
+        solid = solver.ellipse_mask(nxc, nyc, ell)
+        desc = dnnmg.make_desc(nxc, nyc, K, 1, ellipse=ell, solid=solid, precision="f32", ramp=True,
+                               nu=float(f["nu"]), k=float(f["k"]), u_max=float(f["u_max"]))
+        return dnnmg.Mesh(desc), f["fine"][0], f["coarse"][0]
+
+    Xs, Ys = [], []
+    for i, f in enumerate(flows):
+        if i == held_out:
+            continue
+        mesh, fine, coarse = setup(f)
+        X, Y = train.solution_windows(mesh, list(fine), list(coarse), k=mesh.desc.k)
+        n = (X.shape[0] // (halves * T)) * T          # whole windows per part
+        Xs += [X[j * n:(j + 1) * n] for j in range(halves)]
+        Ys += [Y[j * n:(j + 1) * n] for j in range(halves)]
+        del X, Y
+    Xb, Yb = torch.cat(Xs, dim=1).contiguous(), torch.cat(Ys, dim=1).contiguous()
+    del Xs, Ys
+    I = mesh.info
+    steps, P = Xb.shape[0], Xb.shape[1]
+    tn = train.PatchNetTrainer(I.n_in, I.ldx, H, I.n_out, T, P, seed=seed, std=0.02, out_std=0.0, lr=lr,
+                               precision=precision)
+    losses = []
+    for e in range(epochs):
+        h, tot = None, 0.0
+        for w in range(steps // T):
+            L, h = tn.train_window(Xb[w * T:(w + 1) * T], Yb[w * T:(w + 1) * T], h)
+            tot += float(L)
+        losses.append(tot)
+    torch.cuda.synchronize()
+    status = tn.trainer.status() if hasattr(tn.trainer, "status") else 0
+    del Xb, Yb
+    W = tn.weights()
+    zero = [W[0], W[1], np.zeros_like(W[2])]
+    mesh, fine, coarse = setup(flows[held_out])
+    desc = mesh.desc
+    out = {"updates": tn.step_no, "patches_per_update": P, "window": T, "H": H, "precision": precision,
+           "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "trainer_status": status}
+    for name, weights in (("trained", W), ("zero", zero)):
+        net = dnnmg.Net(*weights, precision="f32")
+        teacher = _held_out_errors(mesh, net, list(coarse), list(fine), desc.k)
+        res = {"teacher": float(np.mean(teacher)), "teacher_last": teacher[-1]}
+        if loop_steps:
+            c = coarse_level(desc)
+            corr = LibraryCorrection(mesh, net, keep_fine=True)
+            loop = []
+
+            def step(x, t, corr=corr, loop=loop):
+                bc = corr(x, t)
+                loop.append(e_rel(corr.v_corr(), fine[len(loop) + 1]))
+                return bc
+
+            solver.dnnmg_run(c, step, loop_steps)
+            res.update(loop=float(np.mean(loop)), loop_last=loop[-1])
+        out[name] = res
+    return out
+
+
 def main():
     import json
+    import sys
     import time
     t0 = time.time()
+    if len(sys.argv) > 1 and sys.argv[1] == "flows":
+        # flows <held-out index> <epochs> <precision> <loop steps> <npz files...>
+        held, epochs, prec, loop_steps = int(sys.argv[2]), int(sys.argv[3]), sys.argv[4], int(sys.argv[5])
+        paths = sys.argv[6:]
+        out = flows_experiment(paths, held, epochs=epochs, precision=prec, loop_steps=loop_steps)
+        print(json.dumps({"workload": "solved training flows (solver.main): " + ", ".join(paths),
+                          "held_out": paths[held], "metric": "E_rel(v), mean over steps", **out,
+                          "seconds": round(time.time() - t0, 1)}))
+        return
     out = accuracy_experiment()
     print(json.dumps({"workload": "32x8 coarse cells, K = 1, nu = 1e-3, start-up flow, 20 steps; "
                                   "trained on inflow peaks 1.2, 1.5, 1.8, evaluated at 1.35",
