@@ -169,16 +169,32 @@ k_gemm_tc(const __grid_constant__ GemmArgs g, const __grid_constant__ CUtensorMa
         tc_after_sync();
         if (ok && !*abort_flag) {
             float *crow = g.C + (long long)blockIdx.z * g.cstride + (long long)gm * g.ldc;
+            const bool vec = g.ldc % 4 == 0 && g.cstride % 4 == 0 && ((uintptr_t)g.C & 15) == 0;
             for (int cb = 0; cb < g.BN / 16; ++cb) {
                 float v[16];
                 if (nk > 0) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + 16 * cb, v);
                 else
                     for (int i = 0; i < 16; ++i) v[i] = 0.f;
-                if (gm < g.M)
+                const int c0 = n0 + 16 * cb;
+                if (gm >= g.M) continue;
+                if (vec && c0 + 16 <= g.N) {
+                    // 16 columns as four 16-byte pieces (row starts on 16 bytes)
+                    float4 *q4 = reinterpret_cast<float4 *>(crow + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float4 x = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                        if (g.accumulate) {
+                            const float4 o = q4[j];
+                            x.x += o.x; x.y += o.y; x.z += o.z; x.w += o.w;
+                        }
+                        q4[j] = x;
+                    }
+                } else {
                     for (int i = 0; i < 16; ++i) {
-                        const int col = n0 + 16 * cb + i;
+                        const int col = c0 + i;
                         if (col < g.N) crow[col] = g.accumulate ? crow[col] + v[i] : v[i];
                     }
+                }
             }
         }
     }

@@ -342,43 +342,152 @@ struct dnnmg_trainer_s {
     size_t part_floats;
     double *red;    // reduction partials [kRedBlocks]
     int splits;
-    // BF16 products (dnnmg_trainer_set_precision): operand scratch, K contiguous
+    // BF16 products (dnnmg_trainer_set_precision)
     int bf16;
-    __nv_bfloat16 *opA, *opB;
-    size_t opA_elems, opB_elems;
     int *d_status;
+    // BF16 copies, each tensor rounded once (offsets into arena, in elements;
+    // row strides kx = kpad(n_in), kh = kpad(H), k2 = kpad(2H), ko = kpad(n_out),
+    // kt = kpad(T P), ks = kpad((T+1) P))
+    __nv_bfloat16 *arena;
+    size_t arena_elems;
+    int kx, kh, k2, ko, kt, ks;
+    size_t o_Wx, o_U, o_Wfc, o_X, o_hs, o_rh;                        // forward
+    size_t o_WfcT, o_UcT, o_UzrT, o_dD, o_dGc, o_dGzr;               // backward, per step
+    size_t o_dGT, o_XT, o_hsT, o_rhT, o_dDT;                         // weight gradients
 };
 
 namespace dnnmg {
 namespace {
 
-// One product of the trainer, C (+)= op(A) op(B) in the layouts of gemm():
-// FP32 on the CUDA cores, or (BF16 mode) its operands rounded to BF16 with K
-// contiguous and multiplied on the tensor cores.  split: K split over
-// t->splits ranges, reduced in a fixed order.
+// One FP32 product of the trainer, C (+)= op(A) op(B) in the layouts of gemm();
+// split: K split over t->splits ranges, reduced in a fixed order.
 template <bool TA, bool TB>
 cudaError_t prod(dnnmg_trainer_s *t, int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C,
                  int ldc, bool accumulate, bool split, cudaStream_t st) {
-    if (!t->bf16)
-        return split ? gemm_splitk<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, t->splits, t->part, st)
-                     : gemm<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, accumulate, st);
-    if (M <= 0 || N <= 0) return cudaSuccess;
-    const int kp = kpad(K);
-    if ((size_t)M * kp > t->opA_elems || (size_t)N * kp > t->opB_elems) return cudaErrorInvalidValue;
-    const dim3 blk(32, 8);
-    k_to_bf16<TA><<<dim3((K + 31) / 32, (M + 31) / 32), blk, 0, st>>>(M, K, A, lda, t->opA, kp);
-    k_to_bf16<!TB><<<dim3((K + 31) / 32, (N + 31) / 32), blk, 0, st>>>(N, K, B, ldb, t->opB, kp);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return split ? gemm_splitk<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, t->splits, t->part, st)
+                 : gemm<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, accumulate, st);
+}
+
+// ---------------------------------------------------------------- BF16 mode
+// Each tensor a product needs is rounded to BF16 once, into the trainer's
+// arena (K contiguous), and the products run on the tensor cores.
+inline __nv_bfloat16 *at(dnnmg_trainer_s *t, size_t off) { return t->arena + off; }
+
+// dst [rows][K] (row stride ldd) = bf16(src) or, with tr, bf16(src^T) for src stored [K][rows].
+cudaError_t to_bf16(int rows, int K, const float *src, int ld, bool tr, __nv_bfloat16 *dst, int ldd,
+                    cudaStream_t st) {
+    if (rows <= 0 || K <= 0) return cudaSuccess;
+    const dim3 grid((K + 31) / 32, (rows + 31) / 32), blk(32, 8);
+    if (tr) k_to_bf16<true><<<grid, blk, 0, st>>>(rows, K, src, ld, dst, ldd);
+    else k_to_bf16<false><<<grid, blk, 0, st>>>(rows, K, src, ld, dst, ldd);
+    return cudaGetLastError();
+}
+
+// C (+)= A B^T on the tensor cores; split: K over t->splits ranges, summed in a fixed order.
+cudaError_t tc(dnnmg_trainer_s *t, int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
+               int ldb, float *C, int ldc, bool accumulate, bool split, cudaStream_t st) {
     if (!split || t->splits <= 1)
-        return launch_gemm_tc(M, N, K, t->opA, kp, t->opB, kp, C, ldc, !split && accumulate, 1, nullptr, t->d_status,
-                              st);
-    e = launch_gemm_tc(M, N, K, t->opA, kp, t->opB, kp, C, ldc, false, t->splits, t->part, t->d_status, st);
+        return launch_gemm_tc(M, N, K, A, lda, B, ldb, C, ldc, accumulate, 1, nullptr, t->d_status, st);
+    cudaError_t e = launch_gemm_tc(M, N, K, A, lda, B, ldb, C, ldc, false, t->splits, t->part, t->d_status, st);
     if (e != cudaSuccess) return e;
     const long long n = (long long)M * N;
     k_reduce_splits<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, N, gemm_tc_splits_used(K, t->splits), t->part, C,
                                                                   ldc, 0);
     return cudaGetLastError();
+}
+
+// The window's forward with BF16 products; h_0 is already in t->hs.
+cudaError_t seq_forward_bf16(dnnmg_trainer_s *t, const float *X, const float *Wx, const float *Uh, const float *Wfc,
+                             float *D, cudaStream_t st) {
+    const int H = t->H, P = t->P, T = t->T, n_in = t->n_in, n_out = t->n_out, TP = T * P;
+    const int kx = t->kx, kh = t->kh;
+    const size_t PH = (size_t)P * H;
+    __nv_bfloat16 *Wxb = at(t, t->o_Wx), *Ub = at(t, t->o_U), *Wfcb = at(t, t->o_Wfc), *Xb = at(t, t->o_X);
+    __nv_bfloat16 *hsb = at(t, t->o_hs), *rhb = at(t, t->o_rh);
+    cudaError_t e;
+#define TRY(x) if ((e = (x)) != cudaSuccess) return e
+    TRY(to_bf16(3 * H, n_in, Wx, n_in, false, Wxb, kx, st));
+    TRY(to_bf16(3 * H, H, Uh, H, false, Ub, kh, st));
+    TRY(to_bf16(n_out, H, Wfc, H, false, Wfcb, kh, st));
+    TRY(to_bf16(TP, n_in, X, t->ldx, false, Xb, kx, st));
+    TRY(to_bf16(P, H, t->hs, H, false, hsb, kh, st));
+    // input parts of every gate, all steps: GX = X W_x^T
+    TRY(tc(t, TP, 3 * H, n_in, Xb, kx, Wxb, kx, t->GX, 3 * H, false, false, st));
+    for (int s = 0; s < T; ++s) {
+        const float *hp = t->hs + (size_t)s * PH;
+        const float *GX = t->GX + (size_t)s * P * 3 * H;
+        float *z = t->z + (size_t)s * PH, *r = t->r + (size_t)s * PH, *rh = t->rh + (size_t)s * PH;
+        float *c = t->c + (size_t)s * PH, *h = t->hs + (size_t)(s + 1) * PH;
+        TRY(tc(t, P, 2 * H, H, hsb + (size_t)s * P * kh, kh, Ub, kh, t->GH, 2 * H, false, false, st));
+        k_gates_fwd<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, GX, t->GH, hp, z, r, rh);
+        TRY(cudaGetLastError());
+        TRY(to_bf16(P, H, rh, H, false, rhb, kh, st));
+        TRY(tc(t, P, H, H, rhb, kh, Ub + (size_t)2 * H * kh, kh, t->AH, H, false, false, st));
+        k_cand_fwd<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, GX, t->AH, z, hp, c, h);
+        TRY(cudaGetLastError());
+        TRY(to_bf16(P, H, h, H, false, hsb + (size_t)(s + 1) * P * kh, kh, st));
+    }
+    // outputs of every step: D = [h_1 .. h_T] W_fc^T
+    TRY(tc(t, TP, n_out, H, hsb + (size_t)P * kh, kh, Wfcb, kh, D, n_out, false, false, st));
+    return cudaSuccess;
+}
+
+// The window's backward with BF16 products (X, Uh, Wfc: the forward's arrays).
+cudaError_t seq_backward_bf16(dnnmg_trainer_s *t, const float *dD, const float *X, const float *Uh, const float *Wfc,
+                              float *gWx, float *gUh, float *gWfc, cudaStream_t st) {
+    const int H = t->H, P = t->P, T = t->T, n_in = t->n_in, n_out = t->n_out, TP = T * P;
+    const int kh = t->kh, k2 = t->k2, ko = t->ko, kt = t->kt, ks = t->ks;
+    const size_t PH = (size_t)P * H;
+    __nv_bfloat16 *WfcT = at(t, t->o_WfcT), *UcT = at(t, t->o_UcT), *UzrT = at(t, t->o_UzrT), *dDb = at(t, t->o_dD);
+    __nv_bfloat16 *dGc = at(t, t->o_dGc), *dGzr = at(t, t->o_dGzr);
+    cudaError_t e;
+    // W_fc^T [H][n_out], U_h^T [H][H], [U_z; U_r]^T [H][2H]
+    TRY(to_bf16(H, n_out, Wfc, H, true, WfcT, ko, st));
+    TRY(to_bf16(H, H, Uh + (size_t)2 * H * H, H, true, UcT, kh, st));
+    TRY(to_bf16(H, 2 * H, Uh, H, true, UzrT, k2, st));
+    TRY(to_bf16(TP, n_out, dD, n_out, false, dDb, ko, st));
+    // gradient reaching each h_t from its own output: dD W_fc, all steps
+    TRY(tc(t, TP, H, n_out, dDb, ko, WfcT, ko, t->dHfc, H, false, false, st));
+    TRY(cudaMemsetAsync(t->carry, 0, PH * sizeof(float), st));
+    for (int s = T - 1; s >= 0; --s) {
+        const float *hp = t->hs + (size_t)s * PH;
+        const float *z = t->z + (size_t)s * PH, *r = t->r + (size_t)s * PH, *c = t->c + (size_t)s * PH;
+        float *dG = t->dG + (size_t)s * P * 3 * H;
+        k_bwd_state<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, t->dHfc + (size_t)s * PH, t->carry, z, c, hp,
+                                                                dG, t->dh);
+        TRY(cudaGetLastError());
+        // d(r h_{t-1}) = dA_c U_h
+        TRY(to_bf16(P, H, dG + 2 * H, 3 * H, false, dGc, kh, st));
+        TRY(tc(t, P, H, H, dGc, kh, UcT, kh, t->drh, H, false, false, st));
+        k_bwd_reset<<<blocks_for((long long)PH), 256, 0, st>>>(P, H, t->drh, hp, r, z, t->dh, dG, t->carry);
+        TRY(cudaGetLastError());
+        // carry += [dA_z, dA_r] [U_z; U_r]
+        TRY(to_bf16(P, 2 * H, dG, 3 * H, false, dGzr, k2, st));
+        TRY(tc(t, P, H, 2 * H, dGzr, k2, UzrT, k2, t->carry, H, true, false, st));
+    }
+    // weight gradients: products over all steps and patches, each operand
+    // transposed (K = T P contiguous) once
+    __nv_bfloat16 *dGT = at(t, t->o_dGT), *XT = at(t, t->o_XT), *hsT = at(t, t->o_hsT), *rhT = at(t, t->o_rhT);
+    __nv_bfloat16 *dDT = at(t, t->o_dDT);
+    TRY(to_bf16(3 * H, TP, t->dG, 3 * H, true, dGT, kt, st));
+    TRY(to_bf16(n_in, TP, X, t->ldx, true, XT, kt, st));
+    TRY(to_bf16(H, TP + P, t->hs, H, true, hsT, ks, st));
+    TRY(to_bf16(H, TP, t->rh, H, true, rhT, kt, st));
+    TRY(to_bf16(n_out, TP, dD, n_out, true, dDT, kt, st));
+    TRY(tc(t, 3 * H, n_in, TP, dGT, kt, XT, kt, gWx, n_in, false, true, st));
+    TRY(tc(t, 2 * H, H, TP, dGT, kt, hsT, ks, gUh, H, false, true, st));
+    TRY(tc(t, H, H, TP, dGT + (size_t)2 * H * kt, kt, rhT, kt, gUh + (size_t)2 * H * H, H, false, true, st));
+    // h_1 .. h_T: columns P.. of hs^T where they start on 16 bytes, else a copy in rhT's place
+    const __nv_bfloat16 *hs1 = hsT + P;
+    int ld1 = ks;
+    if (P % 8) {
+        TRY(to_bf16(H, TP, t->hs + PH, H, true, rhT, kt, st));
+        hs1 = rhT;
+        ld1 = kt;
+    }
+    TRY(tc(t, n_out, H, TP, dDT, kt, hs1, ld1, gWfc, H, false, true, st));
+#undef TRY
+    return cudaSuccess;
 }
 
 void trainer_free(dnnmg_trainer_s *t) {
@@ -387,9 +496,8 @@ void trainer_free(dnnmg_trainer_s *t) {
                      t->part};
     for (float *b : bufs) cudaFree(b);
     cudaFree(t->red);
-    cudaFree(t->opA);
-    cudaFree(t->opB);
     cudaFree(t->d_status);
+    cudaFree(t->arena);
     delete t;
 }
 
@@ -457,31 +565,42 @@ int dnnmg_trainer_set_precision(dnnmg_trainer_t t, int precision) {
         return fail(DNNMG_EINVAL, "trainer precision must be DNNMG_F32 or DNNMG_BF16NET, got %d", precision);
     t->bf16 = 0;
     if (precision == DNNMG_F32) return DNNMG_OK;
-    // the largest operands of the window's products: activations with K up to
-    // max(n_in, 2H, n_out), and the weight gradients' with K = T P
-    const size_t TP = (size_t)t->T * t->P;
-    const size_t kmax = (size_t)kpad(std::max({t->n_in, 2 * t->H, t->n_out}));
-    const size_t ktp = (size_t)kpad((int)TP);
-    const size_t a = std::max({TP * kmax, (size_t)t->P * kmax, (size_t)std::max(3 * t->H, t->n_out) * ktp});
-    const size_t b = std::max({(size_t)std::max({t->n_in, 3 * t->H, t->n_out}) * kmax,
-                               (size_t)std::max(t->n_in, t->H) * ktp});
-    if (a > t->opA_elems || b > t->opB_elems || !t->d_status) {
-        cudaFree(t->opA);
-        cudaFree(t->opB);
-        t->opA = t->opB = nullptr;
-        t->opA_elems = t->opB_elems = 0;
-        if (cudaMalloc(&t->opA, a * sizeof(__nv_bfloat16)) != cudaSuccess ||
-            cudaMalloc(&t->opB, b * sizeof(__nv_bfloat16)) != cudaSuccess ||
+    // BF16 copies of the window's operands, K contiguous, each region 256-byte aligned
+    const int H = t->H, P = t->P, TP = t->T * t->P;
+    t->kx = kpad(t->n_in); t->kh = kpad(H); t->k2 = kpad(2 * H); t->ko = kpad(t->n_out);
+    t->kt = kpad(TP); t->ks = kpad(TP + P);
+    size_t off = 0;
+    auto take = [&](size_t n) { const size_t o = off; off += (n + 127) / 128 * 128; return o; };
+    t->o_Wx = take((size_t)3 * H * t->kx);
+    t->o_U = take((size_t)3 * H * t->kh);
+    t->o_Wfc = take((size_t)t->n_out * t->kh);
+    t->o_X = take((size_t)TP * t->kx);
+    t->o_hs = take((size_t)(TP + P) * t->kh);
+    t->o_rh = take((size_t)P * t->kh);
+    t->o_WfcT = take((size_t)H * t->ko);
+    t->o_UcT = take((size_t)H * t->kh);
+    t->o_UzrT = take((size_t)H * t->k2);
+    t->o_dD = take((size_t)TP * t->ko);
+    t->o_dGc = take((size_t)P * t->kh);
+    t->o_dGzr = take((size_t)P * t->k2);
+    t->o_dGT = take((size_t)3 * H * t->kt);
+    t->o_XT = take((size_t)t->n_in * t->kt);
+    t->o_hsT = take((size_t)H * t->ks);
+    t->o_rhT = take((size_t)H * t->kt);
+    t->o_dDT = take((size_t)t->n_out * t->kt);
+    if (off > t->arena_elems || !t->d_status) {
+        cudaFree(t->arena);
+        t->arena = nullptr;
+        t->arena_elems = 0;
+        if (cudaMalloc(&t->arena, off * sizeof(__nv_bfloat16)) != cudaSuccess ||
             (!t->d_status && cudaMalloc(&t->d_status, sizeof(int)) != cudaSuccess)) {
-            cudaFree(t->opA);
-            cudaFree(t->opB);
-            t->opA = t->opB = nullptr;
+            cudaFree(t->arena);
+            t->arena = nullptr;
             cudaGetLastError();
-            return fail(DNNMG_ENOMEM, "BF16 operand scratch (%zu + %zu values) could not be allocated", a, b);
+            return fail(DNNMG_ENOMEM, "BF16 operand scratch (%zu values) could not be allocated", off);
         }
         DNNMG_CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
-        t->opA_elems = a;
-        t->opB_elems = b;
+        t->arena_elems = off;
     }
     t->bf16 = 1;
     return DNNMG_OK;
@@ -522,6 +641,10 @@ int dnnmg_gru_seq_forward(dnnmg_trainer_t t, const float *X, const float *h0, co
     // h_0 (zero when h0 is NULL)
     if (h0) DNNMG_CUDA_TRY(cudaMemcpyAsync(t->hs, h0, PH * sizeof(float), cudaMemcpyDeviceToDevice, st));
     else DNNMG_CUDA_TRY(cudaMemsetAsync(t->hs, 0, PH * sizeof(float), st));
+    if (t->bf16) {
+        DNNMG_CUDA_TRY(seq_forward_bf16(t, X, Wx, Uh, Wfc, D, st));
+        return DNNMG_OK;
+    }
     // input parts of every gate, all steps: GX = X W_x^T
     DNNMG_CUDA_TRY((prod<false, true>(t, TP, 3 * H, t->n_in, X, t->ldx, Wx, t->n_in, t->GX, 3 * H, false, false, st)));
     for (int s = 0; s < T; ++s) {
@@ -556,6 +679,11 @@ int dnnmg_gru_seq_backward(dnnmg_trainer_t t, const float *dD, const float *X, c
     const int H = t->H, P = t->P, T = t->T, n_out = t->n_out, n_in = t->n_in;
     const size_t PH = (size_t)P * H;
     const int TP = T * P;
+    if (t->bf16) {
+        DNNMG_CUDA_TRY(seq_backward_bf16(t, dD, X, Uh, Wfc, gWx, gUh, gWfc, st));
+        if (dh0) DNNMG_CUDA_TRY(cudaMemcpyAsync(dh0, t->carry, PH * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        return DNNMG_OK;
+    }
     // gradient reaching each h_t from its own output: dD W_fc, all steps
     DNNMG_CUDA_TRY((prod<false, false>(t, TP, H, n_out, dD, n_out, Wfc, H, t->dHfc, H, false, false, st)));
     DNNMG_CUDA_TRY(cudaMemsetAsync(t->carry, 0, PH * sizeof(float), st));
