@@ -434,9 +434,9 @@ int dnnmg_trainer_destroy(dnnmg_trainer_t trainer);
  *   DNNMG_F32      FP32 products on the CUDA cores (the default);
  *   DNNMG_BF16NET  BF16 operands, FP32 accumulation, on the tensor cores
  *                  (tcgen05): each product's operands are rounded to BF16
- *                  (transposed where the product needs it) into scratch the
- *                  trainer allocates here (about T P (3H + max(n_in, H))
- *                  BF16 values).
+ *                  once per tensor (transposed where the product needs it)
+ *                  into scratch the trainer allocates here (about
+ *                  T P (2 n_in + 6 H + 2 n_out) BF16 values).
  * DNNMG_EINVAL for another value, DNNMG_ENOMEM if the scratch cannot be had.
  */
 int dnnmg_trainer_set_precision(dnnmg_trainer_t trainer, int precision);
