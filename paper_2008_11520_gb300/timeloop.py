@@ -14,6 +14,8 @@ with the trained and with a zero network against the plain fine-level solve
 (``accuracy_experiment``).
 """
 
+import time
+
 import numpy as np
 import torch
 
@@ -244,16 +246,65 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
         if loop_steps:
             c = coarse_level(desc)
             corr = LibraryCorrection(mesh, net, keep_fine=True)
-            loop = []
+            loop, stamps = [], [time.perf_counter()]
 
-            def step(x, t, corr=corr, loop=loop):
+            def step(x, t, corr=corr, loop=loop, stamps=stamps):
                 bc = corr(x, t)
+                stamps.append(time.perf_counter())      # one whole step: coarse solve + correction
                 loop.append(e_rel(corr.v_corr(), fine[len(loop) + 1]))
                 return bc
 
             solver.dnnmg_run(c, step, loop_steps)
-            res.update(loop=float(np.mean(loop)), loop_last=loop[-1])
+            res.update(loop=float(np.mean(loop)), loop_last=loop[-1], step_ms=_pcts(np.diff(stamps) * 1e3))
         out[name] = res
+    if loop_steps:
+        out["plain"] = _plain_methods(desc, fine, loop_steps)
+    return out
+
+
+def _pcts(ms):
+    ms = np.asarray(ms, dtype=np.float64)
+    return {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)), "mean": float(ms.mean())}
+
+
+def _plain_methods(desc, fine, steps):
+    """Per-step latency and E_rel(v) of the plain methods on the same flow: the
+    coarse-level solve (level L, host FP64), the fine-level solve (level L+K)
+    on the host, and the GPU plain multigrid fine solve (Newton, GMRES,
+    V-cycles with the Vanka smoother; FP64), against the fine reference."""
+    from . import mg
+    out = {}
+    c, f = coarse_level(desc), fine_level(desc)
+    for name, lev, n in (("coarse_host", c, steps), ("fine_host", f, min(steps, 20))):
+        x, ms = np.zeros((3, lev.N)), []
+        for i in range(1, n + 1):
+            t0 = time.perf_counter()
+            x = lev.advance(x, i * lev.k, "exact")
+            ms.append((time.perf_counter() - t0) * 1e3)
+        if lev is f:
+            err = e_rel(x[:2], fine[n])
+        else:
+            # the coarse solution seen on the fine level: its prolongation with the fine Dirichlet values
+            mesh = dnnmg.Mesh(desc)
+            xf = mesh.fine(3)
+            dnnmg.dnnmg_prolongate(mesh, torch.as_tensor(np.ascontiguousarray(x).reshape(-1)).cuda(), xf, n * lev.k)
+            err = e_rel(mesh.unpack(xf[:2]), fine[n])
+        out[name] = {"steps": n, "step_ms": _pcts(ms), "e_rel_last": err}
+    # GPU plain multigrid on the fine level, levels down to at most 128 x 32 cells
+    levels = 1
+    while (f.nx >> levels) >= 128 and (f.ny >> levels) >= 32 and (f.nx >> (levels - 1)) > 128:
+        levels += 1
+    pm = mg.PlainMG(f.nx, f.ny, levels, f.solid, "f64", lx=f.lx, ly=f.ly, nu=f.nu, k=f.k, alpha0=f.alpha0,
+                    u_max=f.u_max, ramp=f.ramp)
+    x, ms, n = pm.mg.field(0), [], min(steps, 20)
+    for i in range(1, n + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pm.step(x, i * f.k)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+    out["fine_gpu_mg"] = {"steps": n, "levels": levels, "step_ms": _pcts(ms),
+                          "e_rel_last": e_rel(x[:2].double().cpu().numpy(), fine[n])}
     return out
 
 
