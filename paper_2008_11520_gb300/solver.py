@@ -72,6 +72,27 @@ def ellipse_mask(nx, ny, ellipse, lx=LX, ly=LY):
     return ((X - cx) / ax) ** 2 + ((Y - cy) / ay) ** 2 < 1.0
 
 
+def geometry_mask(nx, ny, name, lx=LX, ly=LY):
+    """Solid cells [ny][nx] of the generalization geometries of Sec. 6.7 (cell
+    centroids): "none" (the channel without obstacle), "two" (two elliptic
+    obstacles centred at (0.2, 0.18) and (0.6, 0.24), semi-axes 0.055 x 0.045:
+    the printed axes "1.1" and "0.9" read as 0.11 and 0.09), "L" (the channel
+    with the upper half of its right half solid)."""
+    x = (np.arange(nx) + 0.5) * (lx / nx)
+    y = (np.arange(ny) + 0.5) * (ly / ny)
+    X, Y = np.meshgrid(x, y)
+    if name == "none":
+        return np.zeros((ny, nx), dtype=bool)
+    if name == "two":
+        m = np.zeros((ny, nx), dtype=bool)
+        for cx, cy in ((0.2, 0.18), (0.6, 0.24)):
+            m |= ((X - cx) / 0.055) ** 2 + ((Y - cy) / 0.045) ** 2 < 1.0
+        return m
+    if name == "L":
+        return (X > lx / 2) & (Y > ly / 2)
+    raise ValueError(f"unknown geometry {name!r}")
+
+
 def refine_mask(solid, K):
     """Cell mask of the level K refinements finer: fine cells inherit their parent's flag."""
     r = 2 ** K
@@ -378,6 +399,18 @@ def dnnmg_run(coarse, correct, steps, x0=None, t0=0.0, b0=None, newton="exact"):
     return out
 
 
+def generate_flow(nxc, nyc, K, steps, solid, newton="chord", **params):
+    """One training or evaluation flow on a given coarse mask: the fine-level
+    (L+K) and plain coarse-level solutions of the start-up flow (arrays as in
+    generate_flows, with the mask in place of the ellipse)."""
+    params.setdefault("ramp", True)
+    c = Level(nxc, nyc, solid, **params)
+    f = Level(nxc * 2 ** K, nyc * 2 ** K, refine_mask(solid, K), **params)
+    xf = [np.zeros((3, f.N))] + simulate(f, steps, newton=newton)
+    return {"solid": np.asarray(solid, dtype=bool), "fine": np.array([[x[:2] for x in xf]], dtype=np.float32),
+            "coarse": np.array([simulate(c, steps, newton=newton)]), "k": c.k, "nu": c.nu, "u_max": c.u_max}
+
+
 def generate_flows(nxc, nyc, K, steps, ratios, a_x=0.05, centre=(0.2, 0.2), newton="chord", **params):
     """Training flows of Sec. 5.2: for each axis ratio a_y / a_x of the elliptic
     obstacle, the fine-level (L+K) solution and the plain coarse-level solution
@@ -414,12 +447,16 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--ratios", default="0.5,0.571,0.643,0.714,0.786,0.857,0.929,1.0")
     ap.add_argument("--nu", type=float, default=1e-3)
+    ap.add_argument("--geometry", default="ellipse", help="ellipse (one per ratio), or none, two, L (Sec. 6.7)")
     ap.add_argument("--out", default="flows.npz")
     a = ap.parse_args(argv)
     t0 = time.time()
-    data = generate_flows(a.nxc, a.nyc, a.K, a.steps, [float(r) for r in a.ratios.split(",")], nu=a.nu)
+    if a.geometry == "ellipse":
+        data = generate_flows(a.nxc, a.nyc, a.K, a.steps, [float(r) for r in a.ratios.split(",")], nu=a.nu)
+    else:
+        data = generate_flow(a.nxc, a.nyc, a.K, a.steps, geometry_mask(a.nxc, a.nyc, a.geometry), nu=a.nu)
     np.savez(a.out, nxc=a.nxc, nyc=a.nyc, K=a.K, **data)
-    print(f"{len(data['ellipses'])} flows x {a.steps} steps -> {a.out} ({time.time() - t0:.1f} s)")
+    print(f"{len(data['fine'])} flows x {a.steps} steps -> {a.out} ({time.time() - t0:.1f} s)")
 
 
 if __name__ == "__main__":

@@ -176,7 +176,7 @@ def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1
 
 
 def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision="bf16", seed=0, halves=2,
-                     loop_steps=None):
+                     loop_steps=None, eval_paths=(), eval_loop_steps=None, weights_out=None):
     """Train the patch network on solved training flows and measure what it gains.
 
     The training workload of Sec. 5.2 / 6.3: ``paths`` are .npz files written
@@ -194,6 +194,12 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
     coarse solutions (``teacher``) and, over the first ``loop_steps`` steps,
     of Algorithm 2 end to end (``loop``), each for the trained net and for
     d = 0 (the plain coarse solution).
+
+    ``eval_paths`` are further solved flows on other geometries (written by
+    ``solver.main --geometry``, Sec. 6.7): the net trained on the one-obstacle
+    flows is applied to each unchanged, with the same two errors (the loop over
+    ``eval_loop_steps`` steps).  ``weights_out`` saves the trained weights
+    (.npz, ``W``, ``U``, ``Wfc``).
     """
     from . import train
 
@@ -201,8 +207,11 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
 
     def setup(f):
         nxc, nyc, K = int(f["nxc"]), int(f["nyc"]), int(f["K"])
-        ell = tuple(float(x) for x in f["ellipses"][0])
-        solid = solver.ellipse_mask(nxc, nyc, ell)
+        if "solid" in f:
+            ell, solid = None, np.asarray(f["solid"], dtype=bool)
+        else:
+            ell = tuple(float(x) for x in f["ellipses"][0])
+            solid = solver.ellipse_mask(nxc, nyc, ell)
         desc = dnnmg.make_desc(nxc, nyc, K, 1, ellipse=ell, solid=solid, precision="f32", ramp=True,
                                nu=float(f["nu"]), k=float(f["k"]), u_max=float(f["u_max"]))
         return dnnmg.Mesh(desc), f["fine"][0], f["coarse"][0]
@@ -234,11 +243,32 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
     status = tn.trainer.status() if hasattr(tn.trainer, "status") else 0
     del Xb, Yb
     W = tn.weights()
+    if weights_out:
+        np.savez(weights_out, W=W[0], U=W[1], Wfc=W[2])
     zero = [W[0], W[1], np.zeros_like(W[2])]
-    mesh, fine, coarse = setup(flows[held_out])
-    desc = mesh.desc
     out = {"updates": tn.step_no, "patches_per_update": P, "window": T, "H": H, "precision": precision,
            "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "trainer_status": status}
+    mesh, fine, coarse = setup(flows[held_out])
+    out.update(_evaluate(mesh, fine, coarse, W, zero, loop_steps))
+    if loop_steps:
+        out["plain"] = _plain_methods(mesh.desc, fine, loop_steps)
+    del mesh
+    if eval_paths:
+        out["geometries"] = {}
+    for p in eval_paths:
+        mesh, fine, coarse = setup(np.load(p))
+        out["geometries"][p] = {"solid_cells": int(np.asarray(np.load(p)["solid"]).sum()),
+                                **_evaluate(mesh, fine, coarse, W, zero, eval_loop_steps)}
+        del mesh
+    return out
+
+
+def _evaluate(mesh, fine, coarse, W, zero, loop_steps):
+    """E_rel(v) of the trained net and of d = 0 on one solved flow: with the
+    plain coarse solutions as input (``teacher``, mean over steps and last) and,
+    over ``loop_steps`` steps, of Algorithm 2 end to end (``loop``, with the
+    per-step wall time of coarse solve + correction)."""
+    desc, out = mesh.desc, {}
     for name, weights in (("trained", W), ("zero", zero)):
         net = dnnmg.Net(*weights, precision="f32")
         teacher = _held_out_errors(mesh, net, list(coarse), list(fine), desc.k)
@@ -257,8 +287,6 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
             solver.dnnmg_run(c, step, loop_steps)
             res.update(loop=float(np.mean(loop)), loop_last=loop[-1], step_ms=_pcts(np.diff(stamps) * 1e3))
         out[name] = res
-    if loop_steps:
-        out["plain"] = _plain_methods(desc, fine, loop_steps)
     return out
 
 
@@ -315,9 +343,18 @@ def main():
     t0 = time.time()
     if len(sys.argv) > 1 and sys.argv[1] == "flows":
         # flows <held-out index> <epochs> <precision> <loop steps> <npz files...>
+        #       [--eval <loop steps> <npz files...>] [--weights-out <npz>]
         held, epochs, prec, loop_steps = int(sys.argv[2]), int(sys.argv[3]), sys.argv[4], int(sys.argv[5])
-        paths = sys.argv[6:]
-        out = flows_experiment(paths, held, epochs=epochs, precision=prec, loop_steps=loop_steps)
+        rest, weights_out, eval_paths, eval_steps = sys.argv[6:], None, [], None
+        if "--weights-out" in rest:
+            i = rest.index("--weights-out")
+            weights_out, rest = rest[i + 1], rest[:i] + rest[i + 2:]
+        if "--eval" in rest:
+            i = rest.index("--eval")
+            eval_steps, eval_paths, rest = int(rest[i + 1]), rest[i + 2:], rest[:i]
+        paths = rest
+        out = flows_experiment(paths, held, epochs=epochs, precision=prec, loop_steps=loop_steps,
+                               eval_paths=eval_paths, eval_loop_steps=eval_steps, weights_out=weights_out)
         print(json.dumps({"workload": "solved training flows (solver.main): " + ", ".join(paths),
                           "held_out": paths[held], "metric": "E_rel(v), mean over steps", **out,
                           "seconds": round(time.time() - t0, 1)}))

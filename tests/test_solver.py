@@ -260,3 +260,53 @@ def test_operator_equals_oracle_on_a_single_level_mask():
     for c in range(3):
         scale = np.abs(A[c][free[c]]).max()
         np.testing.assert_allclose(-A[c][free[c]], r[c][free[c]], rtol=0, atol=1e-12 * scale)
+
+
+def test_geometry_flow_is_the_level_solution(tmp_path):
+    # Sec. 6.7 geometries: the stored mask is the named one and the stored
+    # solutions are the two levels' runs on it
+    out = tmp_path / "two.npz"
+    solver.main(["--nxc", "32", "--nyc", "8", "--K", "1", "--steps", "3", "--geometry", "two", "--out", str(out)])
+    z = np.load(out)
+    solid = solver.geometry_mask(32, 8, "two")
+    assert solid.sum() > 0 and (z["solid"] == solid).all()
+    assert z["fine"].shape == (1, 4, 2, 65 * 17) and z["coarse"].shape == (1, 3, 3, 33 * 9)
+    c = solver.Level(32, 8, solid, ramp=True)
+    f = solver.Level(64, 16, solver.refine_mask(solid, 1), ramp=True)
+    for a, b in zip(z["coarse"][0], solver.simulate(c, 3)):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-10 * np.abs(b).max())
+    for a, b in zip(z["fine"][0][1:], solver.simulate(f, 3)):
+        np.testing.assert_allclose(a, b[:2], rtol=0, atol=1e-6 * np.abs(b[:2]).max())
+
+
+def test_geometry_masks():
+    nx, ny = 64, 16
+    xc = (np.arange(nx) + 0.5) * (2.2 / nx)
+    yc = (np.arange(ny) + 0.5) * (0.41 / ny)
+    assert not solver.geometry_mask(nx, ny, "none").any()
+    L = solver.geometry_mask(nx, ny, "L")
+    # the upper half of the right half, every cell of it, nothing else
+    assert L.sum() == (nx // 2) * (ny // 2) and L[ny // 2:, nx // 2:].all()
+    two = solver.geometry_mask(nx, ny, "two")
+    j, i = np.nonzero(two)
+    # two separate obstacles, each around its centre and inside its bounding box
+    left = xc[i] < 0.4
+    for sel, (cx, cy) in ((left, (0.2, 0.18)), (~left, (0.6, 0.24))):
+        assert sel.any()
+        assert (np.abs(xc[i[sel]] - cx) < 0.055).all() and (np.abs(yc[j[sel]] - cy) < 0.045).all()
+    with pytest.raises(ValueError):
+        solver.geometry_mask(nx, ny, "circle")
+
+
+def test_channel_without_obstacle_is_mirror_symmetric():
+    # the empty channel and its parabolic inflow are symmetric about y = H/2, so
+    # u is even and v odd under the mirror, on both levels and at every step
+    z = solver.generate_flow(16, 8, 1, 4, solver.geometry_mask(16, 8, "none"))
+    for sol, (nx, ny) in ((z["coarse"][0][1:], (16, 8)), (z["fine"][0][1:], (32, 16))):
+        for x in sol:
+            u = np.asarray(x[0], dtype=np.float64).reshape(ny + 1, nx + 1)
+            v = np.asarray(x[1], dtype=np.float64).reshape(ny + 1, nx + 1)
+            scale = np.abs(u).max()
+            assert scale > 1e-3
+            np.testing.assert_allclose(u, u[::-1], rtol=0, atol=1e-5 * scale)
+            np.testing.assert_allclose(v, -v[::-1], rtol=0, atol=1e-5 * scale)

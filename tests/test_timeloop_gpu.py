@@ -79,3 +79,34 @@ def test_trained_network_lowers_error(tl):
     tr, zr = out["trained"], out["zero"]
     assert tr["teacher"] < 0.75 * zr["teacher"], out
     assert tr["loop"] < 0.85 * zr["loop"], out
+
+
+def test_flows_experiment_on_other_geometries(tl, tmp_path):
+    # the training workload's driver end to end on tiny flows: train on one
+    # ellipse flow, evaluate on the held-out one and, unchanged, on the
+    # two-obstacle, empty and L-shaped channels of Sec. 6.7
+    _, timeloop = tl
+    paths = []
+    for q in ("0.6", "1.0"):
+        p = str(tmp_path / f"e{q}.npz")
+        solver.main(["--nxc", "32", "--nyc", "8", "--steps", "20", "--ratios", q, "--out", p])
+        paths.append(p)
+    geo = []
+    for g in ("two", "none", "L"):
+        p = str(tmp_path / f"{g}.npz")
+        solver.main(["--nxc", "32", "--nyc", "8", "--steps", "20", "--geometry", g, "--out", p])
+        geo.append(p)
+    wpath = str(tmp_path / "w.npz")
+    out = timeloop.flows_experiment(paths, 1, H=16, epochs=3, precision="f32", loop_steps=0,
+                                    eval_paths=geo, eval_loop_steps=3, weights_out=wpath)
+    assert out["trainer_status"] == 0 and out["updates"] >= 3
+    assert np.isfinite(out["loss_last_epoch"]) and out["loss_last_epoch"] < out["loss_first_epoch"]
+    w = np.load(wpath)
+    assert w["W"].shape[0] == 48 and w["U"].shape == (48, 16) and w["Wfc"].shape[1] == 16
+    for p, g in zip(geo, ("two", "none", "L")):
+        r = out["geometries"][p]
+        assert r["solid_cells"] == int(solver.geometry_mask(32, 8, g).sum())
+        for name in ("trained", "zero"):
+            assert np.isfinite([r[name]["teacher"], r[name]["loop"], r[name]["loop_last"]]).all()
+            assert r[name]["step_ms"]["p50"] > 0
+    assert "loop" not in out["trained"] and "plain" not in out
