@@ -19,6 +19,8 @@ step by step, in float64, written for a reader checking it against the paper:
                    projection stabilisation (Eq. nonlinearshort, Eq. 4cranknicholson3).
 * ``features``  -- per-patch network inputs (Sec. 5.2 "Neural network inputs").
 * ``gru``       -- GRU cell and fully connected output layer (Eq. gru, Sec. 6.2).
+* ``head``      -- convolutional head of the K = 1 network and its fold into the
+                   output layer (Sec. 6.2 parameter counts).
 * ``average``   -- averaging of duplicate predictions on shared nodes (Sec. 5.2).
 * ``step``      -- one DNN-MG correction step of Algorithm 2.
 
@@ -28,4 +30,4 @@ check it against closed forms, invariants, hand-computed values and brute force
 its parts and the zero-network reduction.
 """
 
-from . import mesh, transfer, fem, features, gru, average, step  # noqa: F401
+from . import mesh, transfer, fem, features, gru, head, average, step  # noqa: F401

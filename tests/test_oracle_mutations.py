@@ -9,9 +9,10 @@ import numpy as np
 import pytest
 
 import test_oracle_assembly as assembly
+import test_oracle_head as hpins
 import test_oracle_pins as pins
 import test_train_oracle as tpins
-from oracle import fem, gru, transfer
+from oracle import fem, gru, head, transfer
 from oracle import train as otrain
 
 
@@ -45,6 +46,13 @@ def _lps_pins():
 def _train_pins():
     return [lambda a=a: tpins.test_bptt_gradient_matches_finite_differences(a) for a in (0.0, 1e-4)] + \
            [tpins.test_gradient_of_a_single_step_by_hand, tpins.test_adam_closed_forms]
+
+
+def _head_pins():
+    return [lambda n=n: hpins.test_spatial_block_is_library_correlation_then_convolution(n) for n in hpins.N_OUTS] + \
+           [lambda n=n: hpins.test_vertex_block_is_library_correlation_then_convolution(n) for n in hpins.N_OUTS] + \
+           [lambda n=n: hpins.test_blocks_are_symmetric_positive_semidefinite(n) for n in hpins.N_OUTS] + \
+           [lambda n=n: hpins.test_fold_gradient_matches_central_differences(n) for n in hpins.N_OUTS]
 
 
 def _mutants():
@@ -112,7 +120,27 @@ def _mutants():
         v = b2 * v + (1.0 - b2) * g * g
         return p - lr * m / (np.sqrt(v) + eps), m, v
 
+    o_fold_bw, o_vertex = head.fold_backward, head.vertex_block
+
+    def fold_backward_one_product(theta, Wfc, G):
+        # drops the (C_f x)[p] q[p + t] half of each filter's gradient
+        dth, dW = o_fold_bw(theta, Wfc, G)
+        dth = dth.copy()
+        dth[:head.NF * (head.KS ** 2 + head.KV)] *= 0.5
+        return dth, dW
+
+    def vertex_without_interleaving(y, kv):
+        # the components one after the other instead of vertex by vertex
+        y = np.asarray(y, dtype=np.float64)
+        acc = np.zeros_like(y)
+        for f in range(head.NF):
+            acc += head.corr1d_t(head.corr1d(y, kv[f]), kv[f])
+        return acc
+
     return {
+        "transposed head layer not the adjoint": (head, "corr2d_t", head.corr2d, _head_pins),
+        "vertex block without interleaving": (head, "vertex_block", vertex_without_interleaving, _head_pins),
+        "head filter gradient halved": (head, "fold_backward", fold_backward_one_product, _head_pins),
         "loss gradient without its factor 2": (otrain, "loss_grad_D", lambda D, Y: 0.5 * o_grad_D(D, Y),
                                                _train_pins),
         "reset-gate recurrent gradient dropped": (otrain, "seq_backward", backward_without_reset_recurrence,
