@@ -140,6 +140,38 @@ int dnnmg_net_create(int n_in, int hidden, int n_out, const double *Wx, const do
 int dnnmg_net_destroy(dnnmg_net_t net);
 
 /*
+ * Convolutional head of the patch network (Sec. 6.2: the K = 1 net's two
+ * convolutional blocks of 36 parameters and its last layer of N_out).  On a
+ * prediction row y [n_out] (u on the n x n patch nodes, x fastest, then v;
+ * n_out = 2 n^2, n odd, 3 .. 9):
+ *   d = w * (B_s y + B_v y),   B = sum_f C_f^T C_f over 4 filters,
+ * C_f a zero-padded size-preserving correlation, C_f^T its adjoint (the
+ * transposed layer reusing the first layer's weights); B_s over each
+ * component's n x n nodes with 3 x 3 filters, B_v over the sequence
+ * (u_0, v_0, u_1, v_1, ...) with length-9 filters.  The head has no
+ * nonlinearity, so it folds into the output layer: W_eff [n_out][H], column j
+ * the head applied to column j of W_fc.
+ * theta [72 + n_out]: k_s [4][3][3] (row offset -1..1 in y, column offset
+ * -1..1 in x), k_v [4][9] (offset -4..4), w [n_out].
+ *
+ * dnnmg_head_params: the length of theta for n_out, or 0 if unsupported.
+ * dnnmg_net_create_head: dnnmg_net_create with W_eff (folded on the device in
+ *   FP64); host arrays, synchronous.  DNNMG_EUNSUPPORTED for other n_out.
+ * dnnmg_head_fold: W_eff from theta and W_fc, device FP32, asynchronous.
+ * dnnmg_head_backward: the gradients of sum(G * W_eff) with respect to theta
+ *   (dtheta [72 + n_out]) and W_fc (dWfc [n_out][H]), written; work is device
+ *   scratch of H (72 + n_out) floats.  Device FP32, asynchronous, deterministic
+ *   (fixed summation order).
+ */
+int dnnmg_head_params(int n_out);
+int dnnmg_net_create_head(int n_in, int hidden, int n_out, const double *Wx, const double *Uh,
+                          const double *Wfc, const double *theta, int precision, dnnmg_net_t *out);
+int dnnmg_head_fold(int n_out, int hidden, const float *theta, const float *Wfc, float *Weff,
+                    cudaStream_t stream);
+int dnnmg_head_backward(int n_out, int hidden, const float *theta, const float *Wfc, const float *G,
+                        float *dtheta, float *dWfc, float *work, cudaStream_t stream);
+
+/*
  * S1, the prolongation of Algorithm 2: xf = P xc on (u, v, p) by bilinear interpolation
  * from level L to L+K, then the fine velocity Dirichlet values at time t.
  *   xc [3][Nc] double (in), xf [3][plane] real (out).

@@ -76,6 +76,10 @@ def _load():
         "dnnmg_mesh_maps": [P, P, P, P, P],
         "dnnmg_net_create": [I, I, I, P, P, P, I, ctypes.POINTER(P)],
         "dnnmg_net_destroy": [P],
+        "dnnmg_head_params": [I],
+        "dnnmg_net_create_head": [I, I, I, P, P, P, P, I, ctypes.POINTER(P)],
+        "dnnmg_head_fold": [I, I, P, P, P, P],
+        "dnnmg_head_backward": [I, I, P, P, P, P, P, P, P],
         "dnnmg_prolongate": [P, P, P, D, P],
         "dnnmg_patch_features": [P, P, P, D, P, P, P, P],
         "dnnmg_gru_step": [P, P, P, P, I, P],
@@ -269,9 +273,11 @@ class Mesh:
 
 
 class Net:
-    """Owning wrapper of a dnnmg_net_t (weights uploaded in the given precision)."""
+    """Owning wrapper of a dnnmg_net_t (weights uploaded in the given precision).
+    ``head``: the parameters theta of the convolutional head (Sec. 6.2), folded
+    into the output layer on the device (dnnmg_net_create_head)."""
 
-    def __init__(self, Wx, Uh, Wfc, precision="f64"):
+    def __init__(self, Wx, Uh, Wfc, precision="f64", head=None):
         Wx, Uh, Wfc = (np.ascontiguousarray(a, dtype=np.float64) for a in (Wx, Uh, Wfc))
         G, n_in = Wx.shape
         H = Uh.shape[1]
@@ -280,8 +286,15 @@ class Net:
             raise ValueError("weight shapes must be Wx [3H][n_in], Uh [3H][H], Wfc [n_out][H]")
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         h = ctypes.c_void_p()
-        _check(_lib.dnnmg_net_create(n_in, H, n_out, Wx.ctypes.data, Uh.ctypes.data, Wfc.ctypes.data,
-                                     self.precision, ctypes.byref(h)))
+        if head is None:
+            _check(_lib.dnnmg_net_create(n_in, H, n_out, Wx.ctypes.data, Uh.ctypes.data, Wfc.ctypes.data,
+                                         self.precision, ctypes.byref(h)))
+        else:
+            head = np.ascontiguousarray(head, dtype=np.float64)
+            if head.shape != (head_params(n_out),):
+                raise ValueError(f"head must hold {head_params(n_out)} parameters for n_out = {n_out}")
+            _check(_lib.dnnmg_net_create_head(n_in, H, n_out, Wx.ctypes.data, Uh.ctypes.data, Wfc.ctypes.data,
+                                              head.ctypes.data, self.precision, ctypes.byref(h)))
         self.handle = h
         self.n_in, self.H, self.n_out = n_in, H, n_out
         self.real = _REAL[self.precision]
@@ -586,6 +599,39 @@ def _view_f32(addr, numel):
         __cuda_array_interface__ = {"shape": (numel,), "typestr": "<f4", "data": (addr, False), "version": 2,
                                     "strides": None}
     return torch.as_tensor(_Holder(), device="cuda")
+
+
+# ---------------------------------------------------------------- convolutional head
+def head_params(n_out):
+    """Length of the head's parameter vector for n_out outputs (0: unsupported)."""
+    return int(_lib.dnnmg_head_params(int(n_out)))
+
+
+def head_fold(theta, Wfc, Weff=None, stream=None):
+    """W_eff [n_out][H] = the head applied to each column of W_fc (dnnmg_head_fold; FP32 device)."""
+    n_out, H = Wfc.shape
+    if not head_params(n_out):
+        raise DnnmgError(3, f"no head for n_out = {n_out}: it must be 2 n^2, n odd, 3..9")
+    _need(theta, torch.float32, head_params(n_out), "theta")
+    _need(Wfc, torch.float32, n_out * H, "Wfc")
+    Weff = torch.empty_like(Wfc) if Weff is None else Weff
+    _need(Weff, torch.float32, n_out * H, "Weff")
+    _check(_lib.dnnmg_head_fold(n_out, H, _ptr(theta), _ptr(Wfc), _ptr(Weff), _stream(stream)))
+    return Weff
+
+
+def head_backward(theta, Wfc, G, stream=None):
+    """(d theta, d W_fc) of sum(G * W_eff) (dnnmg_head_backward; FP32 device)."""
+    n_out, H = Wfc.shape
+    nt = head_params(n_out)
+    _need(theta, torch.float32, nt, "theta")
+    _need(Wfc, torch.float32, n_out * H, "Wfc")
+    _need(G, torch.float32, n_out * H, "G")
+    dtheta, dW = torch.empty_like(theta), torch.empty_like(Wfc)
+    work = torch.empty(H * nt, dtype=torch.float32, device=Wfc.device)
+    _check(_lib.dnnmg_head_backward(n_out, H, _ptr(theta), _ptr(Wfc), _ptr(G), _ptr(dtheta), _ptr(dW), _ptr(work),
+                                    _stream(stream)))
+    return dtheta, dW
 
 
 # ---------------------------------------------------------------- training

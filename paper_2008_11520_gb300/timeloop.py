@@ -116,7 +116,7 @@ def _held_out_errors(mesh, net, coarse_states, fine_states, k):
 
 def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1e-3,
                         u_train=(1.2, 1.5, 1.8), u_held=1.35, steps=20, T=10, H=32,
-                        epochs=300, lr=1e-3, seed=0):
+                        epochs=300, lr=1e-3, seed=0, head=False):
     """Train the patch network on solved flows and measure what it gains.
 
     The paper's accuracy study (Sec. 6.3-6.4) in small: fine-level (L+K)
@@ -131,6 +131,9 @@ def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1
     * ``loop``: Algorithm 2 end to end (host coarse solve, library correction
       step, its right-hand side fed back), trained net vs zero net, which
       reduces the method to the plain coarse solve.
+
+    ``head``: the net carries the convolutional head of Sec. 6.2 (the K = 1
+    net of the paper: GRU, output layer, head).
     """
     from . import train
 
@@ -148,7 +151,8 @@ def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1
         mesh, _, xf, xc = setup(u)
         data.append(train.solution_windows(mesh, xf, xc, k=mesh.desc.k))
     I = mesh.info
-    tn = train.PatchNetTrainer(I.n_in, I.ldx, H, I.n_out, T, I.P, seed=seed, std=0.02, out_std=0.0, lr=lr)
+    tn = train.PatchNetTrainer(I.n_in, I.ldx, H, I.n_out, T, I.P, seed=seed, std=0.02, out_std=0.0, lr=lr,
+                               head=head)
     for _ in range(epochs):
         for X, Y in data:
             h = None
@@ -157,9 +161,9 @@ def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1
     W = tn.weights()
     zero = [W[0], W[1], np.zeros_like(W[2])]
     mesh, coarse, xf, xc = setup(u_held)
-    out = {"updates": tn.step_no}
+    out = {"updates": tn.step_no, "head": bool(head), "params": int(sum(w.size for w in W))}
     for name, weights in (("trained", W), ("zero", zero)):
-        net = dnnmg.Net(*weights, precision="f32")
+        net = dnnmg.Net(*weights[:3], precision="f32", head=weights[3] if len(weights) > 3 else None)
         teacher = _held_out_errors(mesh, net, xc, xf, coarse.k)
         corr = LibraryCorrection(mesh, net, keep_fine=True)
         loop = []
@@ -176,7 +180,7 @@ def accuracy_experiment(nxc=32, nyc=8, K=1, ellipse=(0.2, 0.2, 0.05, 0.04), nu=1
 
 
 def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision="bf16", seed=0, halves=2,
-                     loop_steps=None, eval_paths=(), eval_loop_steps=None, weights_out=None):
+                     loop_steps=None, eval_paths=(), eval_loop_steps=None, weights_out=None, head=False):
     """Train the patch network on solved training flows and measure what it gains.
 
     The training workload of Sec. 5.2 / 6.3: ``paths`` are .npz files written
@@ -199,7 +203,8 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
     ``solver.main --geometry``, Sec. 6.7): the net trained on the one-obstacle
     flows is applied to each unchanged, with the same two errors (the loop over
     ``eval_loop_steps`` steps).  ``weights_out`` saves the trained weights
-    (.npz, ``W``, ``U``, ``Wfc``).
+    (.npz, ``W``, ``U``, ``Wfc`` and ``theta``).  ``head``: train the
+    convolutional head of Sec. 6.2 with the net (``train.HeadFold``).
     """
     from . import train
 
@@ -231,7 +236,7 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
     I = mesh.info
     steps, P = Xb.shape[0], Xb.shape[1]
     tn = train.PatchNetTrainer(I.n_in, I.ldx, H, I.n_out, T, P, seed=seed, std=0.02, out_std=0.0, lr=lr,
-                               precision=precision)
+                               precision=precision, head=head)
     losses = []
     for e in range(epochs):
         h, tot = None, 0.0
@@ -244,9 +249,10 @@ def flows_experiment(paths, held_out, H=64, T=10, epochs=200, lr=1e-3, precision
     del Xb, Yb
     W = tn.weights()
     if weights_out:
-        np.savez(weights_out, W=W[0], U=W[1], Wfc=W[2])
+        np.savez(weights_out, W=W[0], U=W[1], Wfc=W[2], **({"theta": W[3]} if head else {}))
     zero = [W[0], W[1], np.zeros_like(W[2])]
     out = {"updates": tn.step_no, "patches_per_update": P, "window": T, "H": H, "precision": precision,
+           "head": bool(head), "params": int(sum(w.size for w in W)),
            "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "trainer_status": status}
     mesh, fine, coarse = setup(flows[held_out])
     out.update(_evaluate(mesh, fine, coarse, W, zero, loop_steps))
@@ -270,7 +276,7 @@ def _evaluate(mesh, fine, coarse, W, zero, loop_steps):
     per-step wall time of coarse solve + correction)."""
     desc, out = mesh.desc, {}
     for name, weights in (("trained", W), ("zero", zero)):
-        net = dnnmg.Net(*weights, precision="f32")
+        net = dnnmg.Net(*weights[:3], precision="f32", head=weights[3] if len(weights) > 3 else None)
         teacher = _held_out_errors(mesh, net, list(coarse), list(fine), desc.k)
         res = {"teacher": float(np.mean(teacher)), "teacher_last": teacher[-1]}
         if loop_steps:
@@ -343,9 +349,11 @@ def main():
     t0 = time.time()
     if len(sys.argv) > 1 and sys.argv[1] == "flows":
         # flows <held-out index> <epochs> <precision> <loop steps> <npz files...>
-        #       [--eval <loop steps> <npz files...>] [--weights-out <npz>]
+        #       [--eval <loop steps> <npz files...>] [--weights-out <npz>] [--head]
         held, epochs, prec, loop_steps = int(sys.argv[2]), int(sys.argv[3]), sys.argv[4], int(sys.argv[5])
         rest, weights_out, eval_paths, eval_steps = sys.argv[6:], None, [], None
+        use_head = "--head" in rest
+        rest = [a for a in rest if a != "--head"]
         if "--weights-out" in rest:
             i = rest.index("--weights-out")
             weights_out, rest = rest[i + 1], rest[:i] + rest[i + 2:]
@@ -354,12 +362,14 @@ def main():
             eval_steps, eval_paths, rest = int(rest[i + 1]), rest[i + 2:], rest[:i]
         paths = rest
         out = flows_experiment(paths, held, epochs=epochs, precision=prec, loop_steps=loop_steps,
-                               eval_paths=eval_paths, eval_loop_steps=eval_steps, weights_out=weights_out)
+                               eval_paths=eval_paths, eval_loop_steps=eval_steps, weights_out=weights_out,
+                               head=use_head)
         print(json.dumps({"workload": "solved training flows (solver.main): " + ", ".join(paths),
                           "held_out": paths[held], "metric": "E_rel(v), mean over steps", **out,
                           "seconds": round(time.time() - t0, 1)}))
         return
-    out = accuracy_experiment()
+    use_head = "--head" in sys.argv[1:]
+    out = accuracy_experiment(head=use_head)
     print(json.dumps({"workload": "32x8 coarse cells, K = 1, nu = 1e-3, start-up flow, 20 steps; "
                                   "trained on inflow peaks 1.2, 1.5, 1.8, evaluated at 1.35",
                       "metric": "E_rel(v), mean over steps", **out,

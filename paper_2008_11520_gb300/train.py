@@ -5,8 +5,11 @@
   gradient by truncated backpropagation through time).
 * ``L2Loss`` -- the loss of Sec. 6.3 (sum over steps of the mean over patches
   of |d - y|^2) as an autograd function on the library's loss kernel.
+* ``HeadFold`` -- the convolutional head of Sec. 6.2 folded into the output
+  layer (W_eff = head applied to each column of W_fc) as an autograd function
+  on the library's fold and fold-gradient kernels.
 * ``PatchNetTrainer`` -- FP32 weights, Adam (Sec. 6.3) with the Tikhonov
-  term alpha = 1e-4, one update per window.
+  term alpha = 1e-4, one update per window; optionally with the head.
 * ``flow_windows`` -- training windows from synthetic flows, built with the
   library's own S1 and S2+S3 kernels: features of x~ = P x_c(t_n) with the
   right-hand side of the previous reference velocity, and targets
@@ -53,6 +56,36 @@ class GruWindow(torch.autograd.Function):
         return None, dh0, gWx, gUh, gWfc, None
 
 
+class HeadFold(torch.autograd.Function):
+    """W_eff [n_out][H]: the convolutional head (Sec. 6.2) applied to each column
+    of W_fc; the head is linear, so the window runs the folded output layer."""
+
+    @staticmethod
+    def forward(ctx, theta, Wfc):
+        ctx.save_for_backward(theta, Wfc)
+        return dnnmg.head_fold(theta, Wfc)
+
+    @staticmethod
+    def backward(ctx, G):
+        theta, Wfc = ctx.saved_tensors
+        return dnnmg.head_backward(theta, Wfc, G.contiguous())
+
+
+def head_init(n_out, seed, std=0.05):
+    """Head parameters that start near the identity (the paper gives no
+    initialisation for the head): filter 0 of both blocks a centred unit tap,
+    filters 1..3 N(0, std^2) (a filter at zero would get no gradient: its
+    block is quadratic in it), w = 1/2, so d = y + O(std^2) y."""
+    rng = np.random.default_rng(seed + 1)
+    nt = dnnmg.head_params(n_out)
+    ks = np.concatenate([np.zeros((1, 9)), rng.normal(0.0, std, (3, 9))])
+    kv = np.concatenate([np.zeros((1, 9)), rng.normal(0.0, std, (3, 9))])
+    ks[0, 4] = kv[0, 4] = 1.0
+    theta = np.concatenate([ks.ravel(), kv.ravel(), np.full(n_out, 0.5)])
+    assert theta.shape == (nt,)
+    return theta
+
+
 class L2Loss(torch.autograd.Function):
     """sum over steps of the mean over the P patches of |D - Y|^2 (Sec. 6.3)."""
 
@@ -73,15 +106,19 @@ class PatchNetTrainer:
     """Weights of the patch network and Adam state; one update per window."""
 
     def __init__(self, n_in, ldx, H, n_out, T, P, seed=0, std=0.1, out_std=None, lr=1e-3, alpha=1e-4,
-                 device="cuda", precision="f32"):
+                 device="cuda", precision="f32", head=False):
         """Initial weights N(0, std^2); the output layer N(0, out_std^2) if given
         (0: zero, so that the untrained net predicts d = 0).  precision: "f32"
         products on the CUDA cores, or "bf16" products on the tensor cores
-        (FP32 master weights and Adam state either way)."""
+        (FP32 master weights and Adam state either way).  head: train the
+        convolutional head of Sec. 6.2 too (``head_init``; its parameters are
+        the fourth entry of ``params``)."""
         Wx, Uh, Wfc = synth.net_weights(n_in, H, n_out, seed=seed, std=std)
         if out_std is not None:
             Wfc = Wfc * (out_std / std)
-        self.params = [torch.tensor(W, dtype=torch.float32, device=device).contiguous() for W in (Wx, Uh, Wfc)]
+        W = [Wx, Uh, Wfc] + ([head_init(n_out, seed)] if head else [])
+        self.params = [torch.tensor(w, dtype=torch.float32, device=device).contiguous() for w in W]
+        self.head = head
         for p in self.params:
             p.requires_grad_(True)
         self.m = [torch.zeros_like(p) for p in self.params]
@@ -92,11 +129,20 @@ class PatchNetTrainer:
         self.P = P
 
     def weights(self):
+        """[Wx, Uh, Wfc] (and theta with the head) as float64 host arrays."""
         return [p.detach().double().cpu().numpy() for p in self.params]
+
+    def net(self, precision="f32"):
+        """An inference net (dnnmg.Net) with the current weights."""
+        W = self.weights()
+        return dnnmg.Net(W[0], W[1], W[2], precision=precision, head=W[3] if self.head else None)
 
     def loss(self, X, Y, h0=None):
         """Loss of the window (data term; autograd-connected) and its D."""
-        D = GruWindow.apply(X, h0, *self.params, self.trainer)
+        Wx, Uh, Wfc = self.params[:3]
+        if self.head:
+            Wfc = HeadFold.apply(self.params[3], Wfc)
+        D = GruWindow.apply(X, h0, Wx, Uh, Wfc, self.trainer)
         return L2Loss.apply(D, Y, self.P), D
 
     def train_window(self, X, Y, h0=None):

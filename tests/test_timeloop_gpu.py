@@ -81,7 +81,19 @@ def test_trained_network_lowers_error(tl):
     assert tr["loop"] < 0.85 * zr["loop"], out
 
 
-def test_flows_experiment_on_other_geometries(tl, tmp_path):
+def test_trained_network_with_head_lowers_error(tl):
+    # the same study with the K = 1 net of Sec. 6.2 (GRU, output layer and
+    # convolutional head): 32 (51 + 32) 3 + 18 32 + 90 parameters at N_in = 51
+    _, timeloop = tl
+    out = timeloop.accuracy_experiment(head=True)
+    tr, zr = out["trained"], out["zero"]
+    assert out["head"] and out["params"] > 90
+    assert tr["teacher"] < 0.85 * zr["teacher"], out
+    assert tr["loop"] < 0.95 * zr["loop"], out
+
+
+@pytest.mark.parametrize("with_head", [False, True])
+def test_flows_experiment_on_other_geometries(tl, tmp_path, with_head):
     # the training workload's driver end to end on tiny flows: train on one
     # ellipse flow, evaluate on the held-out one and, unchanged, on the
     # two-obstacle, empty and L-shaped channels of Sec. 6.7
@@ -98,11 +110,13 @@ def test_flows_experiment_on_other_geometries(tl, tmp_path):
         geo.append(p)
     wpath = str(tmp_path / "w.npz")
     out = timeloop.flows_experiment(paths, 1, H=16, epochs=3, precision="f32", loop_steps=0,
-                                    eval_paths=geo, eval_loop_steps=3, weights_out=wpath)
+                                    eval_paths=geo, eval_loop_steps=3, weights_out=wpath, head=with_head)
     assert out["trainer_status"] == 0 and out["updates"] >= 3
     assert np.isfinite(out["loss_last_epoch"]) and out["loss_last_epoch"] < out["loss_first_epoch"]
     w = np.load(wpath)
-    assert w["W"].shape[0] == 48 and w["U"].shape == (48, 16) and w["Wfc"].shape[1] == 16
+    assert w["W"].shape[0] == 48 and w["U"].shape == (48, 16) and w["Wfc"].shape == (18, 16)
+    assert ("theta" in w) == with_head and out["head"] == with_head
+    assert out["params"] == w["W"].size + 48 * 16 + 18 * 16 + (90 if with_head else 0)
     for p, g in zip(geo, ("two", "none", "L")):
         r = out["geometries"][p]
         assert r["solid_cells"] == int(solver.geometry_mask(32, 8, g).sum())
