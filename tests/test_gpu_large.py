@@ -14,7 +14,7 @@ import pytest
 import torch
 
 from helpers import BOUNDARY_CLASSES, TOL, Params, class_errors, rel_l2
-from oracle import fem, step as ostep
+from oracle import fem, step as ostep, transfer
 from oracle.mesh import Mesh as OMesh
 from paper_2008_11520_gb300 import synth
 from parity import check, record
@@ -175,3 +175,21 @@ def test_large_sampled_windows(dn):
                  & (pj * s >= cj0 + lo_j) & ((pj + 1) * s <= cj0 + hi_j - 1))
         assert inner.sum() > 0
         check("window h", rel_l2(got["h"][gidx[inner]], out["h"][inner]), TOL["bf16"], "bf16", window=name)
+
+
+def test_large_whole_mesh_restriction(dn):
+    # S7 on the whole 2048 x 512 mesh in the bench's precision (4225 tiles, every
+    # tile edge and the obstacle's staircase): float-pair accumulation against
+    # the oracle's FP64 restriction of the same FP32 vector
+    c = synth.config("large")
+    full = OMesh(c["nxc"], c["nyc"], c["K"], c["s"], ellipse=c["ellipse"])
+    mesh = dn.Mesh(dn.make_desc(c["nxc"], c["nyc"], c["K"], c["s"], c["ellipse"], precision="f32"))
+    rng = np.random.default_rng(43)
+    bf = rng.standard_normal((2, full.Nf)).astype(np.float32).astype(np.float64)
+    bc = mesh.coarse(3)
+    dn.dnnmg_restrict(mesh, mesh.pack(bf), bc)
+    torch.cuda.synchronize()
+    ref = transfer.restrict(full, bf)
+    got = bc.cpu().numpy().reshape(3, -1)
+    check("whole-mesh R b_f (FP64 class)", rel_l2(got, ref), 1e-13, "f32", case="large")
+    assert np.array_equal(got == 0, ref == 0)
