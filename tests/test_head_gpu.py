@@ -11,6 +11,7 @@ import pytest
 import torch
 
 from helpers import rel_l2
+from parity import check
 from oracle import gru, head
 from oracle import train as otrain
 
@@ -51,9 +52,10 @@ def test_fold_and_gradient_match_oracle(dn, n_out, H):
     Weff = dn.head_fold(cu(theta), cu(Wfc))
     dth, dW = dn.head_backward(cu(theta), cu(Wfc), cu(G))
     ref_dth, ref_dW = head.fold_backward(theta, Wfc, G)
-    assert rel_l2(Weff.cpu().numpy(), head.fold(theta, Wfc)) <= TOL["f32"]
-    assert rel_l2(dth.cpu().numpy(), ref_dth) <= TOL["f32"]
-    assert rel_l2(dW.cpu().numpy(), ref_dW) <= TOL["f32"]
+    case = f"n_out {n_out}, H {H}"
+    check("head fold W_eff", rel_l2(Weff.cpu().numpy(), head.fold(theta, Wfc)), TOL["f32"], "f32", case=case)
+    check("head fold d theta", rel_l2(dth.cpu().numpy(), ref_dth), TOL["f32"], "f32", case=case)
+    check("head fold d W_fc", rel_l2(dW.cpu().numpy(), ref_dW), TOL["f32"], "f32", case=case)
     # deterministic: the same call gives the same bits
     dth2, _ = dn.head_backward(cu(theta), cu(Wfc), cu(G))
     assert torch.equal(dth, dth2)
@@ -79,8 +81,8 @@ def test_net_with_head_is_gru_step_then_head(dn, prec):
     dn.dnnmg_gru_step(net, Xc.cuda().contiguous(), ht, d, P)
     h_ref, dfc = gru.gru_step(Xq, h, Wx, Uh, Wfc)
     d_ref = head.head_rows(dfc, theta)
-    assert rel_l2(ht.double().cpu().numpy(), h_ref) <= TOL[prec]
-    assert rel_l2(d.double().cpu().numpy(), d_ref) <= TOL[prec]
+    check("net with head h", rel_l2(ht.double().cpu().numpy(), h_ref), TOL[prec], prec)
+    check("net with head d", rel_l2(d.double().cpu().numpy(), d_ref), TOL[prec], prec)
     with pytest.raises(ValueError):
         dn.Net(Wx, Uh, Wfc, prec, head=theta[:-1])
 
@@ -103,8 +105,8 @@ def test_training_with_head_gives_oracle_gradients(dn):
     L0, gWx, gUh, gWeff, _ = otrain.loss_and_grads(X[:, :, :n_in], h0, Y, Wx, Uh, Weff, alpha=0.0)
     gth, gWfc = head.fold_backward(theta, Wfc, gWeff)
     assert L.item() == pytest.approx(L0, rel=1e-5)
-    for g, ref in zip(grads, (gWx, gUh, gWfc, gth)):
-        assert rel_l2(g, ref) <= TOL["f32"]
+    for name, g, ref in zip(("W_x", "U_h", "W_fc", "theta"), grads, (gWx, gUh, gWfc, gth)):
+        check("window gradient with head " + name, rel_l2(g, ref), TOL["f32"], "f32")
     # the head starts near the identity
     assert rel_l2(Weff, Wfc) < 0.2
     # one update moves every parameter group and lowers the window loss
