@@ -149,6 +149,17 @@ def algorithmic_work(info, H):
     }
 
 
+def dominant(kernel_ms):
+    """The kernel with the largest share of the step, as the name of its entry
+    in ``algorithmic_work``.  The two S2+S3 kernels (closed-form tiles and
+    boundary tiles, concurrent inside the step) count as one entry, the stage,
+    with their times summed, should either of them be the largest."""
+    top = max(kernel_ms, key=kernel_ms.get)
+    if top in ("residual_cf", "residual_boundary"):
+        return "residual_features", kernel_ms["residual_cf"] + kernel_ms["residual_boundary"]
+    return top, kernel_ms[top]
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2008_11520_gb300 import dnnmg
@@ -410,9 +421,8 @@ def main():
     value = job_rate(world, dof, args.steps, r["total_ms"])
     pk = peaks()
     work = algorithmic_work(I, c["H"])
-    # dominant kernel: the stage with the largest share of the step
-    dom = max(r["stage_ms"], key=r["stage_ms"].get)
-    dom_ms = r["stage_ms"][dom]
+    # dominant kernel: the kernel with the largest share of the step
+    dom, dom_ms = dominant(r["kernel_ms"])
     # the roofline of a stage is whichever of HBM traffic and tensor work takes
     # longer at the measured peaks (the GRU GEMMs move more bytes than flops allow)
     w = work[dom]
@@ -420,12 +430,12 @@ def main():
     t_tc = w.get("flops", 0) / (pk["bf16_tflops"] * 1e12)
     if t_tc > t_hbm:
         ach = w["flops"] / (dom_ms / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+        roof = {"kernel": dom, "kernel_ms": dom_ms, "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                 "frac": ach / pk["bf16_tflops"], "traffic": measured_traffic(dom),
                 "peak_src": pk["src"] + " bf16 burst"}
     else:
         ach = w["bytes"] / (dom_ms / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+        roof = {"kernel": dom, "kernel_ms": dom_ms, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": measured_traffic(dom),
                 "algorithmic_bytes": w["bytes"], "peak_src": pk["src"] + " copy bandwidth"}
     stages = {}

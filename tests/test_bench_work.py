@@ -52,3 +52,17 @@ def test_algorithmic_work_by_hand(info):
     assert mb == {"coarse_pad": 38, "residual_features": 297, "gru": 586, "scatter_avg": 312,
                   "rhs": 269, "restrict": 160}
     assert round(w["gru"]["flops"] / 1e9, 1) == 92.9
+
+
+def test_dominant_kernel_is_the_largest_single_kernel():
+    import bench
+    # the bench's measured kernel times of the large workload: the GRU is the
+    # largest kernel although the two S2+S3 kernels together take longer
+    ms = {"coarse_pad": 0.0126, "residual_cf": 0.171, "residual_boundary": 0.036, "gru": 0.185,
+          "scatter_avg": 0.098, "rhs": 0.117, "restrict": 0.054}
+    assert bench.dominant(ms) == ("gru", 0.185)
+    ms["residual_cf"] = 0.2
+    name, t = bench.dominant(ms)
+    assert name == "residual_features" and t == pytest.approx(0.236)
+    ms = {"coarse_pad": 0.01, "residual_features": 0.3, "gru": 0.2}
+    assert bench.dominant(ms) == ("residual_features", 0.3)
