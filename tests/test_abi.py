@@ -124,3 +124,51 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             "    raise SystemExit('imported without the library')\n")
     r = _run_isolated(code, str(tmp_path))
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+def test_plain_c_client_links_and_queries(lib, tmp_path):
+    # The boundary is a C ABI: a C99 program that includes only the header
+    # compiles, takes the address of every declared entry point (so each links
+    # from libdnnmg.so), and runs the host-only size query and head-size query
+    # without a GPU, agreeing with the binding.
+    import shutil
+    import subprocess
+    from paper_2008_11520_gb300 import build, synth
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(build.nvcc())), "include")
+    syms = sorted(declared_symbols())
+    c = synth.config("large")
+    cx, cy, ax, ay = c["ellipse"]
+    src = "\n".join([
+        "#include <stdio.h>",
+        '#include "dnnmg.h"',
+        "static void *const entry_points[] = {" + ", ".join(f"(void *)&{s}" for s in syms) + "};",
+        "int main(void) {",
+        "    dnnmg_mesh_desc d = {0};",
+        "    dnnmg_mesh_info info;",
+        f"    d.nxc = {c['nxc']}; d.nyc = {c['nyc']}; d.K = {c['K']}; d.s = {c['s']};",
+        f"    d.lx = 2.2; d.ly = 0.41; d.obst_cx = {cx!r}; d.obst_cy = {cy!r}; d.obst_ax = {ax!r}; d.obst_ay = {ay!r};",
+        "    d.nu = 1e-3; d.k = 0.01; d.alpha0 = 0.1; d.u_max = 1.5; d.precision = DNNMG_F32;",
+        "    if (dnnmg_mesh_query(&d, &info) != DNNMG_OK) { printf(\"error %s\\n\", dnnmg_last_error()); return 1; }",
+        "    printf(\"%d %lld %lld %d %d %d %d\\n\", info.P, info.Nf, info.Nc, info.n_in, info.n_out, info.ldx,",
+        "           dnnmg_head_params(18));",
+        "    d.K = 7;",
+        "    if (dnnmg_mesh_query(&d, &info) != DNNMG_EINVAL) return 2;",
+        "    return entry_points[0] == 0;",
+        "}",
+    ])
+    (tmp_path / "client.c").write_text(src)
+    exe = str(tmp_path / "client")
+    libdir = os.path.dirname(build.LIB)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
+                        str(tmp_path / "client.c"), "-o", exe, "-L", libdir, "-ldnnmg", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    P, Nf, Nc, n_in, n_out, ldx, nt = (int(v) for v in r.stdout.split())
+    info = lib.dnnmg_mesh_query(lib.make_desc(c["nxc"], c["nyc"], c["K"], c["s"], c["ellipse"], precision="f32"))
+    assert (P, Nf, Nc, n_in, n_out, ldx) == (info.P, info.Nf, info.Nc, info.n_in, info.n_out, info.ldx)
+    assert nt == 90
