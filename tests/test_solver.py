@@ -300,6 +300,11 @@ def test_geometry_masks():
         assert (np.abs(xc[i[sel]] - cx) < 0.055).all() and (np.abs(yc[j[sel]] - cy) < 0.045).all()
     with pytest.raises(ValueError):
         solver.geometry_mask(nx, ny, "circle")
+    # the parity suite's own masks of the same geometries (written separately for the oracle meshes)
+    from helpers import geometry_mask as parity_mask
+    for g in ("two", "L"):
+        for nxc, nyc in ((64, 12), (40, 10), (128, 32)):
+            assert (parity_mask({"nxc": nxc, "nyc": nyc, "geometry": g}) == solver.geometry_mask(nxc, nyc, g)).all()
 
 
 def test_channel_without_obstacle_is_mirror_symmetric():
