@@ -12,7 +12,7 @@ import test_oracle_assembly as assembly
 import test_oracle_head as hpins
 import test_oracle_pins as pins
 import test_train_oracle as tpins
-from oracle import fem, gru, head, transfer
+from oracle import average, features, fem, gru, head, transfer
 from oracle import train as otrain
 
 
@@ -46,6 +46,15 @@ def _lps_pins():
 def _train_pins():
     return [lambda a=a: tpins.test_bptt_gradient_matches_finite_differences(a) for a in (0.0, 1e-4)] + \
            [tpins.test_gradient_of_a_single_step_by_hand, tpins.test_adam_closed_forms]
+
+
+def _feature_pins():
+    return [pins.test_features_hand_indexed]
+
+
+def _average_pins():
+    return [pins.test_constant_correction_survives_averaging, pins.test_general_constant_correction_within_one_ulp,
+            pins.test_averaging_of_two_patch_predictions]
 
 
 def _head_pins():
@@ -121,6 +130,33 @@ def _mutants():
         return p - lr * m / (np.sqrt(v) + eps), m, v
 
     o_fold_bw, o_vertex = head.fold_backward, head.vertex_block
+    o_feat, o_geo, o_avg = features.patch_features, features.patch_geometry, average.scatter_average
+
+    def features_uv_swapped(mesh, prm, xf, r):
+        # the coarse u and v columns exchanged (D9 orders u before v)
+        X = o_feat(mesh, prm, xf, r).copy()
+        nf, nc = mesh.nf, mesh.nc
+        u0 = 3 * nf
+        X[:, u0:u0 + nc], X[:, u0 + nc:u0 + 2 * nc] = X[:, u0 + nc:u0 + 2 * nc].copy(), X[:, u0:u0 + nc].copy()
+        return X
+
+    def geometry_angles_in_degrees(mesh):
+        g = o_geo(mesh).copy()
+        g[8:] = np.degrees(g[8:])
+        return g
+
+    def average_by_sum(mesh, d, xf):
+        # sums the predictions of a shared node instead of averaging them
+        fine, _ = features.patch_node_indices(mesh)
+        v = np.array([np.asarray(xf[0], dtype=np.float64), np.asarray(xf[1], dtype=np.float64)])
+        d = np.asarray(d, dtype=np.float64)
+        sums = np.zeros((2, mesh.Nf))
+        for p in range(mesh.P):
+            sums[0, fine[p]] += d[p, :mesh.nf]
+            sums[1, fine[p]] += d[p, mesh.nf:]
+        free = ~mesh.dirichlet.ravel()
+        v[:, free] += sums[:, free]
+        return v
 
     def fold_backward_one_product(theta, Wfc, G):
         # drops the (C_f x)[p] q[p + t] half of each filter's gradient
@@ -138,6 +174,9 @@ def _mutants():
         return acc
 
     return {
+        "coarse u and v features swapped": (features, "patch_features", features_uv_swapped, _feature_pins),
+        "geometry angles in degrees": (features, "patch_geometry", geometry_angles_in_degrees, _feature_pins),
+        "shared-node predictions summed, not averaged": (average, "scatter_average", average_by_sum, _average_pins),
         "transposed head layer not the adjoint": (head, "corr2d_t", head.corr2d, _head_pins),
         "vertex block without interleaving": (head, "vertex_block", vertex_without_interleaving, _head_pins),
         "head filter gradient halved": (head, "fold_backward", fold_backward_one_product, _head_pins),
