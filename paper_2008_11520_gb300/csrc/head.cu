@@ -17,8 +17,7 @@
 // back (dnnmg_head_backward).
 //
 // theta [72 + N_out]: k_s [4][3][3] (row offset -1..1 in y, column offset
-// -1..1 in x), k_v [4][9] (offset -4..4), w [N_out].  One thread per column of
-// W_fc; the columns are few (the GRU width), so these kernels are tiny.
+// -1..1 in x), k_v [4][9] (offset -4..4), w [N_out].
 #include "common.cuh"
 
 namespace dnnmg {
@@ -26,140 +25,133 @@ namespace {
 
 constexpr int HF = 4, HKS = 3, HKV = 9, HMAXN = 9, HMAXOUT = 2 * HMAXN * HMAXN;
 constexpr int HCONV = HF * (HKS * HKS + HKV);   // filter weights of both blocks (72)
+constexpr int HTH = 128;                        // threads per column block
 
-// c = C y over an n x n grid
-template <typename T> __device__ void corr2d(const T *g, const T *k, int n, T *c) {
-    for (int j = 0; j < n; ++j)
-        for (int i = 0; i < n; ++i) {
-            T a = T(0);
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx)
-                    if (j + dy >= 0 && j + dy < n && i + dx >= 0 && i + dx < n)
-                        a += k[(dy + 1) * HKS + dx + 1] * g[(j + dy) * n + i + dx];
-            c[j * n + i] = a;
-        }
-}
+// One block per column j of W_fc, one thread per entry: the rows of a column
+// are few (N_out <= 162), and the filters' work per column is a few thousand
+// products, so the column's vectors and their correlations stay in shared
+// memory.  Entry e = comp nf + jj n + ii (node (ii, jj) of component comp);
+// position p = 2 node + comp in the vertex-by-vertex sequence.
+struct HeadIdx {
+    int n, nf, m;
+    __device__ HeadIdx(int n_) : n(n_), nf(n_ * n_), m(2 * n_ * n_) {}
+    // the entry of sequence position p
+    __device__ int seq(int p) const { return (p & 1) * nf + (p >> 1); }
+    // the sequence position of entry e
+    __device__ int pos(int e) const { return 2 * (e % nf) + e / nf; }
+};
 
-// y += C^T c over an n x n grid
-template <typename T> __device__ void corr2d_t_add(const T *c, const T *k, int n, T *y) {
-    for (int j = 0; j < n; ++j)
-        for (int i = 0; i < n; ++i)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx)
-                    if (j + dy >= 0 && j + dy < n && i + dx >= 0 && i + dx < n)
-                        y[(j + dy) * n + i + dx] += k[(dy + 1) * HKS + dx + 1] * c[j * n + i];
-}
-
-template <typename T> __device__ void corr1d(const T *s, const T *k, int m, T *c) {
-    for (int p = 0; p < m; ++p) {
+// c = C_f y for the 4 spatial filters (per component, zero outside the n x n
+// grid) and the 4 vertex filters (on the sequence), for every entry / position
+template <typename T>
+__device__ void head_corr(const HeadIdx &ix, const T *ks, const T *kv, const T *y, T *cs, T *cv) {
+    for (int it = threadIdx.x; it < HF * ix.m; it += blockDim.x) {
+        const int f = it / ix.m, e = it - f * ix.m;
+        const int comp = e / ix.nf, node = e - comp * ix.nf, jj = node / ix.n, ii = node - jj * ix.n;
+        const T *k = ks + f * HKS * HKS;
         T a = T(0);
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                if (jj + dy >= 0 && jj + dy < ix.n && ii + dx >= 0 && ii + dx < ix.n)
+                    a += k[(dy + 1) * HKS + dx + 1] * y[comp * ix.nf + (jj + dy) * ix.n + ii + dx];
+        cs[f * ix.m + e] = a;
+        // the same item as sequence position p = e of vertex filter f
+        const T *kf = kv + f * HKV;
+        T b = T(0);
         for (int t = -HKV / 2; t <= HKV / 2; ++t)
-            if (p + t >= 0 && p + t < m) a += k[t + HKV / 2] * s[p + t];
-        c[p] = a;
+            if (e + t >= 0 && e + t < ix.m) b += kf[t + HKV / 2] * y[ix.seq(e + t)];
+        cv[f * ix.m + e] = b;
     }
 }
 
-template <typename T> __device__ void corr1d_t_add(const T *c, const T *k, int m, T *s) {
-    for (int p = 0; p < m; ++p)
-        for (int t = -HKV / 2; t <= HKV / 2; ++t)
-            if (p + t >= 0 && p + t < m) s[p + t] += k[t + HKV / 2] * c[p];
-}
-
-// out = B_s x + B_v x (no weighting); c, s, acc are scratch of N_out entries
+// (B_s y + B_v y)[e] from the correlations of y: the adjoints C_f^T summed
+// over the filters of both blocks
 template <typename T>
-__device__ void head_blocks(const T *theta, int n, const T *x, T *out, T *c, T *s, T *acc) {
-    const int nf = n * n, m = 2 * nf;
-    const T *ks = theta, *kv = theta + HF * HKS * HKS;
-    for (int e = 0; e < m; ++e) out[e] = T(0);
-    for (int comp = 0; comp < 2; ++comp)
-        for (int f = 0; f < HF; ++f) {
-            corr2d(x + comp * nf, ks + f * HKS * HKS, n, c);
-            corr2d_t_add(c, ks + f * HKS * HKS, n, out + comp * nf);
-        }
-    for (int v = 0; v < nf; ++v) {
-        s[2 * v] = x[v];
-        s[2 * v + 1] = x[nf + v];
-    }
-    for (int e = 0; e < m; ++e) acc[e] = T(0);
+__device__ T head_adjoint(const HeadIdx &ix, const T *ks, const T *kv, const T *cs, const T *cv, int e) {
+    const int comp = e / ix.nf, node = e - comp * ix.nf, jj = node / ix.n, ii = node - jj * ix.n;
+    T a = T(0);
     for (int f = 0; f < HF; ++f) {
-        corr1d(s, kv + f * HKV, m, c);
-        corr1d_t_add(c, kv + f * HKV, m, acc);
+        const T *k = ks + f * HKS * HKS;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                if (jj - dy >= 0 && jj - dy < ix.n && ii - dx >= 0 && ii - dx < ix.n)
+                    a += k[(dy + 1) * HKS + dx + 1] * cs[f * ix.m + comp * ix.nf + (jj - dy) * ix.n + ii - dx];
     }
-    for (int v = 0; v < nf; ++v) {
-        out[v] += acc[2 * v];
-        out[nf + v] += acc[2 * v + 1];
+    const int p = ix.pos(e);
+    T b = T(0);
+    for (int f = 0; f < HF; ++f) {
+        const T *kf = kv + f * HKV;
+        for (int t = -HKV / 2; t <= HKV / 2; ++t)
+            if (p - t >= 0 && p - t < ix.m) b += kf[t + HKV / 2] * cv[f * ix.m + p - t];
     }
+    return a + b;
 }
 
-// W_eff[:, j] = w * (B_s + B_v) W_fc[:, j]; W_fc, W_eff [N_out][H]
+// W_eff[:, j] = w * (B_s + B_v) W_fc[:, j]; W_fc, W_eff [N_out][H]; block j
 template <typename T>
-__global__ void k_head_fold(int n, int H, const T *__restrict__ theta, const T *__restrict__ Wfc, T *__restrict__ Weff) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= H) return;
-    const int m = 2 * n * n;
-    const T *w = theta + HCONV;
-    T x[HMAXOUT], out[HMAXOUT], c[HMAXOUT], s[HMAXOUT], acc[HMAXOUT];
-    for (int e = 0; e < m; ++e) x[e] = Wfc[(size_t)e * H + j];
-    head_blocks(theta, n, x, out, c, s, acc);
-    for (int e = 0; e < m; ++e) Weff[(size_t)e * H + j] = w[e] * out[e];
+__global__ void __launch_bounds__(HTH)
+k_head_fold(int n, int H, const T *__restrict__ theta, const T *__restrict__ Wfc, T *__restrict__ Weff) {
+    __shared__ T x[HMAXOUT], cs[HF * HMAXOUT], cv[HF * HMAXOUT];
+    const HeadIdx ix(n);
+    const int j = blockIdx.x;
+    const T *ks = theta, *kv = theta + HF * HKS * HKS, *w = theta + HCONV;
+    for (int e = threadIdx.x; e < ix.m; e += blockDim.x) x[e] = Wfc[(size_t)e * H + j];
+    __syncthreads();
+    head_corr(ix, ks, kv, x, cs, cv);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ix.m; e += blockDim.x)
+        Weff[(size_t)e * H + j] = w[e] * head_adjoint(ix, ks, kv, cs, cv, e);
 }
 
-// Gradient of sum(G * W_eff) for column j: dW_fc[:, j] = (B_s + B_v)(w * g)
+// Gradient of sum(G * W_eff) for column j (block j): dW_fc[:, j] = (B_s + B_v)(w * g)
 // (both blocks are symmetric) and this column's share of d theta in
 // work[j][72 + N_out]: with q = w * g and x = W_fc[:, j],
 //   d k_f[t] = sum_p (C_f q)[p] x[p + t] + (C_f x)[p] q[p + t],   d w = g * (B_s + B_v) x.
 template <typename T>
-__global__ void k_head_grad_cols(int n, int H, const T *__restrict__ theta, const T *__restrict__ Wfc,
-                                 const T *__restrict__ G, T *__restrict__ dWfc, T *__restrict__ work) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= H) return;
-    const int nf = n * n, m = 2 * nf, nt = HCONV + m;
+__global__ void __launch_bounds__(HTH)
+k_head_grad_cols(int n, int H, const T *__restrict__ theta, const T *__restrict__ Wfc, const T *__restrict__ G,
+                 T *__restrict__ dWfc, T *__restrict__ work) {
+    __shared__ T x[HMAXOUT], g[HMAXOUT], q[HMAXOUT];
+    __shared__ T csx[HF * HMAXOUT], cvx[HF * HMAXOUT], csq[HF * HMAXOUT], cvq[HF * HMAXOUT];
+    const HeadIdx ix(n);
+    const int j = blockIdx.x, nt = HCONV + ix.m;
     const T *ks = theta, *kv = theta + HF * HKS * HKS, *w = theta + HCONV;
-    T x[HMAXOUT], q[HMAXOUT], out[HMAXOUT], c[HMAXOUT], s[HMAXOUT], acc[HMAXOUT];
     T *part = work + (size_t)j * nt;
-    for (int e = 0; e < m; ++e) {
+    for (int e = threadIdx.x; e < ix.m; e += blockDim.x) {
         x[e] = Wfc[(size_t)e * H + j];
-        q[e] = w[e] * G[(size_t)e * H + j];
+        g[e] = G[(size_t)e * H + j];
+        q[e] = w[e] * g[e];
     }
-    head_blocks(theta, n, q, out, c, s, acc);
-    for (int e = 0; e < m; ++e) dWfc[(size_t)e * H + j] = out[e];
-    head_blocks(theta, n, x, out, c, s, acc);
-    for (int e = 0; e < m; ++e) part[HCONV + e] = G[(size_t)e * H + j] * out[e];
-    // spatial filters: both components; c holds C_f q, acc holds C_f x
-    for (int f = 0; f < HF; ++f) {
-        T dk[HKS * HKS];
-        for (int t = 0; t < HKS * HKS; ++t) dk[t] = T(0);
-        for (int comp = 0; comp < 2; ++comp) {
-            const T *xs = x + comp * nf, *qs = q + comp * nf;
-            corr2d(qs, ks + f * HKS * HKS, n, c);
-            corr2d(xs, ks + f * HKS * HKS, n, acc);
-            for (int jj = 0; jj < n; ++jj)
-                for (int ii = 0; ii < n; ++ii)
-                    for (int dy = -1; dy <= 1; ++dy)
-                        for (int dx = -1; dx <= 1; ++dx)
-                            if (jj + dy >= 0 && jj + dy < n && ii + dx >= 0 && ii + dx < n) {
-                                const int o = (jj + dy) * n + ii + dx;
-                                dk[(dy + 1) * HKS + dx + 1] += c[jj * n + ii] * xs[o] + acc[jj * n + ii] * qs[o];
-                            }
+    __syncthreads();
+    head_corr(ix, ks, kv, x, csx, cvx);
+    head_corr(ix, ks, kv, q, csq, cvq);
+    __syncthreads();
+    for (int it = threadIdx.x; it < ix.m + HCONV; it += blockDim.x) {
+        if (it < ix.m) {
+            dWfc[(size_t)it * H + j] = head_adjoint(ix, ks, kv, csq, cvq, it);
+            part[HCONV + it] = g[it] * head_adjoint(ix, ks, kv, csx, cvx, it);
+        } else if (it < ix.m + HF * HKS * HKS) {
+            // spatial filter f, tap (dy, dx): both components
+            const int r = it - ix.m, f = r / (HKS * HKS), tap = r - f * HKS * HKS;
+            const int dy = tap / HKS - 1, dx = tap % HKS - 1;
+            T a = T(0);
+            for (int e = 0; e < ix.m; ++e) {
+                const int comp = e / ix.nf, node = e - comp * ix.nf, jj = node / ix.n, ii = node - jj * ix.n;
+                if (jj + dy >= 0 && jj + dy < ix.n && ii + dx >= 0 && ii + dx < ix.n) {
+                    const int o = comp * ix.nf + (jj + dy) * ix.n + ii + dx;
+                    a += csq[f * ix.m + e] * x[o] + csx[f * ix.m + e] * q[o];
+                }
+            }
+            part[r] = a;
+        } else {
+            // vertex filter f, offset t, on the sequences of x and q
+            const int r = it - ix.m - HF * HKS * HKS, f = r / HKV, t = r - f * HKV - HKV / 2;
+            T a = T(0);
+            for (int p = 0; p < ix.m; ++p)
+                if (p + t >= 0 && p + t < ix.m)
+                    a += cvq[f * ix.m + p] * x[ix.seq(p + t)] + cvx[f * ix.m + p] * q[ix.seq(p + t)];
+            part[HF * HKS * HKS + r] = a;
         }
-        for (int t = 0; t < HKS * HKS; ++t) part[f * HKS * HKS + t] = dk[t];
-    }
-    // vertex filters on the interleaved sequences (x into s, q into out)
-    for (int v = 0; v < nf; ++v) {
-        s[2 * v] = x[v];
-        s[2 * v + 1] = x[nf + v];
-        out[2 * v] = q[v];
-        out[2 * v + 1] = q[nf + v];
-    }
-    for (int f = 0; f < HF; ++f) {
-        T dk[HKV];
-        for (int t = 0; t < HKV; ++t) dk[t] = T(0);
-        corr1d(out, kv + f * HKV, m, c);
-        corr1d(s, kv + f * HKV, m, acc);
-        for (int p = 0; p < m; ++p)
-            for (int t = -HKV / 2; t <= HKV / 2; ++t)
-                if (p + t >= 0 && p + t < m) dk[t + HKV / 2] += c[p] * s[p + t] + acc[p] * out[p + t];
-        for (int t = 0; t < HKV; ++t) part[HF * HKS * HKS + f * HKV + t] = dk[t];
     }
 }
 
@@ -194,7 +186,7 @@ int dnnmg_head_fold(int n_out, int hidden, const float *theta, const float *Wfc,
     const int n = head_side(n_out);
     if (!n) return fail(DNNMG_EUNSUPPORTED, "head: N_out = %d is not 2 n^2 with n odd, 3..9", n_out);
     if (hidden < 1 || !theta || !Wfc || !Weff) return fail(DNNMG_EINVAL, "head: bad argument");
-    k_head_fold<float><<<(hidden + 63) / 64, 64, 0, st>>>(n, hidden, theta, Wfc, Weff);
+    k_head_fold<float><<<hidden, HTH, 0, st>>>(n, hidden, theta, Wfc, Weff);
     DNNMG_LAUNCH_CHECK("k_head_fold");
     return DNNMG_OK;
 }
@@ -207,7 +199,7 @@ int dnnmg_head_backward(int n_out, int hidden, const float *theta, const float *
     if (hidden < 1 || !theta || !Wfc || !G || !dtheta || !dWfc || !work)
         return fail(DNNMG_EINVAL, "head: bad argument");
     const int nt = HCONV + n_out;
-    k_head_grad_cols<float><<<(hidden + 63) / 64, 64, 0, st>>>(n, hidden, theta, Wfc, G, dWfc, work);
+    k_head_grad_cols<float><<<hidden, HTH, 0, st>>>(n, hidden, theta, Wfc, G, dWfc, work);
     DNNMG_LAUNCH_CHECK("k_head_grad_cols");
     k_head_grad_sum<float><<<(nt + 127) / 128, 128, 0, st>>>(nt, hidden, work, dtheta);
     DNNMG_LAUNCH_CHECK("k_head_grad_sum");
@@ -228,7 +220,7 @@ int dnnmg_net_create_head(int n_in, int hidden, int n_out, const double *Wx, con
     cudaError_t e = cudaMemcpy(d, theta, sizeof(double) * nt, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d + nt, Wfc, sizeof(double) * nw, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_head_fold<double><<<(hidden + 63) / 64, 64>>>(n, hidden, d, d + nt, d + nt + nw);
+        k_head_fold<double><<<hidden, HTH>>>(n, hidden, d, d + nt, d + nt + nw);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(weff.data(), d + nt + nw, sizeof(double) * nw, cudaMemcpyDeviceToHost);

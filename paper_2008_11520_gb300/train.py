@@ -288,16 +288,17 @@ def e_rel(mesh, weights, spec, steps, H, k=synth.DT, t0=0.0):
     return float(np.mean(with_net)), float(np.mean(without))
 
 
-def bench(P=65536, T=10, n_in=51, H=64, n_out=18, iters=10, warmup=3, precision="f32"):
+def bench(P=65536, T=10, n_in=51, H=64, n_out=18, iters=10, warmup=3, precision="f32", head=False):
     """Time one training update (window forward, backward, Adam) at the
     training workload's batch (65 536 patches, T = 10, H = 64, K = 1 net) on
-    random inputs (the cost does not depend on the values)."""
+    random inputs (the cost does not depend on the values); ``head``: with the
+    convolutional head (its fold and fold gradient in every update)."""
     import json
     ldx = (n_in + 15) // 16 * 16
     g = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn(T, P, ldx, device="cuda", generator=g)
     Y = 0.1 * torch.randn(T, P, n_out, device="cuda", generator=g)
-    tn = PatchNetTrainer(n_in, ldx, H, n_out, T, P, seed=0, std=0.05, out_std=0.05, precision=precision)
+    tn = PatchNetTrainer(n_in, ldx, H, n_out, T, P, seed=0, std=0.05, out_std=0.05, precision=precision, head=head)
     for _ in range(warmup):
         tn.train_window(X, Y)
     torch.cuda.synchronize()
@@ -312,12 +313,12 @@ def bench(P=65536, T=10, n_in=51, H=64, n_out=18, iters=10, warmup=3, precision=
     flops = 3.0 * fwd                                          # + state and weight gradients
     line = {"metric": "training update time", "unit": "ms", "value": ms, "patches": P, "T": T, "H": H,
             "n_in": n_in, "n_out": n_out, "gflop_per_update": flops / 1e9,
-            "tflops": flops / (ms / 1e3) / 1e12, "dtype": precision, "data": "synthetic"}
+            "tflops": flops / (ms / 1e3) / 1e12, "dtype": precision, "head": bool(head), "data": "synthetic"}
     print(json.dumps(line))
     return line
 
 
 if __name__ == "__main__":
     import sys
-    bench(precision=sys.argv[1] if len(sys.argv) > 1 else "f32")
+    bench(precision=sys.argv[1] if len(sys.argv) > 1 else "f32", head="--head" in sys.argv[2:])
 
